@@ -1,0 +1,77 @@
+"""Pins of the oracle CTMRG: the norm network of a PEPS whose double layer is
+the 2D Ising partition function (Onsager, Yang), with anisotropic couplings
+and random bond gauges so that a transposed or swapped leg fails."""
+import numpy as np
+import pytest
+
+from oracle import ctmrg, exact
+
+
+def _run(T, chi, edge_vec=None, tol=1e-13, max_sweeps=400):
+    a = ctmrg.double_tensor(T)
+    env = ctmrg.init_env(chi, T.shape[1], edge_vec)
+    env, info = ctmrg.ctmrg(a, env, tol=tol, max_sweeps=max_sweeps)
+    return a, env, info
+
+
+@pytest.mark.parametrize("Kh,Kv,seed", [(0.30, 0.30, None), (0.30, 0.20, 7), (0.15, 0.36, 11), (0.25, 0.25, 3)])
+def test_onsager_disordered(Kh, Kv, seed):
+    T = exact.ising_peps(Kh, Kv, gauge_seed=seed)
+    a, env, info = _run(T, 24)
+    assert info["delta"] < 1e-12
+    assert abs(np.log(ctmrg.kappa(env, a)) - exact.onsager_lnZ(Kh, Kv)) < 1e-10
+
+
+def test_onsager_ordered_with_broken_boundary():
+    Kh, Kv = 0.6, 0.5
+    T = exact.ising_peps(Kh, Kv)
+    V = exact.ising_bond_root(Kh)
+    a, env, info = _run(T, 24, edge_vec=np.outer(V[0], V[0]).reshape(4))
+    assert abs(np.log(ctmrg.kappa(env, a)) - exact.onsager_lnZ(Kh, Kv)) < 1e-10
+
+
+@pytest.mark.parametrize("K", [0.5, 0.7])
+def test_yang_magnetisation(K):
+    T = exact.ising_peps(K, K)
+    V = exact.ising_bond_root(K)
+    a, env, info = _run(T, 24, edge_vec=np.outer(V[0], V[0]).reshape(4))
+    X = ctmrg.expval_matrix(T, ctmrg.metric(env, 2))
+    m = np.trace(np.diag([1.0, -1.0]) @ X.T) / np.trace(X)
+    assert abs(m - exact.yang_m(K)) < 1e-9
+
+
+def test_rotation_is_a_4_cycle_and_moves_are_gauge_covariant():
+    T = exact.ising_peps(0.3, 0.2, gauge_seed=5)
+    a = ctmrg.double_tensor(T)
+    assert np.array_equal(ctmrg.rotate(a, 4), a)
+    # rotating the lattice by 90 degrees swaps the couplings: same free energy
+    # as the transposed anisotropy
+    T2 = exact.ising_peps(0.2, 0.3, gauge_seed=None)
+    a2, env2, _ = _run(T2, 20)
+    a1, env1, _ = _run(T, 20)
+    assert abs(np.log(ctmrg.kappa(env1, a1)) - np.log(ctmrg.kappa(env2, a2))) < 1e-10
+
+
+def test_product_state_is_exact_at_chi_1_and_truncation_zero():
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(3)
+    # a D=1 product PEPS with a random 3-dim physical vector: rank-1 everything
+    T = v.reshape(3, 1, 1, 1, 1)
+    a, env, info = _run(T, 4)
+    assert max(info["trunc"]) < 1e-28
+    X = ctmrg.expval_matrix(T, ctmrg.metric(env, 1))
+    assert np.allclose(X / np.trace(X), np.outer(v, v) / (v @ v), atol=1e-14)
+
+
+def test_projector_is_oblique_identity_when_untruncated():
+    """With chi >= rank, P P~ acts as the identity between the two halves."""
+    rng = np.random.default_rng(1)
+    chi, d2 = 3, 4
+    Qul = rng.standard_normal((chi, d2, chi, d2))
+    Qdl = rng.standard_normal((chi, d2, chi, d2))
+    P, Pt, spec, trunc = ctmrg.projectors(Qul, Qdl, chi * d2, 1e-14)
+    n = chi * d2
+    M = Qul.reshape(n, n).T @ Qdl.reshape(n, n)
+    assert np.allclose(Qul.reshape(n, n).T @ P @ Pt @ Qdl.reshape(n, n), M, atol=1e-10)
+    assert trunc < 1e-28
+    assert np.allclose(np.sort(spec)[::-1], np.linalg.svd(M, compute_uv=False), atol=1e-12)

@@ -1,0 +1,140 @@
+"""Pins of the oracle's bond update and of the whole eeFU pipeline against
+closed forms and exact diagonalisation."""
+import numpy as np
+import pytest
+
+import kh_inputs
+from oracle import bond, ctmrg, eefu, exact, model, peps
+
+
+def _fresh(D, chi, **kw):
+    prm = eefu.Params(D=D, chi=chi, **kw)
+    A, B = peps.product_state(D)
+    return eefu.State(A, B, prm)
+
+
+def test_beta0_invariants():
+    st = _fresh(2, 6, J=0.5, K=1.2)
+    r = eefu.measure(st)
+    for k in ("E_site", "Hx", "Hy", "Hz", "Ax", "Ay", "Az", "Bx", "By", "Bz"):
+        assert abs(r[k]) < 1e-15
+    assert r["trunc"] < 1e-28
+    # the identity gate leaves the product state exactly representable
+    info = eefu.apply_gate(st, "z", np.eye(4))
+    assert info["rel_cost"] < 1e-28
+
+
+@pytest.mark.parametrize("gamma", ["x", "y", "z"])
+def test_single_layer_is_exact_dimer(gamma):
+    J, K = model.couplings(0.3 * np.pi)
+    st = _fresh(4, 6, J=J, K=K)
+    db = 0.2
+    tau = dict(x=db / 4, y=db / 4, z=db / 2)[gamma]
+    info = eefu.apply_gate(st, gamma, st.prm.gate(gamma, tau))
+    assert info["rel_cost"] < 1e-20
+    r = eefu.measure(st)
+    want = exact.dimer_energy(J, K, 2 * tau)
+    assert abs(r["H" + gamma] - want) < 1e-13
+    for g in "xyz":
+        if g != gamma:
+            assert abs(r["H" + g]) < 1e-13
+    assert abs(r["E_site"] - 0.5 * want) < 1e-13
+
+
+def test_kz_only_closed_form_all_beta():
+    Kz = 1.3
+    st = _fresh(2, 6, J=0.0, K=0.0, K_gamma={"x": 0.0, "y": 0.0, "z": Kz})
+    for n in range(1, 9):
+        eefu.trotter_step(st, 0.05)
+        if n % 4 == 0:
+            r = eefu.measure(st)
+            assert abs(r["E_site"] - exact.kz_only_energy(Kz, 0.05 * n)) < 1e-10
+
+
+@pytest.mark.parametrize("hA,hB", [(0.7, 0.7), (0.7, -0.3)])
+def test_field_only_closed_form(hA, hB):
+    st = _fresh(2, 4, J=0.0, K=0.0, hA=hA, hB=hB)
+    for _ in range(6):
+        eefu.trotter_step(st, 0.05)
+    r = eefu.measure(st)
+    beta = 0.3
+    eA, mA = exact.field_only(hA, beta)
+    eB, mB = exact.field_only(hB, beta)
+    assert abs(r["Az"] - mA) < 1e-12 and abs(r["Bz"] - mB) < 1e-12
+    assert abs(r["E_site"] - 0.5 * (eA + eB)) < 1e-12
+
+
+def test_kh_high_temperature_against_ed_and_series():
+    """D=4 eeFU at beta=0.05, 0.1 against 8- and 12-site ED: the eeFU value must
+    sit within the finite-size spread |E8-E12| (+ Trotter margin) of E12, and
+    E/beta must approach the high-T slope."""
+    phi = 0.3 * np.pi
+    J, K = model.couplings(phi)
+    betas = np.array([0.05, 0.1])
+    E8 = exact.honeycomb_ed(2, 2, J, K, betas)
+    E12 = exact.honeycomb_ed(2, 3, J, K, betas)
+    st = _fresh(4, 12, J=J, K=K)
+    res = eefu.evolve(st, 0.01, 10, measure_every=5)
+    for r, e8, e12, b in zip(res, E8, E12, betas):
+        assert abs(r["beta"] - b) < 1e-12
+        assert abs(r["E_site"] - e12) < abs(e8 - e12) + 5e-6
+        assert abs(r["E_site"] / b - exact.high_T_energy_slope(J, K)) < 0.05 * b + 1e-4
+        # C3 symmetry at h=0 up to Trotter asymmetry
+        assert abs(r["Hx"] - r["Hz"]) < 1e-4 and abs(r["Hy"] - r["Hz"]) < 1e-4
+        assert abs(r["Ay"]) < 1e-15 and abs(r["By"]) < 1e-15
+
+
+def test_site_moments_agree_across_mappings():
+    """All three gamma-mapped environments describe the same state: <S^z_A>
+    and <S^x_B> agree between mappings (a leg mix-up between mappings fails)."""
+    J, K = model.couplings(0.3 * np.pi)
+    st = _fresh(4, 12, J=J, K=K, hA=0.5, hB=-0.2)
+    eefu.evolve(st, 0.02, 3)
+    eefu.measure(st)
+    vals = []
+    for gamma in "xyz":
+        T = peps.composite(st.A, st.B, gamma)
+        X = ctmrg.expval_matrix(T, ctmrg.metric(st.obs_env[gamma], 4))
+        from oracle import observables
+        vals.append(observables.site_moments(X))
+    for key in ("Az", "Bz", "Ax", "Bx"):
+        v = [m[key] for m in vals]
+        assert max(v) - min(v) < 1e-9, (key, v)
+    assert abs(vals[0]["Az"]) > 1e-3
+
+
+def test_bond_update_eckart_young():
+    """N = identity: the ALS optimum is the truncated SVD and the cost is the
+    discarded sum of squared singular values."""
+    D = 2
+    Tp = kh_inputs.random_composite(D, 3)
+    N = np.eye(D ** 4)
+    A2, B2, S = bond.svd_init(Tp, D)
+    A3, B3, info = bond.als(Tp, N, D, tol=1e-15, max_iter=20, reg=0.0)
+    want = np.sum(S[D:] ** 2) / np.sum(S ** 2)
+    assert abs(info["rel_cost"] - want) < 1e-12
+    # rank <= D: the cost is zero
+    T0 = np.einsum("abURk,cdDLk->abcdLURD", A2, B2).reshape(Tp.shape)
+    _, _, info0 = bond.als(T0, N, D, tol=1e-15, max_iter=5, reg=0.0)
+    assert info0["rel_cost"] < 1e-26
+
+
+def test_bond_update_monotone_and_gauge_invariant():
+    D = 2
+    Tp = kh_inputs.random_composite(D, 4)
+    rng = np.random.default_rng(9)
+    G = rng.standard_normal((D ** 4, D ** 4))
+    N = G @ G.T / D ** 4 + 0.1 * np.eye(D ** 4)
+    A2, B2, info = bond.als(Tp, N, D, tol=0.0, max_iter=15, reg=0.0)
+    h = np.array(info["history"])
+    assert np.all(np.diff(h) <= 1e-14)
+    assert h[-1] < h[0]
+    An, Bn, _ = bond.balance_gauge(A2, B2)
+    T1 = np.einsum("abURk,cdDLk->abcdLURD", A2, B2).ravel()
+    T2 = np.einsum("abURk,cdDLk->abcdLURD", An, Bn).ravel()
+    assert np.allclose(T2 / np.linalg.norm(T2), T1 / np.linalg.norm(T1), atol=1e-13)
+    # balanced: A^T A = B^T B = diag(S)/scale
+    ga = An.reshape(-1, D).T @ An.reshape(-1, D)
+    gb = Bn.reshape(-1, D).T @ Bn.reshape(-1, D)
+    assert np.allclose(ga, np.diag(np.diag(ga)), atol=1e-13)
+    assert np.allclose(np.diag(ga) / np.trace(ga), np.diag(gb) / np.trace(gb), atol=1e-13)
