@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: eeFU imaginary-time Trotter steps (and CTM sweeps) per second.
+
+One step = one second-order Trotter step of the exact-environment full update
+(five gate layers x, y, z, y, x; each builds the gated composite, runs a fixed
+number of CTM sweeps, forms the metric and runs the ALS bond update) followed
+by the observables (three gamma-mapped CTMRGs of the un-gated state with a
+fixed number of sweeps, E/site and sublattice magnetisations read back).
+
+Workload: Kitaev point K=1, J=0, D=4, chi=64, dbeta=0.01, seeded synthetic
+start (beta=0 product state plus 5% N(0,1) noise, seed = rank).  Multi-GPU:
+independent replicas per rank (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N --steps K --warmup W --prec fp32 --impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import kh_inputs  # noqa: E402
+
+METRIC = "CTM sweeps/s and eeFU Trotter steps/s at (D,chi); TC TFLOP/s vs peak; err vs FP64"
+WORKLOAD = "kitaev_D4_chi64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--ctm-sweeps", type=int, default=4, help="CTM sweeps per gate layer")
+    ap.add_argument("--obs-sweeps", type=int, default=2, help="CTM sweeps per mapping in the observables")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="default: = --steps")
+    return ap.parse_args()
+
+
+def workload():
+    w = dict(kh_inputs.WORKLOADS[WORKLOAD])
+    return w
+
+
+def sweeps_per_step(a):
+    return 5 * a.ctm_sweeps + 3 * a.obs_sweeps
+
+
+# ----------------------------------------------------------------- distributed
+
+def dist_setup(a):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % gpu_index) \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % gpu_index
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- ours
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def roofline_for(prec, prof, pk, pk_src):
+    """Dominant timed kernel category -> achieved vs peak."""
+    cat = max(prof, key=lambda k: prof[k]["ms"])
+    c = prof[cat]
+    if c["launches"] == 0 or c["ms"] <= 0:
+        return None, cat
+    per_launch_flops = c["flops"] / c["launches"]
+    per_launch_s = c["ms"] * 1e-3 / c["launches"]
+    achieved = per_launch_flops / per_launch_s / 1e12
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    if prec == "fp32":
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12            # FP32 CUDA-core FMA peak
+        bound, src = "alu", "FP32 CUDA-core peak 152 SM x 128 FMA x 2 x %.0f MHz" % sm_mhz
+    elif prec == "fp64":
+        peak = 1.25
+        bound, src = "alu", "nominal FP64 1.25 TFLOP/s"
+    elif prec == "bf16":
+        peak = pk["bf16_tflops"]
+        bound, src = "tensor", "bf16 %s" % pk_src
+    else:
+        peak = pk["bf16_tflops"] * 1.1 / 2.25
+        bound, src = "tensor", "tf32 = bf16 %s x 1.1/2.25 nominal ratio" % pk_src
+    return {"bound": bound, "kernel": cat, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": src,
+            "flops_per_launch": per_launch_flops, "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6}, cat
+
+
+def run_ours(a, rank, world, local, pg):
+    import torch
+    import paper_1906_02220_gb300 as g
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = workload()
+    D, chi, dbeta, J, K = w["D"], w["chi"], w["dbeta"], w["J"], w["K"]
+    svd_cut = 1e-12 if a.prec == "fp64" else 1e-6
+    A0, B0 = kh_inputs.perturbed_product_state(D, seed=rank, eps=0.05)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ctx = g.Context(D, chi, a.prec, device=dev, stream=stream, svd_cut=svd_cut)
+        At = torch.as_tensor(A0, device=dev)
+        Bt = torch.as_tensor(B0, device=dev)
+        ctx.set_state(At, Bt)
+    Hs = [g.bond_hamiltonian(gm, J, K) for gm in "xyz"]
+    Kxyz = [K, K, K]
+
+    def step():
+        ctx.eefu_trotter_step(J, Kxyz, dbeta, ctm_max_sweeps=a.ctm_sweeps, ctm_min_sweeps=a.ctm_sweeps,
+                              ctm_tol=-1.0, info=False)
+        return ctx.observables(Hs, ctm_max_sweeps=a.obs_sweeps, ctm_min_sweeps=a.obs_sweeps, ctm_tol=-1.0)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = g.launch_count()
+    ctx.profile_start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    last = None
+    for i in range(a.steps):
+        with torch.cuda.stream(stream):
+            flush_l2(flush)
+        ev[i][0].record(stream)
+        last = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    prof = ctx.profile_stop()
+    launches = g.launch_count() - launches0
+    clk = clocks.stop()
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    t_ms = sum(s.elapsed_time(e) for s, e in ev)
+    t_max = max_over_ranks(pg, t_ms)
+    value = a.steps * world / (t_max * 1e-3)
+
+    # end to end through the public API with host buffers
+    ne = a.e2e_steps or a.steps
+    hA = torch.empty((2, 2, D, D, D), dtype=torch.float64, pin_memory=True)
+    hB = torch.empty_like(hA)
+    dA, dB = ctx.get_state()
+    hA.copy_(dA)
+    hB.copy_(dB)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        with torch.cuda.stream(stream):
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+        ctx.set_state(dA, dB)
+        r = step()
+        dA, dB = ctx.get_state()
+        hA.copy_(dA)
+        hB.copy_(dB)
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter() - t0
+    te = max_over_ranks(pg, te)
+    state_bytes = 2 * 4 * D ** 3 * 8
+    e2e = {"value": ne * world / te, "unit": "steps/s", "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": state_bytes + 12 * 8}
+
+    out = None
+    if rank == 0:
+        pk, pk_src = peaks()
+        roof, cat = roofline_for(a.prec, prof, pk, pk_src)
+        err = None
+        if not a.no_fp64_check and a.prec != "fp64":
+            err = fp64_check(a, g, dev, A0, B0, w, Hs, last, a.warmup + a.steps)
+        cpu = None if a.no_cpu_baseline else cpu_baseline(a, w, A0, B0)
+        out = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64"}.get(a.prec, a.prec),
+            "data": "synthetic (seeded perturbed beta=0 product state)",
+            "config": {"workload": WORKLOAD, "D": D, "chi": chi, "J": J, "K": K, "dbeta": dbeta,
+                       "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
+                       "prec": a.prec, "parallelism": "replicas x%d" % world,
+                       "l2": "flushed between timed steps (256 MB write outside the timed events)"},
+            "ctm_sweeps_per_s": value * sweeps_per_step(a),
+            "E_site": last["E_site"] if last else None,
+            "err_vs_fp64": err,
+            "roofline": roof,
+            "profile": prof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+    return out
+
+
+def fp64_check(a, g, dev, A0, B0, w, Hs, last, nsteps):
+    """|E_site(prec) - E_site(fp64)| / max(|E|, 1) after the same steps on the GPU FP64 path."""
+    import torch
+    D, chi = w["D"], w["chi"]
+    ctx = g.Context(D, chi, "fp64", device=dev, svd_cut=1e-12)
+    ctx.set_state(torch.as_tensor(A0, device=dev), torch.as_tensor(B0, device=dev))
+    r = None
+    for _ in range(nsteps):
+        ctx.eefu_trotter_step(w["J"], [w["K"]] * 3, w["dbeta"], ctm_max_sweeps=a.ctm_sweeps,
+                              ctm_min_sweeps=a.ctm_sweeps, ctm_tol=-1.0, info=False)
+        r = ctx.observables(Hs, ctm_max_sweeps=a.obs_sweeps, ctm_min_sweeps=a.obs_sweeps, ctm_tol=-1.0)
+    ctx.close()
+    return {"E_site_fp64": r["E_site"], "rel_err": abs(last["E_site"] - r["E_site"]) / max(abs(r["E_site"]), 1.0),
+            "note": "E/site after the warm-up + timed steps vs the GPU FP64 path on the same start; "
+                    "the timed run's e2e steps are not included"}
+
+
+# ----------------------------------------------------------------- oracle (CPU)
+
+def oracle_layer_seconds(a, w, A0, B0):
+    """Time one gate layer of the oracle (composite, ctm_sweeps CTM sweeps,
+    metric, ALS, gauge) at the bench workload."""
+    from oracle import eefu, model
+    prm = eefu.Params(D=w["D"], chi=w["chi"], J=w["J"], K=w["K"], ctm_tol=-1.0,
+                      ctm_max_sweeps=a.ctm_sweeps, ctm_min_sweeps=a.ctm_sweeps, svd_cut=1e-12)
+    st = eefu.State(A0, B0, prm)
+    g = prm.gate("x", w["dbeta"] / 4)
+    t0 = time.perf_counter()
+    eefu.apply_gate(st, "x", g)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(a, w, A0, B0):
+    t_layer = oracle_layer_seconds(a, w, A0, B0)
+    scale = 5 + 3 * a.obs_sweeps / a.ctm_sweeps
+    step_s = t_layer * scale
+    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one gate layer (%d CTM sweeps + metric + ALS) of the bench workload, %.1f s, scaled x%.2f "
+                      "to a full step (5 layers + 3 x %d observable sweeps)" % (a.ctm_sweeps, t_layer, scale,
+                                                                                 a.obs_sweeps)}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    w = workload()
+    A0, B0 = kh_inputs.perturbed_product_state(w["D"], seed=0, eps=0.05)
+    for _ in range(a.warmup):
+        oracle_layer_seconds(a, w, A0, B0)
+    ts = [oracle_layer_seconds(a, w, A0, B0) for _ in range(a.steps)]
+    scale = 5 + 3 * a.obs_sweeps / a.ctm_sweeps
+    step_s = statistics.mean(ts) * scale
+    value = 1.0 / step_s
+    cpu = {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "per step: one gate layer (%d CTM sweeps + metric + ALS), scaled x%.2f to a full step"
+                     % (a.ctm_sweeps, scale)}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "D": w["D"], "chi": w["chi"], "J": w["J"], "K": w["K"],
+                       "dbeta": w["dbeta"], "ctm_sweeps_per_layer": a.ctm_sweeps,
+                       "obs_sweeps_per_mapping": a.obs_sweeps, "prec": "fp64 (CPU oracle)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank, world, local, pg = dist_setup(a)
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+    else:
+        out = run_ours(a, rank, world, local, pg)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * eefu.h -- C ABI of the GB300 exact-environment full update (eeFU) library.
+ *
+ * Method: Czarnik, Francuz, Dziarmaga, "Tensor network simulation of the
+ * Kitaev-Heisenberg model at finite temperature" (arXiv:1906.02220), Sec. III
+ * with Figs. 3 and 4: an iPEPS purification of exp(-beta H) on the honeycomb
+ * lattice is evolved in imaginary time by Trotter gates (Eq. 6); for each gate
+ * layer on bond direction gamma, every A-B pair joined by a gamma bond is
+ * fused into one composite site so that the lattice becomes a square
+ * (rhombic) lattice, CTMRG on the double-layer norm network of the gated
+ * composite gives the exact environment of the gamma bond, and the bond
+ * A'-B' (dimension 4D) is replaced by A''-B'' (dimension D) minimising the
+ * environment-weighted error.
+ *
+ * Conventions shared by every call
+ *   - All pointers named dev_* are device pointers on the context's device;
+ *     host_* are host pointers.  The caller owns every buffer passed in,
+ *     including the workspace; the library never allocates device memory.
+ *   - All work is issued on the stream given to kh_create.  Calls that return
+ *     host values synchronise that stream before returning.
+ *   - Site tensors are real FP64, row-major A[s][a][x][y][z] (spin, ancilla,
+ *     the three bonds), shape [2][2][D][D][D] (Fig. 3(a)).
+ *   - Composite (rhombic) site tensors are row-major T[p][l][u][r][d] with
+ *     p = (s_A, a_A, s_B, a_B) for composites (p = 16) and bonds of dimension
+ *     D (Fig. 4(b)).  For mapping gamma with (alpha, alpha') the other two
+ *     directions in cyclic order: r = A.alpha, u = A.alpha', l = B.alpha,
+ *     d = B.alpha'.
+ *   - Two-site operators (gates, bond Hamiltonians) are 4x4 row-major on
+ *     (s_A, s_B): row 2*s_A'+s_B', column 2*s_A+s_B; s = 0 is S^z = +1/2.
+ *   - Environments (Fig. 4(c)), clockwise C1 E1 C2 E2 C3 E3 C4 E4:
+ *     C[i][x][y] (chi x chi), x = leg to the previous edge, y = to the next;
+ *     E[i][x][k][b][y] (chi x D x D x chi), k = ket leg, b = bra leg.
+ *     E1 attaches to u, E2 to r, E3 to d, E4 to l.
+ *   - Errors: every call returns a kh_status; nothing aborts or traps.
+ *     On failure kh_last_error() gives a one-line reason.
+ */
+#ifndef EEFU_H
+#define EEFU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KH_OK = 0,
+    KH_EINVAL = 1,      /* bad argument or size beyond a stated limit */
+    KH_ENOMEM = 2,      /* workspace smaller than kh_workspace_bytes() */
+    KH_ENOCONV = 3,     /* CTM or ALS did not converge within its limit */
+    KH_ENUMERIC = 4,    /* NaN/Inf or a breakdown in a solve */
+    KH_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    KH_ECUDA = 6        /* a CUDA runtime call failed */
+} kh_status;
+
+/* Arithmetic of the dense contractions (enlarged corners, half-system
+ * product, absorption, metric).  Masters of C, E, T and everything in the
+ * projector solve, metric solve and normalisation stay FP64 / FP32 as
+ * documented per call. */
+typedef enum {
+    KH_FP64 = 0,        /* CUDA-core FP64 throughout (plain FP64 GPU form)      */
+    KH_FP32 = 1,        /* CUDA-core FP32 contractions, FP32 accumulate         */
+    KH_TF32 = 2,        /* tcgen05 kind::tf32, FP32 accumulate in TMEM          */
+    KH_TF32X3 = 3,      /* tcgen05 kind::tf32 with hi/lo operand split (3 MMAs) */
+    KH_BF16 = 4         /* tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
+} kh_prec;
+
+typedef struct kh_config {
+    int D;                   /* bond dimension, 1 <= D <= 8                           */
+    int chi;                 /* environment dimension, 1 <= chi <= 256                */
+    int prec;                /* kh_prec                                              */
+    int n_slots;             /* environment slots, >= 1 (eeFU uses 0..2, measure 3..5) */
+    int p_max;               /* largest physical dimension of a slot tensor (<= 16)    */
+    int svd_oversample;      /* subspace vectors beyond chi in the projector SVD      */
+    int svd_iters_cold;      /* subspace iterations on a cold start                   */
+    int svd_iters_warm;      /* subspace iterations when warm-started                 */
+    int jacobi_max_sweeps;   /* cap on Jacobi sweeps per small eigenproblem           */
+    double svd_cut;          /* drop singular values below svd_cut * s_1 (S^-1/2)    */
+    double als_tol;          /* ALS stop: |d_old - d_new| / <T'|N|T'> < als_tol       */
+    int als_max_iter;        /* ALS iteration cap                                    */
+    double als_reg;          /* Tikhonov shift reg * tr(R)/dim(R) in the normal eqns  */
+    uint64_t seed;           /* seed of the counter-based start vectors              */
+} kh_config;
+
+typedef struct kh_ctx kh_ctx;   /* opaque; host memory owned by the library */
+
+/* Fills cfg with the defaults used by the tests (D, chi must then be set). */
+void kh_config_defaults(kh_config* cfg);
+
+/* Device workspace the context needs for cfg, in bytes (0 on invalid cfg). */
+size_t kh_workspace_bytes(const kh_config* cfg);
+
+/* Creates a context on the current device.  dev_workspace: caller-owned,
+ * 256-byte aligned, at least kh_workspace_bytes(cfg) bytes, not touched by
+ * the caller while the context lives.  stream: a cudaStream_t (0 = legacy
+ * default stream).  All environments start at the traced boundary; the
+ * state starts at the beta = 0 purification (Sec. III). */
+kh_status kh_create(kh_ctx** ctx, const kh_config* cfg, void* dev_workspace,
+                    size_t workspace_bytes, void* stream);
+void kh_destroy(kh_ctx* ctx);
+const char* kh_last_error(const kh_ctx* ctx);
+
+/* Copy the FP64 site tensors A, B ([2][2][D][D][D] each) in / out. */
+kh_status kh_set_state(kh_ctx* ctx, const double* dev_A, const double* dev_B);
+kh_status kh_get_state(kh_ctx* ctx, double* dev_A, double* dev_B);
+
+/* --- CTMRG (Fig. 4(c), Sec. III) ------------------------------------------ */
+
+/* Load an arbitrary site tensor T[p][D][D][D][D] (FP64, device) into slot;
+ * p <= p_max.  Used for generic square-lattice tensors (e.g. the Ising PEPS). */
+kh_status ctm_set_tensor(kh_ctx* ctx, int slot, const double* dev_T, int p);
+
+/* Build the gamma-composite of the current A, B into slot (Fig. 4(b)),
+ * applying the 4x4 gate host_gate on (s_A, s_B) if non-NULL (the exact
+ * A'-B' pair of Fig. 3(b), its 4D bond contracted inside the composite). */
+kh_status ctm_build_composite(kh_ctx* ctx, int slot, int gamma, const double* host_gate);
+
+/* Reset slot's environment to the traced boundary: every corner e0 e0^T and
+ * every edge E[0][k][b][0] = host_edge[k*D+b] (delta_kb if host_edge is
+ * NULL).  Also marks the projector subspaces cold. */
+kh_status ctm_init(kh_ctx* ctx, int slot, const double* host_edge);
+
+/* Copy the environment (and warm subspaces) of src_slot into dst_slot. */
+kh_status ctm_copy_env(kh_ctx* ctx, int dst_slot, int src_slot);
+
+/* CTM sweeps (left, up, right, down moves) on slot.  Runs until the
+ * normalised top-chi projector spectra of all four moves change by less than
+ * tol between sweeps (at least min_sweeps), or max_sweeps.  tol < 0 runs
+ * exactly max_sweeps with no host synchronisation; then host outputs may be
+ * NULL.  Returns KH_ENOCONV if tol >= 0 and max_sweeps was reached. */
+kh_status ctm_sweep(kh_ctx* ctx, int slot, int max_sweeps, int min_sweeps, double tol,
+                    int* host_sweeps_done, double* host_delta);
+
+/* Spectrum (chi values, descending, zeros past the kept ones) of the last
+ * half-system product M = Q_ul^T Q_dl of move dir (0 left, 1 up, 2 right,
+ * 3 down) and its discarded weight sum_{i>=chi} s_i^2 / sum_i s_i^2. */
+kh_status ctm_projectors(kh_ctx* ctx, int slot, int dir, double* dev_spectrum,
+                         double* host_trunc_err);
+
+/* Copy out the FP64 environment: dev_C [4][chi][chi], dev_E [4][chi][D][D][chi]. */
+kh_status ctm_get_env(kh_ctx* ctx, int slot, double* dev_C, double* dev_E);
+
+/* Environment metric of one site (ring of C1..C4, E1..E4), reshaped to
+ * N[(l,u,r,d) ket][(l,u,r,d) bra] (D^4 x D^4, FP64) and symmetrised. */
+kh_status ctm_metric(kh_ctx* ctx, int slot, double* dev_N);
+
+/* Free energy per site of slot's norm network, kappa = Z11 Z00 / (Z10 Z01). */
+kh_status ctm_kappa(kh_ctx* ctx, int slot, double* host_kappa);
+
+/* <O_i> = Tr(O_i X) / Tr(X), X = T N T^T, for n_ops p x p operators. */
+kh_status ctm_expval(kh_ctx* ctx, int slot, const double* host_ops, int n_ops,
+                     double* host_vals);
+
+/* --- eeFU bond update (Fig. 3(b), Sec. III) -------------------------------- */
+
+/* One gate layer on direction gamma (0 x, 1 y, 2 z): build the gated
+ * composite T' into slot gamma, converge its CTMRG (warm start from that
+ * slot; ctm_* arguments as in ctm_sweep), form the metric N, minimise
+ * <T''-T'|N|T''-T'> by ALS from the truncated SVD of T', fix the balanced
+ * gauge and normalise, and store A'', B'' as the new state.
+ * host_info (may be NULL when ctm_tol < 0): [0] relative cost d/<T'|N|T'>,
+ * [1] CTM sweeps, [2] ALS iterations, [3] largest discarded weight. */
+kh_status eefu_apply_gate(kh_ctx* ctx, int gamma, const double* host_gate,
+                          int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
+                          double* host_info);
+
+/* Observables of the current (un-gated) state: for each gamma a CTMRG of the
+ * composite in slot 3+gamma (warm start from its last run, else from slot
+ * gamma), then <H^gamma> with host_H = three 4x4 bond Hamiltonians (x, y, z,
+ * without bias), <S^a> of both sublattices from the z mapping, and
+ * E/site = 1/2 sum_gamma <H^gamma> - (hA <S^z_A> + hB <S^z_B>)/2.
+ * host_out[12]: E_site, Hx, Hy, Hz, SxA, SyA, SzA, SxB, SyB, SzB, trunc, sweeps. */
+kh_status observables(kh_ctx* ctx, const double* host_H, double hA, double hB,
+                      int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
+                      double* host_out);
+
+/* --- gates (Sec. II Eqs. 2-5, Sec. III Eq. 6); host FP64 -------------------- */
+
+/* H^gamma = J S_A.S_B + K_gamma S_A^gamma S_B^gamma - hA S^z_A - hB S^z_B as a
+ * 4x4 row-major matrix on (s_A, s_B) (pass hA = hB = 0 except for the z
+ * bond, which carries the bias of Eq. 5). */
+kh_status kh_bond_hamiltonian(int gamma, double J, double K_gamma, double hA, double hB,
+                              double* host_H);
+
+/* g = exp(-tau H) for a real symmetric 4x4 H (eigendecomposition by Jacobi). */
+kh_status kh_gate(const double* host_H, double tau, double* host_g);
+
+/* One second-order Trotter step (Eq. 6): gate layers x, y, z, y, x with
+ * exp(-tau H^gamma), tau = dbeta/4, dbeta/4, dbeta/2, dbeta/4, dbeta/4, the
+ * bias (hA, hB) in the z gate, couplings J and K_gamma = K_xyz[gamma].  Each
+ * layer is eefu_apply_gate with the given CTM arguments.  host_info (may be
+ * NULL when ctm_tol < 0): [0] largest relative cost, [1] total CTM sweeps,
+ * [2] total ALS iterations, [3] largest discarded weight. */
+kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* host_K_xyz, double hA, double hB,
+                            double dbeta, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
+                            double* host_info);
+
+/* --- instrumentation (no counterpart in the paper; used by the benchmark) -- */
+
+/* Number of kernels this library has launched since it was loaded. */
+unsigned long long kh_launch_count(void);
+
+/* enable != 0: reset and start CUDA-event timing of two kernel categories
+ * on the context's stream; enable == 0: synchronise, stop, and write
+ * host_out[6] = {launches, milliseconds, algorithmic flops} for category 0
+ * (half-system product Mt = Q_{s+3} Q_s, 2 n^3 flops, n = chi D^2) and
+ * category 1 (two-layer site contractions, 4 nb p D^6 flops per call). */
+kh_status kh_profile(kh_ctx* ctx, int enable, double* host_out);
+
+/* Library build information (static string). */
+const char* kh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EEFU_H */

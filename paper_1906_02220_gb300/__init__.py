@@ -1,0 +1,304 @@
+"""Python binding of the eeFU GB300 library (argument marshalling only).
+
+Every call forwards to the C ABI declared in include/eefu.h; all arithmetic
+of the method runs in the CUDA library.  PyTorch supplies device memory (the
+workspace and the caller's tensors) and the stream.  Importing this package
+fails loudly if the compiled library is missing: there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeefu_gb300.so")
+
+KH_OK, KH_EINVAL, KH_ENOMEM, KH_ENOCONV, KH_ENUMERIC, KH_ETIMEOUT, KH_ECUDA = range(7)
+STATUS_NAMES = ["KH_OK", "KH_EINVAL", "KH_ENOMEM", "KH_ENOCONV", "KH_ENUMERIC", "KH_ETIMEOUT", "KH_ECUDA"]
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4}
+GAMMA = {"x": 0, "y": 1, "z": 2}
+
+# every entry point of include/eefu.h (checked by the CPU symbol test)
+ABI_FUNCTIONS = [
+    "kh_config_defaults", "kh_workspace_bytes", "kh_create", "kh_destroy", "kh_last_error",
+    "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
+    "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
+    "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
+    "eefu_trotter_step", "kh_launch_count", "kh_profile",
+]
+
+
+class KhConfig(ctypes.Structure):
+    _fields_ = [
+        ("D", ctypes.c_int), ("chi", ctypes.c_int), ("prec", ctypes.c_int), ("n_slots", ctypes.c_int),
+        ("p_max", ctypes.c_int), ("svd_oversample", ctypes.c_int), ("svd_iters_cold", ctypes.c_int),
+        ("svd_iters_warm", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int), ("svd_cut", ctypes.c_double),
+        ("als_tol", ctypes.c_double), ("als_max_iter", ctypes.c_int), ("als_reg", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class KhError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("eeFU CUDA library not built (%s); run paper_1906_02220_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    cfgp = ctypes.POINTER(KhConfig)
+    sig = {
+        "kh_config_defaults": (None, [cfgp]),
+        "kh_workspace_bytes": (S, [cfgp]),
+        "kh_create": (I, [ctypes.POINTER(P), cfgp, P, S, P]),
+        "kh_destroy": (None, [P]),
+        "kh_last_error": (ctypes.c_char_p, [P]),
+        "kh_version": (ctypes.c_char_p, []),
+        "kh_set_state": (I, [P, P, P]),
+        "kh_get_state": (I, [P, P, P]),
+        "ctm_set_tensor": (I, [P, I, P, I]),
+        "ctm_build_composite": (I, [P, I, I, dp]),
+        "ctm_init": (I, [P, I, dp]),
+        "ctm_copy_env": (I, [P, I, I]),
+        "ctm_sweep": (I, [P, I, I, I, D, ip, dp]),
+        "ctm_projectors": (I, [P, I, I, P, dp]),
+        "ctm_get_env": (I, [P, I, P, P]),
+        "ctm_metric": (I, [P, I, P]),
+        "ctm_kappa": (I, [P, I, dp]),
+        "ctm_expval": (I, [P, I, dp, I, dp]),
+        "eefu_apply_gate": (I, [P, I, dp, I, I, D, dp]),
+        "observables": (I, [P, dp, D, D, I, I, D, dp]),
+        "kh_bond_hamiltonian": (I, [I, D, D, D, D, dp]),
+        "kh_gate": (I, [dp, D, dp]),
+        "eefu_trotter_step": (I, [P, D, dp, D, D, D, I, I, D, dp]),
+        "kh_launch_count": (ctypes.c_ulonglong, []),
+        "kh_profile": (I, [P, I, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def launch_count():
+    return int(lib().kh_launch_count())
+
+
+def default_config(D, chi, prec="fp64", **kw):
+    c = KhConfig()
+    lib().kh_config_defaults(ctypes.byref(c))
+    c.D, c.chi, c.prec = D, chi, PREC[prec] if isinstance(prec, str) else int(prec)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def bond_hamiltonian(gamma, J, K_gamma, hA=0.0, hB=0.0):
+    """4x4 H^gamma built by the library (host FP64)."""
+    H = np.zeros(16)
+    h, hp = _dptr(H)
+    st = lib().kh_bond_hamiltonian(GAMMA.get(gamma, gamma), J, K_gamma, hA, hB, hp)
+    if st != KH_OK:
+        raise KhError(st, "kh_bond_hamiltonian")
+    return h.reshape(4, 4)
+
+
+def gate(H, tau):
+    """exp(-tau H) built by the library (host FP64)."""
+    Hc, hp = _dptr(np.asarray(H).reshape(16))
+    g = np.zeros(16)
+    gg, gp = _dptr(g)
+    st = lib().kh_gate(hp, tau, gp)
+    if st != KH_OK:
+        raise KhError(st, "kh_gate")
+    return gg.reshape(4, 4)
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _tptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One eeFU context: owns a device workspace (torch uint8 tensor) and a
+    stream; wraps every ABI call of include/eefu.h."""
+
+    def __init__(self, D, chi, prec="fp64", device="cuda:0", stream=None, **cfg_kw):
+        import torch
+        self.torch = torch
+        self.cfg = default_config(D, chi, prec, **cfg_kw)
+        self.D, self.chi = D, chi
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = lib().kh_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise KhError(KH_EINVAL, "invalid configuration")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self._ctx = ctypes.c_void_p()
+        st = lib().kh_create(ctypes.byref(self._ctx), ctypes.byref(self.cfg), ctypes.c_void_p(aligned),
+                             nbytes, ctypes.c_void_p(self.stream.cuda_stream))
+        if st != KH_OK:
+            raise KhError(st, "kh_create failed")
+
+    def _check(self, st):
+        if st != KH_OK:
+            raise KhError(st, lib().kh_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().kh_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- instrumentation
+    def profile_start(self):
+        self._check(lib().kh_profile(self._ctx, 1, None))
+
+    def profile_stop(self):
+        out = np.zeros(6)
+        o, op = _dptr(out)
+        self._check(lib().kh_profile(self._ctx, 0, op))
+        names = ["half_system_product", "site_layer"]
+        return {names[k]: dict(launches=int(o[3 * k]), ms=o[3 * k + 1], flops=o[3 * k + 2]) for k in range(2)}
+
+    # ---- state
+    def set_state(self, A, B):
+        self._check(lib().kh_set_state(self._ctx, _tptr(A), _tptr(B)))
+
+    def get_state(self):
+        t = self.torch
+        A = t.empty((2, 2, self.D, self.D, self.D), dtype=t.float64, device=self.device)
+        B = t.empty_like(A)
+        self._check(lib().kh_get_state(self._ctx, _tptr(A), _tptr(B)))
+        return A, B
+
+    # ---- CTMRG
+    def ctm_set_tensor(self, slot, T):
+        self._check(lib().ctm_set_tensor(self._ctx, slot, _tptr(T), int(T.shape[0])))
+
+    def ctm_build_composite(self, slot, gamma, gate=None):
+        if gate is None:
+            self._check(lib().ctm_build_composite(self._ctx, slot, GAMMA.get(gamma, gamma), None))
+        else:
+            g, gp = _dptr(gate)
+            self._check(lib().ctm_build_composite(self._ctx, slot, GAMMA.get(gamma, gamma), gp))
+
+    def ctm_init(self, slot, edge=None):
+        if edge is None:
+            self._check(lib().ctm_init(self._ctx, slot, None))
+        else:
+            e, ep = _dptr(edge)
+            self._check(lib().ctm_init(self._ctx, slot, ep))
+
+    def ctm_copy_env(self, dst, src):
+        self._check(lib().ctm_copy_env(self._ctx, dst, src))
+
+    def ctm_sweep(self, slot, max_sweeps, min_sweeps=1, tol=-1.0, allow_noconv=False):
+        done = ctypes.c_int(0)
+        delta = ctypes.c_double(0.0)
+        st = lib().ctm_sweep(self._ctx, slot, max_sweeps, min_sweeps, tol, ctypes.byref(done), ctypes.byref(delta))
+        if not (allow_noconv and st == KH_ENOCONV):
+            self._check(st)
+        return done.value, delta.value
+
+    def ctm_projectors(self, slot, direction):
+        t = self.torch
+        spec = t.empty(self.chi, dtype=t.float64, device=self.device)
+        tr = ctypes.c_double(0.0)
+        self._check(lib().ctm_projectors(self._ctx, slot, direction, _tptr(spec), ctypes.byref(tr)))
+        return spec, tr.value
+
+    def ctm_get_env(self, slot):
+        t = self.torch
+        C = t.empty((4, self.chi, self.chi), dtype=t.float64, device=self.device)
+        E = t.empty((4, self.chi, self.D, self.D, self.chi), dtype=t.float64, device=self.device)
+        self._check(lib().ctm_get_env(self._ctx, slot, _tptr(C), _tptr(E)))
+        return C, E
+
+    def ctm_metric(self, slot):
+        t = self.torch
+        n = self.D ** 4
+        N = t.empty((n, n), dtype=t.float64, device=self.device)
+        self._check(lib().ctm_metric(self._ctx, slot, _tptr(N)))
+        return N
+
+    def ctm_kappa(self, slot):
+        k = ctypes.c_double(0.0)
+        self._check(lib().ctm_kappa(self._ctx, slot, ctypes.byref(k)))
+        return k.value
+
+    def ctm_expval(self, slot, ops):
+        ops = np.ascontiguousarray(ops, dtype=np.float64)
+        if ops.ndim == 2:
+            ops = ops[None]
+        o, op = _dptr(ops)
+        vals = np.zeros(ops.shape[0])
+        v, vp = _dptr(vals)
+        self._check(lib().ctm_expval(self._ctx, slot, op, ops.shape[0], vp))
+        return v
+
+    # ---- eeFU
+    def eefu_apply_gate(self, gamma, gate, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12, info=True):
+        g, gp = _dptr(gate)
+        if info:
+            out = np.zeros(4)
+            o, op = _dptr(out)
+            self._check(lib().eefu_apply_gate(self._ctx, GAMMA.get(gamma, gamma), gp, ctm_max_sweeps,
+                                              ctm_min_sweeps, ctm_tol, op))
+            return dict(rel_cost=o[0], ctm_sweeps=int(o[1]), als_iters=int(o[2]), trunc=o[3])
+        self._check(lib().eefu_apply_gate(self._ctx, GAMMA.get(gamma, gamma), gp, ctm_max_sweeps, ctm_min_sweeps,
+                                          ctm_tol, None))
+        return None
+
+    def eefu_trotter_step(self, J, K_xyz, dbeta, hA=0.0, hB=0.0, ctm_max_sweeps=100, ctm_min_sweeps=1,
+                          ctm_tol=1e-12, info=True):
+        k, kp = _dptr(np.asarray(K_xyz, dtype=np.float64))
+        if info:
+            out = np.zeros(4)
+            o, op = _dptr(out)
+            self._check(lib().eefu_trotter_step(self._ctx, J, kp, hA, hB, dbeta, ctm_max_sweeps, ctm_min_sweeps,
+                                                ctm_tol, op))
+            return dict(rel_cost=o[0], ctm_sweeps=int(o[1]), als_iters=int(o[2]), trunc=o[3])
+        self._check(lib().eefu_trotter_step(self._ctx, J, kp, hA, hB, dbeta, ctm_max_sweeps, ctm_min_sweeps,
+                                            ctm_tol, None))
+        return None
+
+    def observables(self, H_xyz, hA=0.0, hB=0.0, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12):
+        H = np.ascontiguousarray(np.stack([np.asarray(h, dtype=np.float64) for h in H_xyz]))
+        h, hp = _dptr(H)
+        out = np.zeros(12)
+        o, op = _dptr(out)
+        self._check(lib().observables(self._ctx, hp, hA, hB, ctm_max_sweeps, ctm_min_sweeps, ctm_tol, op))
+        keys = ["E_site", "Hx", "Hy", "Hz", "Ax", "Ay", "Az", "Bx", "By", "Bz", "trunc", "sweeps"]
+        return dict(zip(keys, o.tolist()))

@@ -1,0 +1,341 @@
+// extern "C" boundary of the eeFU library (declarations and contracts in
+// include/eefu.h).  Every entry point converts internal errors into a
+// kh_status and a one-line message; nothing throws across the boundary.
+#include <cmath>
+
+#include "engine.cuh"
+
+namespace kh {
+unsigned long long g_launches = 0;
+}
+
+struct kh_ctx {
+    kh::EngineBase* eng = nullptr;
+    std::string err;
+};
+
+namespace {
+
+template <typename F>
+kh_status guard(kh_ctx* ctx, F&& f) {
+    if (!ctx || !ctx->eng) return KH_EINVAL;
+    try {
+        f();
+        ctx->err.clear();
+        return KH_OK;
+    } catch (const kh::Error& e) {
+        ctx->err = e.msg;
+        return e.st;
+    } catch (const std::exception& e) {
+        ctx->err = e.what();
+        return KH_EINVAL;
+    }
+}
+
+bool slot_ok(kh_ctx* ctx, int slot) { return slot >= 0 && slot < ctx->eng->dm.nslots; }
+
+// Cyclic Jacobi for a symmetric 4x4 (host, FP64): A -> diag, V eigenvectors.
+void jacobi4(double A[16], double V[16]) {
+    for (int i = 0; i < 16; ++i) V[i] = (i / 4 == i % 4) ? 1.0 : 0.0;
+    for (int sw = 0; sw < 50; ++sw) {
+        double off = 0.0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j)
+                if (i != j) off += A[i * 4 + j] * A[i * 4 + j];
+        if (off < 1e-60) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                double apq = A[p * 4 + q];
+                if (apq == 0.0) continue;
+                double tau = (A[q * 4 + q] - A[p * 4 + p]) / (2.0 * apq);
+                double t = (tau >= 0.0) ? 1.0 / (tau + std::sqrt(1.0 + tau * tau))
+                                        : -1.0 / (-tau + std::sqrt(1.0 + tau * tau));
+                double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < 4; ++k) {
+                    double akp = A[k * 4 + p], akq = A[k * 4 + q];
+                    A[k * 4 + p] = c * akp - s * akq;
+                    A[k * 4 + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    double apk = A[p * 4 + k], aqk = A[q * 4 + k];
+                    A[p * 4 + k] = c * apk - s * aqk;
+                    A[q * 4 + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    double vkp = V[k * 4 + p], vkq = V[k * 4 + q];
+                    V[k * 4 + p] = c * vkp - s * vkq;
+                    V[k * 4 + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+void bond_h(int gamma, double J, double Kg, double hA, double hB, double H[16]) {
+    // sigma^a (x) sigma^a on (sA,sB), row 2*sA'+sB', col 2*sA+sB
+    static const double XX[16] = {0, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 1, 0, 0, 0};
+    static const double YY[16] = {0, 0, 0, -1, 0, 0, 1, 0, 0, 1, 0, 0, -1, 0, 0, 0};
+    static const double ZZ[16] = {1, 0, 0, 0, 0, -1, 0, 0, 0, 0, -1, 0, 0, 0, 0, 1};
+    const double* G[3] = {XX, YY, ZZ};
+    for (int i = 0; i < 16; ++i) H[i] = 0.25 * J * (XX[i] + YY[i] + ZZ[i]) + 0.25 * Kg * G[gamma][i];
+    // -hA S^z_A - hB S^z_B: S^z (x) 1 = diag(1,1,-1,-1)/2, 1 (x) S^z = diag(1,-1,1,-1)/2
+    const double zA[4] = {0.5, 0.5, -0.5, -0.5}, zB[4] = {0.5, -0.5, 0.5, -0.5};
+    for (int i = 0; i < 4; ++i) H[i * 4 + i] -= hA * zA[i] + hB * zB[i];
+}
+
+void gate_from_h(const double* Hin, double tau, double g[16]) {
+    double A[16], V[16];
+    for (int i = 0; i < 16; ++i) A[i] = 0.5 * (Hin[i] + Hin[(i % 4) * 4 + i / 4]);
+    jacobi4(A, V);
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k) s += V[i * 4 + k] * std::exp(-tau * A[k * 4 + k]) * V[j * 4 + k];
+            g[i * 4 + j] = s;
+        }
+}
+
+}  // namespace
+
+extern "C" {
+
+void kh_config_defaults(kh_config* c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->D = 2;
+    c->chi = 16;
+    c->prec = KH_FP64;
+    c->n_slots = 6;
+    c->p_max = 16;
+    c->svd_oversample = 16;
+    c->svd_iters_cold = 4;
+    c->svd_iters_warm = 1;
+    c->jacobi_max_sweeps = 40;
+    c->svd_cut = 1e-12;
+    c->als_tol = 1e-12;
+    c->als_max_iter = 50;
+    c->als_reg = 1e-12;
+    c->seed = 0x5eed;
+}
+
+size_t kh_workspace_bytes(const kh_config* c) {
+    if (!c) return 0;
+    try {
+        kh::validate(*c);
+        if (c->prec == KH_FP64) return kh::Engine<double>::bytes_needed(*c);
+        return kh::Engine<float>::bytes_needed(*c);
+    } catch (...) {
+        return 0;
+    }
+}
+
+kh_status kh_create(kh_ctx** out, const kh_config* c, void* ws, size_t bytes, void* stream) {
+    if (!out || !c) return KH_EINVAL;
+    *out = nullptr;
+    kh_ctx* ctx = new kh_ctx();
+    try {
+        kh::validate(*c);
+        if ((uintptr_t)ws % 256 != 0) kh::fail(KH_EINVAL, "workspace must be 256-byte aligned");
+        size_t need = kh_workspace_bytes(c);
+        if (bytes < need) kh::fail(KH_ENOMEM, "workspace smaller than kh_workspace_bytes()");
+        if (c->prec != KH_FP64 && c->prec != KH_FP32)
+            kh::fail(KH_EINVAL, "precision not built in this library version");
+        cudaStream_t st = (cudaStream_t)stream;
+        if (c->prec == KH_FP64) ctx->eng = new kh::Engine<double>(*c, ws, bytes, st);
+        else ctx->eng = new kh::Engine<float>(*c, ws, bytes, st);
+        KH_CUDA(cudaStreamSynchronize(st));
+    } catch (const kh::Error& e) {
+        delete ctx->eng;
+        delete ctx;
+        return e.st;
+    }
+    *out = ctx;
+    return KH_OK;
+}
+
+void kh_destroy(kh_ctx* ctx) {
+    if (!ctx) return;
+    delete ctx->eng;
+    delete ctx;
+}
+
+const char* kh_last_error(const kh_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+const char* kh_version(void) { return "eefu-gb300 0.1 (sm_103a)"; }
+
+kh_status kh_set_state(kh_ctx* ctx, const double* A, const double* B) {
+    return guard(ctx, [&] {
+        if (!A || !B) kh::fail(KH_EINVAL, "null tensor");
+        ctx->eng->set_state(A, B);
+    });
+}
+
+kh_status kh_get_state(kh_ctx* ctx, double* A, double* B) {
+    return guard(ctx, [&] {
+        if (!A || !B) kh::fail(KH_EINVAL, "null tensor");
+        ctx->eng->get_state(A, B);
+    });
+}
+
+kh_status ctm_set_tensor(kh_ctx* ctx, int slot, const double* T, int p) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !T) kh::fail(KH_EINVAL, "bad slot or tensor");
+        ctx->eng->set_tensor(slot, T, p);
+    });
+}
+
+kh_status ctm_build_composite(kh_ctx* ctx, int slot, int gamma, const double* gate) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot)) kh::fail(KH_EINVAL, "bad slot");
+        ctx->eng->build_composite(slot, gamma, gate);
+    });
+}
+
+kh_status ctm_init(kh_ctx* ctx, int slot, const double* edge) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot)) kh::fail(KH_EINVAL, "bad slot");
+        ctx->eng->init_env(slot, edge);
+    });
+}
+
+kh_status ctm_copy_env(kh_ctx* ctx, int dst, int src) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, dst) || !slot_ok(ctx, src)) kh::fail(KH_EINVAL, "bad slot");
+        ctx->eng->copy_env(dst, src);
+    });
+}
+
+kh_status ctm_sweep(kh_ctx* ctx, int slot, int max_sweeps, int min_sweeps, double tol, int* done,
+                    double* delta) {
+    kh_status s = KH_OK;
+    int n = 0;
+    double dl = 0.0;
+    s = guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || max_sweeps < 1) kh::fail(KH_EINVAL, "bad slot or sweep count");
+        n = ctx->eng->sweep(slot, max_sweeps, min_sweeps, tol, &dl);
+    });
+    if (s != KH_OK) return s;
+    if (done) *done = n;
+    if (delta) *delta = dl;
+    if (tol >= 0.0 && !(dl < tol)) {
+        ctx->err = "CTM did not reach the tolerance within max_sweeps";
+        return KH_ENOCONV;
+    }
+    return KH_OK;
+}
+
+kh_status ctm_projectors(kh_ctx* ctx, int slot, int dir, double* spec, double* trunc) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || dir < 0 || dir > 3) kh::fail(KH_EINVAL, "bad slot or dir");
+        ctx->eng->projectors_out(slot, dir, spec, trunc);
+    });
+}
+
+kh_status ctm_get_env(kh_ctx* ctx, int slot, double* C, double* E) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot)) kh::fail(KH_EINVAL, "bad slot");
+        ctx->eng->get_env(slot, C, E);
+    });
+}
+
+kh_status ctm_metric(kh_ctx* ctx, int slot, double* N) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !N) kh::fail(KH_EINVAL, "bad slot");
+        ctx->eng->metric(slot, N);
+    });
+}
+
+kh_status ctm_kappa(kh_ctx* ctx, int slot, double* kappa) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !kappa) kh::fail(KH_EINVAL, "bad slot");
+        *kappa = ctx->eng->kappa(slot);
+    });
+}
+
+kh_status ctm_expval(kh_ctx* ctx, int slot, const double* ops, int n_ops, double* vals) {
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !ops || !vals) kh::fail(KH_EINVAL, "bad arguments");
+        ctx->eng->expval(slot, ops, n_ops, vals);
+    });
+}
+
+kh_status eefu_apply_gate(kh_ctx* ctx, int gamma, const double* gate, int mx, int mn, double tol,
+                          double* info) {
+    return guard(ctx, [&] {
+        if (!gate || mx < 1) kh::fail(KH_EINVAL, "bad gate or sweep count");
+        ctx->eng->apply_gate(gamma, gate, mx, mn, tol, info);
+    });
+}
+
+kh_status observables(kh_ctx* ctx, const double* H, double hA, double hB, int mx, int mn, double tol,
+                      double* out) {
+    return guard(ctx, [&] {
+        if (!H || !out || mx < 1) kh::fail(KH_EINVAL, "bad arguments");
+        ctx->eng->observables(H, hA, hB, mx, mn, tol, out);
+    });
+}
+
+kh_status kh_bond_hamiltonian(int gamma, double J, double Kg, double hA, double hB, double* H) {
+    if (gamma < 0 || gamma > 2 || !H) return KH_EINVAL;
+    bond_h(gamma, J, Kg, hA, hB, H);
+    return KH_OK;
+}
+
+kh_status kh_gate(const double* H, double tau, double* g) {
+    if (!H || !g) return KH_EINVAL;
+    gate_from_h(H, tau, g);
+    return KH_OK;
+}
+
+kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta,
+                            int mx, int mn, double tol, double* info) {
+    return guard(ctx, [&] {
+        if (!Kxyz || mx < 1) kh::fail(KH_EINVAL, "bad arguments");
+        static const int order[5] = {0, 1, 2, 1, 0};
+        const double taus[5] = {dbeta / 4, dbeta / 4, dbeta / 2, dbeta / 4, dbeta / 4};
+        double worst = 0.0, sweeps = 0.0, iters = 0.0, tr = 0.0;
+        for (int l = 0; l < 5; ++l) {
+            int g = order[l];
+            double H[16], G[16], inf[4];
+            bond_h(g, J, Kxyz[g], g == 2 ? hA : 0.0, g == 2 ? hB : 0.0, H);
+            gate_from_h(H, taus[l], G);
+            ctx->eng->apply_gate(g, G, mx, mn, tol, info ? inf : nullptr);
+            if (info) {
+                worst = std::fmax(worst, inf[0]);
+                sweeps += inf[1];
+                iters += inf[2];
+                tr = std::fmax(tr, inf[3]);
+            }
+        }
+        if (info) { info[0] = worst; info[1] = sweeps; info[2] = iters; info[3] = tr; }
+    });
+}
+
+unsigned long long kh_launch_count(void) { return kh::g_launches; }
+
+kh_status kh_profile(kh_ctx* ctx, int enable, double* out) {
+    return guard(ctx, [&] {
+        kh::EngineBase* e = ctx->eng;
+        if (enable) {
+            for (auto& c : e->prof) { c.used = 0; c.flops = 0.0; }
+            e->prof_on = true;
+            return;
+        }
+        KH_CUDA(cudaStreamSynchronize(e->st));
+        e->prof_on = false;
+        for (int k = 0; k < 2; ++k) {
+            double ms = 0.0;
+            for (int i = 0; i < e->prof[k].used; ++i) {
+                float t = 0.f;
+                KH_CUDA(cudaEventElapsedTime(&t, e->prof[k].a[i], e->prof[k].b[i]));
+                ms += t;
+            }
+            if (out) {
+                out[3 * k + 0] = e->prof[k].used;
+                out[3 * k + 1] = ms;
+                out[3 * k + 2] = e->prof[k].flops;
+            }
+        }
+    });
+}
+
+}  // extern "C"

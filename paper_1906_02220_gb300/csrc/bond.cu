@@ -1,0 +1,666 @@
+// Gate application and environment-weighted bond update, Fig. 3(b) and Sec. III
+// of arXiv:1906.02220, plus the observables of Sec. V (energy per site,
+// sublattice magnetisations).
+//
+// Composite for mapping gamma (Fig. 4(b)): with (alpha, alpha') the other two
+// bond directions in cyclic order, T'[p'; l,u,r,d] =
+//   sum_{sA,sB} g[(sA',sB'),(sA,sB)] sum_k A[sA,aA; u=alpha', r=alpha, k=gamma]
+//                                         B[sB,aB; d=alpha', l=alpha, k=gamma].
+// Bond update: minimise d = <T''-T'|N|T''-T'> over A''[sA,aA,u,r,k],
+// B''[sB,aB,d,l,k] (k < D) with the CTMRG metric N; start from the truncated
+// SVD of T' as a (4D^2)x(4D^2) matrix; alternate the two quadratic
+// subproblems (R + reg tr(R)/m I) X = S (FP64 Cholesky); balanced gauge from
+// the Gram matrices of A'' and B''.
+#include "engine.cuh"
+
+namespace kh {
+
+struct Mat4 { double v[16]; };
+struct Mat4x3 { double v[48]; };
+
+// ------------------------------------------------------------------ composite
+
+__device__ __forceinline__ void bond_strides(int gamma, int D, int& s_u, int& s_r, int& s_k) {
+    // site tensor A[s][a][x][y][z]: bond strides x: D^2, y: D, z: 1
+    int str[3] = {D * D, D, 1};
+    int al = (gamma + 1) % 3, alp = (gamma + 2) % 3;
+    s_u = str[alp];
+    s_r = str[al];
+    s_k = str[gamma];
+}
+
+__global__ void composite_kernel(const double* __restrict__ A, const double* __restrict__ B, int D, int gamma,
+                                 Mat4 g, int has_gate, double* __restrict__ T) {
+    const int D4 = D * D * D * D, D3 = D * D * D;
+    int tot = 16 * D4;
+    int su, sr, sk;
+    bond_strides(gamma, D, su, sr, sk);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+        int p = i / D4, leg = i % D4;
+        int l = leg / (D * D * D), u = (leg / (D * D)) % D, r = (leg / D) % D, d = leg % D;
+        int sAo = (p >> 3) & 1, aA = (p >> 2) & 1, sBo = (p >> 1) & 1, aB = p & 1;
+        double acc = 0.0;
+        for (int sA = 0; sA < 2; ++sA)
+            for (int sB = 0; sB < 2; ++sB) {
+                double gv = has_gate ? g.v[(sAo * 2 + sBo) * 4 + sA * 2 + sB] : ((sA == sAo && sB == sBo) ? 1.0 : 0.0);
+                if (gv == 0.0) continue;
+                const double* a = A + (sA * 2 + aA) * D3 + u * su + r * sr;
+                const double* b = B + (sB * 2 + aB) * D3 + d * su + l * sr;
+                double s = 0.0;
+                for (int k = 0; k < D; ++k) s += a[k * sk] * b[k * sk];
+                acc += gv * s;
+            }
+        T[i] = acc;
+    }
+}
+
+// Rotated operand layouts for frames f = 0..3 (counter-clockwise quarter
+// turns: new (l,u,r,d) = old (u,r,d,l)):
+//   Tcor_f[l][u][p][r][d], Tedg_f[l][d][p][u][r]  (frame-f legs).
+template <typename T>
+__global__ void derived_kernel(const double* __restrict__ Tm, int p, int D, int pmax, T* Tcor, T* Tedg) {
+    const int D4 = D * D * D * D;
+    int tot = 4 * p * D4;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += gridDim.x * blockDim.x) {
+        int f = i / (p * D4), rem = i % (p * D4);
+        int pp = rem / D4, leg = rem % D4;
+        int L = leg / (D * D * D), Uu = (leg / (D * D)) % D, Rr = (leg / D) % D, Dd = leg % D;
+        // frame-f legs (L,U,R,D) -> original legs: undo f rotations
+        int l = L, u = Uu, r = Rr, d = Dd;
+        for (int t = 0; t < f; ++t) {
+            int ol = d, ou = l, orr = u, od = r;   // old legs of one rotation
+            l = ol; u = ou; r = orr; d = od;
+        }
+        double v = Tm[pp * D4 + ((l * D + u) * D + r) * D + d];
+        // Tcor_f[L][U][p][R][D]
+        long long ic = (long long)f * pmax * D4 + (((long long)(L * D + Uu) * p + pp) * D + Rr) * D + Dd;
+        // Tedg_f[L][D][p][U][R]
+        long long ie = (long long)f * pmax * D4 + (((long long)(L * D + Dd) * p + pp) * D + Uu) * D + Rr;
+        Tcor[ic] = (T)v;
+        Tedg[ie] = (T)v;
+    }
+}
+
+template <typename T>
+void Engine<T>::build_derived(Slot<T>& sl) {
+    int tot = 4 * sl.p * dm.D4;
+    derived_kernel<T><<<grid_for(tot), 256, 0, st>>>(sl.Ts, sl.p, dm.D, dm.pmax, sl.Tcor, sl.Tedg);
+    KH_LAUNCHED();
+}
+
+template <typename T>
+void Engine<T>::set_tensor(int slot, const double* Tin, int p) {
+    if (p < 1 || p > dm.pmax) fail(KH_EINVAL, "p out of range");
+    Slot<T>& sl = slots[slot];
+    KH_CUDA(cudaMemcpyAsync(sl.Ts, Tin, sizeof(double) * p * dm.D4, cudaMemcpyDeviceToDevice, st));
+    sl.p = p;
+    build_derived(sl);
+}
+
+template <typename T>
+void Engine<T>::build_composite(int slot, int gamma, const double* gate) {
+    if (gamma < 0 || gamma > 2) fail(KH_EINVAL, "gamma must be 0, 1 or 2");
+    if (dm.pmax < 16) fail(KH_EINVAL, "composites need p_max = 16");
+    Slot<T>& sl = slots[slot];
+    Mat4 g;
+    for (int i = 0; i < 16; ++i) g.v[i] = gate ? gate[i] : 0.0;
+    composite_kernel<<<grid_for(16 * dm.D4), 256, 0, st>>>(A, B, dm.D, gamma, g, gate != nullptr, sl.Ts);
+    KH_LAUNCHED();
+    sl.p = 16;
+    build_derived(sl);
+}
+
+template <typename T>
+void Engine<T>::set_state(const double* Ain, const double* Bin) {
+    const size_t b = sizeof(double) * 4 * dm.D * dm.D * dm.D;
+    KH_CUDA(cudaMemcpyAsync(A, Ain, b, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaMemcpyAsync(B, Bin, b, cudaMemcpyDeviceToDevice, st));
+}
+
+template <typename T>
+void Engine<T>::get_state(double* Aout, double* Bout) {
+    const size_t b = sizeof(double) * 4 * dm.D * dm.D * dm.D;
+    KH_CUDA(cudaMemcpyAsync(Aout, A, b, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaMemcpyAsync(Bout, B, b, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ ALS kernels
+
+// Leg positions in the composite row index (l,u,r,d): A owns (u,r), B owns (d,l).
+// side 0 (solve A): own (o1,o2) = (u,r), other (t1,t2) = (d,l) = layout of B''.
+// side 1 (solve B): own (o1,o2) = (d,l), other (t1,t2) = (u,r) = layout of A''.
+__device__ __forceinline__ int row_index(int side, int o1, int o2, int t1, int t2, int D) {
+    int l, u, r, d;
+    if (side == 0) { u = o1; r = o2; d = t1; l = t2; }
+    else { d = o1; l = o2; u = t1; r = t2; }
+    return ((l * D + u) * D + r) * D + d;
+}
+
+// X[(o1,o2)][j][(ph,k)] = sum_{t1,t2} N[row(o,t)][j] Oth[ph][t1][t2][k]
+__global__ void als_x_kernel(const double* __restrict__ N, const double* __restrict__ Oth, int D, int side,
+                             double* __restrict__ X) {
+    const int D4 = D * D * D * D, d2 = D * D;
+    long long tot = (long long)d2 * D4 * 4 * D;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int k = (int)(i % D);
+        int ph = (int)((i / D) % 4);
+        int j = (int)((i / (4 * D)) % D4);
+        int o = (int)(i / ((long long)4 * D * D4));
+        int o1 = o / D, o2 = o % D;
+        double s = 0.0;
+        for (int t1 = 0; t1 < D; ++t1)
+            for (int t2 = 0; t2 < D; ++t2)
+                s += N[(long long)row_index(side, o1, o2, t1, t2, D) * D4 + j] * Oth[((ph * D + t1) * D + t2) * D + k];
+        X[i] = s;
+    }
+}
+
+// R[(o1,o2,k)][(o1',o2',k')] = sum_{t1',t2',ph} X[(o1,o2)][row(o',t')][(ph,k)] Oth[ph][t1'][t2'][k']
+// S[(o1,o2,k)][q]           = sum_{j,ph} X[(o1,o2)][j][(ph,k)] Tp[pidx(q,ph)][j]
+__global__ void als_rs_kernel(const double* __restrict__ X, const double* __restrict__ Oth,
+                              const double* __restrict__ Tp, int D, int side, double* __restrict__ R,
+                              double* __restrict__ S) {
+    const int D4 = D * D * D * D, m = D * D * D;
+    long long totR = (long long)m * m, tot = totR + 4LL * m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < totR) {
+            int a = (int)(i / m), b = (int)(i % m);
+            int o1 = a / (D * D), o2 = (a / D) % D, k = a % D;
+            int q1 = b / (D * D), q2 = (b / D) % D, kp = b % D;
+            const double* x = X + (long long)(o1 * D + o2) * D4 * 4 * D;
+            double s = 0.0;
+            for (int t1 = 0; t1 < D; ++t1)
+                for (int t2 = 0; t2 < D; ++t2) {
+                    int j = row_index(side, q1, q2, t1, t2, D);
+                    for (int ph = 0; ph < 4; ++ph)
+                        s += x[((long long)j * 4 + ph) * D + k] * Oth[((ph * D + t1) * D + t2) * D + kp];
+                }
+            R[i] = s;
+        } else {
+            long long e = i - totR;
+            int a = (int)(e / 4), q = (int)(e % 4);
+            int o1 = a / (D * D), o2 = (a / D) % D, k = a % D;
+            const double* x = X + (long long)(o1 * D + o2) * D4 * 4 * D;
+            double s = 0.0;
+            for (int j = 0; j < D4; ++j)
+                for (int ph = 0; ph < 4; ++ph) {
+                    int pidx = (side == 0) ? (q * 4 + ph) : (ph * 4 + q);
+                    s += x[((long long)j * 4 + ph) * D + k] * Tp[(long long)pidx * D4 + j];
+                }
+            S[a * 4 + q] = s;
+        }
+    }
+}
+
+// One-CTA solve of (R + delta I) X = S (m x m, 4 right-hand sides) by a
+// right-looking Cholesky in global memory (work copy W).  X written to the
+// own tensor in layout [ph][o1][o2][k] = Own[ph][a].  flag[0] |= 1 on a
+// non-positive pivot.  skip: if *skip, do nothing.
+__global__ void chol_solve_kernel(const double* __restrict__ R, const double* __restrict__ S, int m, double reg,
+                                  double* __restrict__ W, double* __restrict__ Own, int* flag, const int* skip) {
+    if (skip && *skip) return;
+    __shared__ double s_delta;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < m; ++i) tr += R[(long long)i * m + i];
+        s_delta = reg * tr / m;
+    }
+    __syncthreads();
+    for (long long e = tid; e < (long long)m * m; e += nt) {
+        int i = (int)(e / m), j = (int)(e % m);
+        W[e] = R[e] + ((i == j) ? s_delta : 0.0);
+    }
+    double* y = W + (long long)m * m;   // m x 4
+    for (int e = tid; e < 4 * m; e += nt) y[e] = S[e];
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) {
+            double dj = W[(long long)j * m + j];
+            if (!(dj > 0.0)) { flag[0] |= 1; dj = 1e-300; }
+            W[(long long)j * m + j] = sqrt(dj);
+        }
+        __syncthreads();
+        double ljj = W[(long long)j * m + j];
+        for (int i = j + 1 + tid; i < m; i += nt) W[(long long)i * m + j] /= ljj;
+        __syncthreads();
+        int rows = m - j - 1;
+        for (long long e = tid; e < (long long)rows * rows; e += nt) {
+            int i = j + 1 + (int)(e / rows), c = j + 1 + (int)(e % rows);
+            if (c <= i) W[(long long)i * m + c] -= W[(long long)i * m + j] * W[(long long)c * m + j];
+        }
+        __syncthreads();
+    }
+    // forward: L y = S
+    for (int j = 0; j < m; ++j) {
+        double ljj = W[(long long)j * m + j];
+        if (tid < 4) y[j * 4 + tid] /= ljj;
+        __syncthreads();
+        for (int e = tid; e < (m - j - 1) * 4; e += nt) {
+            int i = j + 1 + e / 4, q = e % 4;
+            y[i * 4 + q] -= W[(long long)i * m + j] * y[j * 4 + q];
+        }
+        __syncthreads();
+    }
+    // backward: L^T x = y
+    for (int j = m - 1; j >= 0; --j) {
+        double ljj = W[(long long)j * m + j];
+        if (tid < 4) y[j * 4 + tid] /= ljj;
+        __syncthreads();
+        for (int e = tid; e < j * 4; e += nt) {
+            int i = e / 4, q = e % 4;
+            y[i * 4 + q] -= W[(long long)j * m + i] * y[j * 4 + q];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < 4 * m; e += nt) {
+        int a = e / 4, q = e % 4;
+        Own[q * m + a] = y[e];
+    }
+}
+
+// cost d = sum_ph b^T R b - 2 b.S + c, with b = Own (layout [ph][a]); c = cost[0].
+// Writes cost[1 + slot] and compares with the previous value cost[2] -> flag[1].
+__global__ void als_cost_kernel(const double* __restrict__ R, const double* __restrict__ S,
+                                const double* __restrict__ Own, int m, double* cost, int* done, double tol,
+                                int first) {
+    __shared__ double red[32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double s = 0.0;
+    for (long long e = tid; e < (long long)m * m; e += nt) {
+        int a = (int)(e / m), b = (int)(e % m);
+        double r = R[e];
+        for (int q = 0; q < 4; ++q) s += Own[q * m + a] * r * Own[q * m + b];
+    }
+    for (int e = tid; e < 4 * m; e += nt) {
+        int a = e / 4, q = e % 4;
+        s -= 2.0 * Own[q * m + a] * S[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nt / 32; ++w) t += red[w];
+        double c = cost[0];
+        double dnew = t + c;
+        if (!first) {
+            double dold = cost[1];
+            if (c == 0.0 || fabs(dold - dnew) / c < tol) *done = 1;
+        }
+        cost[1] = dnew;
+        cost[3] += 1.0;     // iterations counted
+    }
+}
+
+// c = <T'|N|T'> = sum_p T'_p N T'_p
+__global__ void tnt_kernel(const double* __restrict__ Tp, const double* __restrict__ N, int D4, double* out) {
+    double s = 0.0;
+    long long tot = 16LL * D4 * D4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int p = (int)(i / ((long long)D4 * D4));
+        int a = (int)((i / D4) % D4), b = (int)(i % D4);
+        s += Tp[(long long)p * D4 + a] * N[(long long)a * D4 + b] * Tp[(long long)p * D4 + b];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// truncated-SVD start from the eigenpairs of Tm Tm^T (descending):
+// A''[(sA,aA,u,r)][k] = W[:,k] lam_k^{1/4}; colscale for B'' = Tm^T W lam^{-1/4}
+template <typename TJ>
+__global__ void svd_init_kernel(const TJ* Wt, const TJ* Lt, int mT, int D, double* A2m, double* colsc, double* Wd) {
+    double l0 = (double)Lt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mT * D; i += gridDim.x * blockDim.x) {
+        int r = i / D, k = i % D;
+        double lk = (k < mT) ? (double)Lt[k] : 0.0;
+        bool ok = (l0 > 0.0) && (lk > 1e-28 * l0);
+        double w = (double)Wt[(long long)r * mT + k];
+        A2m[i] = ok ? w * pow(lk, 0.25) : 0.0;
+        Wd[i] = w;
+        if (r == 0) colsc[k] = ok ? pow(lk, -0.25) : 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ gauge
+
+__device__ void jacobi_serial(double* A, double* V, int n) {
+    for (int i = 0; i < n * n; ++i) V[i] = (i / n == i % n) ? 1.0 : 0.0;
+    for (int sw = 0; sw < 60; ++sw) {
+        double off = 0.0, dg = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                if (i == j) dg += A[i * n + j] * A[i * n + j];
+                else off += A[i * n + j] * A[i * n + j];
+            }
+        if (off <= 1e-30 * dg || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - s * vkq;
+                    V[k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// Balanced gauge: G_A = A^T A, G_B = B^T B (D x D); X = G_A^-1/2 U mu^1/4,
+// Y = G_A^1/2 U mu^-1/4 with U mu U^T = G_A^1/2 G_B G_A^1/2 (mu descending);
+// A <- A X, B <- B Y; column signs so the largest |A| entry is positive;
+// unit Frobenius norms; then written back to the site layouts.
+__global__ void gauge_kernel(const double* __restrict__ A2, const double* __restrict__ B2, int D, int gamma,
+                             double* __restrict__ Asite, double* __restrict__ Bsite) {
+    __shared__ double GA[64], GB[64], WA[64], H[64], Uh[64], SA[64], SAi[64], Xg[64], Yg[64], mu[8], lam[8];
+    __shared__ int perm[8];
+    __shared__ double sgn[8], nrm[2];
+    extern __shared__ double sh[];           // An[mR*D], Bn[mR*D]
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int mR = 4 * D * D;                // rows (ph, o1, o2)
+    // own layouts: A2[ph][u][r][k] -> row (ph,u,r); B2[ph][d][l][k] -> row (ph,d,l)
+    for (int e = tid; e < D * D; e += nt) {
+        int i = e / D, j = e % D;
+        double sa = 0.0, sb = 0.0;
+        for (int r = 0; r < mR; ++r) {
+            sa += A2[r * D + i] * A2[r * D + j];
+            sb += B2[r * D + i] * B2[r * D + j];
+        }
+        GA[e] = sa;
+        GB[e] = sb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double tmp[64];
+        for (int i = 0; i < D * D; ++i) tmp[i] = GA[i];
+        jacobi_serial(tmp, WA, D);
+        double lmax = 0.0;
+        for (int i = 0; i < D; ++i) { lam[i] = tmp[i * D + i]; lmax = fmax(lmax, lam[i]); }
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                double a = 0.0, b = 0.0;
+                for (int k = 0; k < D; ++k) {
+                    bool ok = lam[k] > 1e-28 * lmax && lam[k] > 0.0;
+                    double sq = ok ? sqrt(lam[k]) : 0.0;
+                    double isq = ok ? 1.0 / sqrt(lam[k]) : 0.0;
+                    a += WA[i * D + k] * sq * WA[j * D + k];
+                    b += WA[i * D + k] * isq * WA[j * D + k];
+                }
+                SA[i * D + j] = a;
+                SAi[i * D + j] = b;
+            }
+        // H = SA GB SA
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                double s = 0.0;
+                for (int a = 0; a < D; ++a)
+                    for (int b = 0; b < D; ++b) s += SA[i * D + a] * GB[a * D + b] * SA[b * D + j];
+                H[i * D + j] = s;
+            }
+        for (int i = 0; i < D * D; ++i) tmp[i] = H[i];
+        jacobi_serial(tmp, Uh, D);
+        // sort descending
+        for (int i = 0; i < D; ++i) perm[i] = i;
+        for (int i = 0; i < D; ++i)
+            for (int j = i + 1; j < D; ++j)
+                if (tmp[perm[j] * D + perm[j]] > tmp[perm[i] * D + perm[i]]) { int t = perm[i]; perm[i] = perm[j]; perm[j] = t; }
+        double m0 = tmp[perm[0] * D + perm[0]];
+        for (int c = 0; c < D; ++c) {
+            int src = perm[c];
+            mu[c] = tmp[src * D + src];
+            bool ok = m0 > 0.0 && mu[c] > 1e-28 * m0;
+            double q4 = ok ? pow(mu[c], 0.25) : 0.0, iq4 = ok ? pow(mu[c], -0.25) : 0.0;
+            for (int i = 0; i < D; ++i) {
+                double x = 0.0, y = 0.0;
+                for (int a = 0; a < D; ++a) {
+                    x += SAi[i * D + a] * Uh[a * D + src];
+                    y += SA[i * D + a] * Uh[a * D + src];
+                }
+                Xg[i * D + c] = x * q4;
+                Yg[i * D + c] = y * iq4;
+            }
+        }
+    }
+    __syncthreads();
+    double* An = sh;
+    double* Bn = sh + mR * D;
+    for (int e = tid; e < mR * D; e += nt) {
+        int r = e / D, c = e % D;
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < D; ++k) {
+            a += A2[r * D + k] * Xg[k * D + c];
+            b += B2[r * D + k] * Yg[k * D + c];
+        }
+        An[e] = a;
+        Bn[e] = b;
+    }
+    __syncthreads();
+    if (tid < D) {
+        int c = tid;
+        double best = 0.0, v = 0.0;
+        for (int r = 0; r < mR; ++r) {
+            double x = An[r * D + c];
+            if (fabs(x) > best) { best = fabs(x); v = x; }
+        }
+        sgn[c] = (v < 0.0) ? -1.0 : 1.0;
+    }
+    if (tid == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int e = 0; e < mR * D; ++e) { sa += An[e] * An[e]; sb += Bn[e] * Bn[e]; }
+        nrm[0] = sa > 0.0 ? 1.0 / sqrt(sa) : 1.0;
+        nrm[1] = sb > 0.0 ? 1.0 / sqrt(sb) : 1.0;
+    }
+    __syncthreads();
+    // write back: A''[ph][u][r][k] -> Asite[ph][x][y][z] with u = alpha', r = alpha, k = gamma
+    int str[3] = {D * D, D, 1};
+    int al = (gamma + 1) % 3, alp = (gamma + 2) % 3;
+    const int D3 = D * D * D;
+    for (int e = tid; e < mR * D; e += nt) {
+        int r = e / D, c = e % D;
+        int ph = r / (D * D), o1 = (r / D) % D, o2 = r % D;
+        int off = ph * D3 + o1 * str[alp] + o2 * str[al] + c * str[gamma];
+        Asite[off] = An[e] * sgn[c] * nrm[0];
+        Bsite[off] = Bn[e] * sgn[c] * nrm[1];
+    }
+}
+
+// ------------------------------------------------------------------ ALS driver
+
+template <typename T>
+int Engine<T>::als_run(int gamma, double* rel_cost) {
+    (void)gamma;
+    const int D = dm.D, D4 = dm.D4, m = D * D * D, mT = 4 * dm.d2;
+    Slot<T>& sl = slots[gamma];
+    const double* Tp = sl.Ts;
+    // <T'|N|T'>
+    KH_CUDA(cudaMemsetAsync(cost, 0, 8 * sizeof(double), st));
+    KH_CUDA(cudaMemsetAsync(flags, 0, 8 * sizeof(int), st));
+    tnt_kernel<<<grid_for(16LL * D4 * D4), 256, 0, st>>>(Tp, N, D4, cost);
+    KH_LAUNCHED();
+    // truncated SVD start: Tm[(sA,aA,u,r)][(sB,aB,d,l)] from T'[sA,aA,sB,aB,l,u,r,d]
+    permute<double, double>(Tp, Tm, {2, 2, 2, 2, D, D, D, D}, {0, 1, 5, 6, 2, 3, 7, 4}, st);
+    gemm_rm<double>(mT, mT, mT, Tm, false, Tm, true, Gt, st);               // Tm Tm^T
+    double* colsc = dwork;
+    double* Wd = dwork + 64;
+    if (mT <= jacobi_kmax<double>()) {
+        jacobi_eig<double>(Gt, mT, mT, 0, Wt, mT, 0, Lt, 0, 1, 60, 1e-15, nullptr, nullptr, st);
+        svd_init_kernel<double><<<grid_for(mT * D), 256, 0, st>>>(Wt, Lt, mT, D, A2, colsc, Wd);
+        KH_LAUNCHED();
+    } else {
+        cast<double, float>(Gt, Gtf, (long long)mT * mT, st);
+        jacobi_eig<float>(Gtf, mT, mT, 0, Wtf, mT, 0, Ltf, 0, 1, 60, 1e-7, nullptr, nullptr, st);
+        svd_init_kernel<float><<<grid_for(mT * D), 256, 0, st>>>(Wtf, Ltf, mT, D, A2, colsc, Wd);
+        KH_LAUNCHED();
+    }
+    // B''[(sB,aB,d,l)][k] = sum_i Tm[i][.] Wd[i][k] colsc[k]
+    gemm_rm<double>(mT, D, mT, Tm, true, Wd, false, B2, st, 1.0, 0.0, colsc);
+    // initial cost with (A'', B'') from the start: B-side normal equations from A''
+    const int threads = 256;
+    als_x_kernel<<<grid_for(4LL * dm.d2 * D4 * D), threads, 0, st>>>(N, A2, D, 1, XA);
+    KH_LAUNCHED();
+    als_rs_kernel<<<grid_for((long long)m * m + 4 * m), threads, 0, st>>>(XA, A2, Tp, D, 1, R, S);
+    KH_LAUNCHED();
+    als_cost_kernel<<<1, 256, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 1);
+    KH_LAUNCHED();
+    int iters = 0;
+    for (int it = 1; it <= cfg.als_max_iter; ++it) {
+        // A step (fixed B'')
+        als_x_kernel<<<grid_for(4LL * dm.d2 * D4 * D), threads, 0, st>>>(N, B2, D, 0, XA);
+        KH_LAUNCHED();
+        als_rs_kernel<<<grid_for((long long)m * m + 4 * m), threads, 0, st>>>(XA, B2, Tp, D, 0, R, S);
+        KH_LAUNCHED();
+        chol_solve_kernel<<<1, 512, 0, st>>>(R, S, m, cfg.als_reg, Xmat, A2, flags, nullptr);
+        KH_LAUNCHED();
+        // B step (fixed A'')
+        als_x_kernel<<<grid_for(4LL * dm.d2 * D4 * D), threads, 0, st>>>(N, A2, D, 1, XA);
+        KH_LAUNCHED();
+        als_rs_kernel<<<grid_for((long long)m * m + 4 * m), threads, 0, st>>>(XA, A2, Tp, D, 1, R, S);
+        KH_LAUNCHED();
+        chol_solve_kernel<<<1, 512, 0, st>>>(R, S, m, cfg.als_reg, Xmat, B2, flags, nullptr);
+        KH_LAUNCHED();
+        als_cost_kernel<<<1, 256, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 0);
+        KH_LAUNCHED();
+        iters = it;
+        int hf[2];
+        KH_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+        KH_CUDA(cudaStreamSynchronize(st));
+        if (hf[0]) fail(KH_ENUMERIC, "ALS: Cholesky breakdown (metric not positive)");
+        if (hf[1]) break;
+    }
+    double hc[2];
+    KH_CUDA(cudaMemcpyAsync(hc, cost, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+    *rel_cost = hc[0] != 0.0 ? hc[1] / hc[0] : 0.0;
+    return iters;
+}
+
+template <typename T>
+void Engine<T>::gauge_and_store(int gamma) {
+    const int D = dm.D, mR = 4 * D * D;
+    size_t sm = sizeof(double) * 2 * mR * D;
+    gauge_kernel<<<1, 256, sm, st>>>(A2, B2, D, gamma, A, B);
+    KH_LAUNCHED();
+}
+
+template <typename T>
+void Engine<T>::apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) {
+    if (gamma < 0 || gamma > 2) fail(KH_EINVAL, "gamma must be 0, 1 or 2");
+    if (dm.nslots < 3) fail(KH_EINVAL, "eeFU needs n_slots >= 3");
+    if (4 * dm.d2 > jacobi_kmax<float>()) fail(KH_EINVAL, "bond update start limited to D <= 6");
+    build_composite(gamma, gamma, gate);
+    double delta = 0.0;
+    int sw = sweep(gamma, mx, mn, tol, &delta);
+    compute_metric(slots[gamma], N);
+    double rel = 0.0;
+    int it = als_run(gamma, &rel);
+    gauge_and_store(gamma);
+    if (info) {
+        double tr[4];
+        KH_CUDA(cudaMemcpyAsync(tr, slots[gamma].trunc, sizeof(tr), cudaMemcpyDeviceToHost, st));
+        KH_CUDA(cudaStreamSynchronize(st));
+        info[0] = rel;
+        info[1] = sw;
+        info[2] = it;
+        info[3] = fmax(fmax(tr[0], tr[1]), fmax(tr[2], tr[3]));
+    }
+}
+
+// ------------------------------------------------------------------ observables
+
+// X[p][q] = (T N T^T)[p][q] for the three mappings -> E_site etc.
+__global__ void obs_kernel(const double* __restrict__ Xs, Mat4x3 H, double hA, double hB, double* out) {
+    if (threadIdx.x != 0) return;
+    double Hg[3];
+    for (int g = 0; g < 3; ++g) {
+        const double* X = Xs + g * 256;
+        double tr = 0.0, s = 0.0;
+        for (int a = 0; a < 16; ++a) tr += X[a * 16 + a];
+        // sum H4[(sA' sB'),(sA sB)] X[(sA',aA,sB',aB)][(sA,aA,sB,aB)]
+        for (int sAo = 0; sAo < 2; ++sAo)
+            for (int sBo = 0; sBo < 2; ++sBo)
+                for (int sA = 0; sA < 2; ++sA)
+                    for (int sB = 0; sB < 2; ++sB) {
+                        double h = H.v[g * 16 + (sAo * 2 + sBo) * 4 + sA * 2 + sB];
+                        if (h == 0.0) continue;
+                        for (int aA = 0; aA < 2; ++aA)
+                            for (int aB = 0; aB < 2; ++aB) {
+                                int pa = ((sAo * 2 + aA) * 2 + sBo) * 2 + aB;
+                                int pb = ((sA * 2 + aA) * 2 + sB) * 2 + aB;
+                                s += h * X[pa * 16 + pb];
+                            }
+                    }
+        Hg[g] = s / tr;
+    }
+    // site moments from the z mapping: S^x = sigma^x/2, S^z = sigma^z/2 (S^y gives 0 on real X)
+    const double* X = Xs + 2 * 256;
+    double tr = 0.0;
+    for (int a = 0; a < 16; ++a) tr += X[a * 16 + a];
+    double sxA = 0, szA = 0, sxB = 0, szB = 0;
+    for (int a = 0; a < 16; ++a) {
+        int sA = (a >> 3) & 1, sB = (a >> 1) & 1;
+        szA += (sA ? -0.5 : 0.5) * X[a * 16 + a];
+        szB += (sB ? -0.5 : 0.5) * X[a * 16 + a];
+        sxA += 0.5 * X[(a ^ 8) * 16 + a];
+        sxB += 0.5 * X[(a ^ 2) * 16 + a];
+    }
+    sxA /= tr; szA /= tr; sxB /= tr; szB /= tr;
+    out[0] = 0.5 * (Hg[0] + Hg[1] + Hg[2]) - 0.5 * (hA * szA + hB * szB);
+    out[1] = Hg[0]; out[2] = Hg[1]; out[3] = Hg[2];
+    out[4] = sxA; out[5] = 0.0; out[6] = szA;
+    out[7] = sxB; out[8] = 0.0; out[9] = szB;
+}
+
+template <typename T>
+void Engine<T>::observables(const double* Hh, double hA, double hB, int mx, int mn, double tol, double* out) {
+    if (dm.nslots < 6) fail(KH_EINVAL, "observables need n_slots >= 6");
+    int sweeps = 0;
+    for (int g = 0; g < 3; ++g) {
+        int s = 3 + g;
+        if (!slots[s].env_valid || slots[s].p == 0) {
+            if (slots[g].p != 0) copy_env(s, g);
+            else init_env(s, nullptr);
+        }
+        build_composite(s, g, nullptr);
+        sweeps += sweep(s, mx, mn, tol, nullptr);
+        compute_metric(slots[s], N);
+        gemm_rm<double>(16, dm.D4, dm.D4, slots[s].Ts, false, N, false, dwork, st);
+        gemm_rm<double>(16, 16, dm.D4, dwork, false, slots[s].Ts, true, Xs + g * 256, st);
+    }
+    Mat4x3 H;
+    for (int i = 0; i < 48; ++i) H.v[i] = Hh[i];
+    double* dout = dscr + 4200;
+    obs_kernel<<<1, 32, 0, st>>>(Xs, H, hA, hB, dout);
+    KH_LAUNCHED();
+    double tr[12];
+    KH_CUDA(cudaMemcpyAsync(out, dout, sizeof(double) * 10, cudaMemcpyDeviceToHost, st));
+    for (int g = 0; g < 3; ++g)
+        KH_CUDA(cudaMemcpyAsync(tr + 4 * g, slots[3 + g].trunc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+    double mt = 0.0;
+    for (int i = 0; i < 12; ++i) mt = fmax(mt, tr[i]);
+    out[10] = mt;
+    out[11] = sweeps;
+}
+
+template struct Engine<double>;
+template struct Engine<float>;
+
+}  // namespace kh

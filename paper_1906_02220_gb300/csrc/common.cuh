@@ -1,0 +1,269 @@
+// Internal header of the eeFU GB300 library: context layout, workspace
+// carving, error handling and the small generic kernels (permutation,
+// strided batched GEMM on CUDA cores, reductions, casts).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+#include <string>
+#include <vector>
+
+#include "../../include/eefu.h"
+
+namespace kh {
+
+// ------------------------------------------------------------------ errors
+
+struct Error {
+    kh_status st;
+    std::string msg;
+};
+
+#define KH_CUDA(call)                                                                 \
+    do {                                                                              \
+        cudaError_t _e = (call);                                                      \
+        if (_e != cudaSuccess) {                                                      \
+            throw ::kh::Error{KH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)}; \
+        }                                                                             \
+    } while (0)
+
+#define KH_CHECK_LAUNCH() KH_CUDA(cudaGetLastError())
+#define KH_LAUNCHED() do { KH_CUDA(cudaGetLastError()); ::kh::count_launch(); } while (0)
+
+inline void fail(kh_status st, const std::string& m) { throw Error{st, m}; }
+
+// number of kernels this library has launched (read by kh_launch_count)
+extern unsigned long long g_launches;
+inline void count_launch() { ++g_launches; }
+
+// ------------------------------------------------------------------ workspace
+
+// Bump allocator over the caller's workspace; every block 256-byte aligned.
+struct Carver {
+    char* base;
+    size_t cap, off;
+    explicit Carver(void* b = nullptr, size_t c = 0) : base((char*)b), cap(c), off(0) {}
+    template <typename T>
+    T* take(size_t n) {
+        size_t bytes = ((n * sizeof(T) + 255) / 256) * 256;
+        size_t at = off;
+        off += bytes;
+        if (base == nullptr) return nullptr;          // sizing pass
+        if (off > cap) fail(KH_ENOMEM, "workspace too small");
+        return (T*)(base + at);
+    }
+};
+
+// ------------------------------------------------------------------ permutation
+
+constexpr int kMaxRank = 8;
+struct PermArgs {
+    int rank;
+    long long total;
+    long long out_dims[kMaxRank];   // output shape (row-major)
+    long long in_strides[kMaxRank]; // input stride of each output axis
+};
+
+// out[i_0..i_{r-1}] = in[sum_j i_j * in_strides[j]]
+template <typename Ti, typename To>
+__global__ void permute_kernel(const Ti* __restrict__ in, To* __restrict__ out, PermArgs a) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long step = (long long)gridDim.x * blockDim.x;
+    for (; idx < a.total; idx += step) {
+        long long rem = idx, src = 0;
+        for (int j = a.rank - 1; j >= 0; --j) {
+            long long d = a.out_dims[j];
+            long long i = rem % d;
+            rem /= d;
+            src += i * a.in_strides[j];
+        }
+        out[idx] = (To)in[src];
+    }
+}
+
+// Build PermArgs from an input shape and the axis order of the output:
+// out axis j is input axis order[j].
+inline PermArgs make_perm(const std::vector<long long>& in_shape, const std::vector<int>& order) {
+    PermArgs a;
+    memset(&a, 0, sizeof(a));
+    int r = (int)in_shape.size();
+    if (r > kMaxRank || (int)order.size() != r) fail(KH_EINVAL, "permute rank");
+    std::vector<long long> in_str(r);
+    long long s = 1;
+    for (int j = r - 1; j >= 0; --j) { in_str[j] = s; s *= in_shape[j]; }
+    a.rank = r;
+    a.total = s;
+    for (int j = 0; j < r; ++j) {
+        a.out_dims[j] = in_shape[order[j]];
+        a.in_strides[j] = in_str[order[j]];
+    }
+    return a;
+}
+
+inline int grid_for(long long n, int block = 256) {
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 64) g = 152LL * 64;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename Ti, typename To>
+inline void permute(const Ti* in, To* out, const std::vector<long long>& in_shape,
+                    const std::vector<int>& order, cudaStream_t st) {
+    PermArgs a = make_perm(in_shape, order);
+    permute_kernel<Ti, To><<<grid_for(a.total), 256, 0, st>>>(in, out, a);
+    KH_LAUNCHED();
+}
+
+template <typename Ti, typename To>
+__global__ void cast_kernel(const Ti* __restrict__ in, To* __restrict__ out, long long n) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long step = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += step) out[i] = (To)in[i];
+}
+
+template <typename Ti, typename To>
+inline void cast(const Ti* in, To* out, long long n, cudaStream_t st) {
+    cast_kernel<Ti, To><<<grid_for(n), 256, 0, st>>>(in, out, n);
+    KH_LAUNCHED();
+}
+
+// ------------------------------------------------------------------ SIMT GEMM
+
+// C[b](m,n) = alpha * colscale[n] * sum_k A[b](m,k) B[b](k,n) + beta * C[b](m,n)
+// with arbitrary element strides.  CUDA-core FMA in T.
+template <typename T>
+struct GemmArgs {
+    int M, N, K, batch;
+    const T* A; long long sAm, sAk, sAb;
+    const T* B; long long sBk, sBn, sBb;
+    T* C; long long sCm, sCn, sCb;
+    T alpha, beta;
+    const T* colscale;   // nullable, length N
+};
+
+constexpr int GT_K = 16;
+
+// Tile BM x BN per CTA, each of the 256 threads computes TM x TN outputs
+// strided by (BM/TM, BN/TN) so that shared-memory reads are conflict-free.
+template <typename T, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
+    static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+    constexpr int RX = BN / TN;                    // threads along N
+    __shared__ T As[GT_K][BM + 1];
+    __shared__ T Bs[GT_K][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % RX, ty = tid / RX;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const long long b = blockIdx.z;
+    const T* A = g.A + b * g.sAb;
+    const T* B = g.B + b * g.sBb;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+    const bool a_kfast = (g.sAk == 1);
+    const bool b_nfast = (g.sBn == 1);
+    for (int k0 = 0; k0 < g.K; k0 += GT_K) {
+        for (int e = tid; e < BM * GT_K; e += 256) {
+            int mm, kk;
+            if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : T(0);
+        }
+        for (int e = tid; e < BN * GT_K; e += 256) {
+            int nn, kb;
+            if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
+            int gn = n0 + nn, gkb = k0 + kb;
+            Bs[kb][nn] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GT_K; ++kk) {
+            T a[TM], bb[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + (BM / TM) * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + RX * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    T* C = g.C + b * g.sCb;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        int gm = m0 + ty + (BM / TM) * i;
+        if (gm >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            int gn = n0 + tx + RX * j;
+            if (gn >= g.N) continue;
+            T v = g.alpha * acc[i][j];
+            if (g.colscale) v *= g.colscale[gn];
+            T* dst = C + gm * g.sCm + gn * g.sCn;
+            if (g.beta != T(0)) v += g.beta * (*dst);
+            *dst = v;
+        }
+    }
+}
+
+template <typename T, int BM, int BN, int TM, int TN>
+inline void gemm_launch(const GemmArgs<T>& g, cudaStream_t st) {
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch);
+    if (grid.y > 65535) fail(KH_EINVAL, "gemm M too large");
+    gemm_simt_kernel<T, BM, BN, TM, TN><<<grid, 256, 0, st>>>(g);
+    KH_LAUNCHED();
+}
+
+template <typename T>
+inline void gemm(const GemmArgs<T>& g, cudaStream_t st) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+    if (g.batch > 65535) fail(KH_EINVAL, "gemm batch > 65535");
+    if (g.M <= 16 && g.N <= 16) gemm_launch<T, 16, 16, 1, 1>(g, st);
+    else if (g.N <= 16) gemm_launch<T, 128, 16, 2, 4>(g, st);
+    else if (g.M <= 16) gemm_launch<T, 16, 128, 4, 2>(g, st);
+    else gemm_launch<T, 64, 64, 4, 4>(g, st);
+}
+
+// Plain row-major C(MxN) = A(MxK) B(KxN) [+beta C]; transposes by flags.
+template <typename T>
+inline void gemm_rm(int M, int N, int K, const T* A, bool tA, const T* B, bool tB, T* C,
+                    cudaStream_t st, T alpha = T(1), T beta = T(0), const T* colscale = nullptr) {
+    GemmArgs<T> g;
+    g.M = M; g.N = N; g.K = K; g.batch = 1;
+    g.A = A; g.sAm = tA ? 1 : K; g.sAk = tA ? M : 1; g.sAb = 0;
+    g.B = B; g.sBk = tB ? 1 : N; g.sBn = tB ? K : 1; g.sBb = 0;
+    g.C = C; g.sCm = N; g.sCn = 1; g.sCb = 0;
+    g.alpha = alpha; g.beta = beta; g.colscale = colscale;
+    gemm(g, st);
+}
+
+// ------------------------------------------------------------------ reductions
+
+// out[0] = sum x^2 (FP64 accumulate), single block-grid reduction via atomics
+template <typename T>
+__global__ void sumsq_kernel(const T* __restrict__ x, long long n, double* out) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = (double)x[i];
+        s += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) atomicAdd(out, s);
+    }
+}
+
+}  // namespace kh

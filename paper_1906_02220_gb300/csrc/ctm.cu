@@ -1,0 +1,744 @@
+// CTMRG on the rhombic (square) lattice of composites, Fig. 4(c) and Sec. III
+// of arXiv:1906.02220.  Ket and bra layers are contracted separately (the
+// D^2 double-layer index is never formed): every enlarged corner and every
+// edge absorption applies the site tensor twice, once per layer.
+//
+// One move (the left move in a frame rotated by s quarter turns):
+//   Q_f   = C1 E1 E4 (T, T)         upper-left enlarged corner of frame f,
+//           rows c = (E4 leg, d_ket, d_bra), cols (E1 leg, r_ket, r_bra);
+//   the lower-left corner of frame s is Q_{s+3}^T, so the half-system
+//   product is M = Q_s^T Q_{s+3}^T and we form Mt = M^T = Q_{s+3} Q_s;
+//   top-chi SVD M = U S V^T by subspace iteration with Rayleigh-Ritz steps
+//   (Jacobi on the k x k Gram matrices), warm-started from the previous
+//   subspace of the same direction;
+//   P = Q_{s+3}^T V S^-1/2, P~^T = Q_s U S^-1/2;
+//   C1 <- P^T (C1 E1), C4 <- (C4 E3) P~^T, E4 <- P^T (E4 T T) P~^T,
+//   each divided by its Frobenius norm (FP64).
+#include "engine.cuh"
+
+namespace kh {
+
+// ------------------------------------------------------------------ config
+
+void validate(const kh_config& c) {
+    if (c.D < 1 || c.D > 8) fail(KH_EINVAL, "D must be in [1, 8]");
+    if (c.chi < 1 || c.chi > 256) fail(KH_EINVAL, "chi must be in [1, 256]");
+    if (c.prec < KH_FP64 || c.prec > KH_BF16) fail(KH_EINVAL, "unknown precision");
+    if (c.n_slots < 1 || c.n_slots > 16) fail(KH_EINVAL, "n_slots must be in [1, 16]");
+    if (c.p_max < 1 || c.p_max > 16) fail(KH_EINVAL, "p_max must be in [1, 16]");
+    if (c.svd_oversample < 0 || c.svd_iters_cold < 1 || c.svd_iters_warm < 1)
+        fail(KH_EINVAL, "bad subspace iteration settings");
+    if (c.jacobi_max_sweeps < 1) fail(KH_EINVAL, "jacobi_max_sweeps < 1");
+    if (!(c.svd_cut >= 0.0) || !(c.als_reg >= 0.0) || c.als_max_iter < 0) fail(KH_EINVAL, "bad tolerances");
+}
+
+Dims make_dims(const kh_config& c, bool fp64) {
+    Dims d;
+    d.D = c.D;
+    d.d2 = c.D * c.D;
+    d.D4 = d.d2 * d.d2;
+    d.chi = c.chi;
+    d.n = c.chi * d.d2;
+    d.pmax = c.p_max;
+    d.nslots = c.n_slots;
+    int kmax = fp64 ? 112 : 160;
+    if (d.n <= kmax) {
+        d.kk = d.n;
+        d.full = true;
+    } else {
+        d.kk = c.chi + c.svd_oversample;
+        if (d.kk > d.n) d.kk = d.n;
+        d.full = false;
+        if (d.kk > kmax) fail(KH_EINVAL, "chi + svd_oversample exceeds the Jacobi limit");
+    }
+    return d;
+}
+
+template <typename T>
+void Engine<T>::layout(Carver& cv) {
+    const Dims& d = dm;
+    const long long chi2 = (long long)d.chi * d.chi, E1 = (long long)d.chi * d.d2 * d.chi;
+    const long long n = d.n, n2 = n * n, D3 = (long long)d.D * d.D * d.D, kk = d.kk;
+    A = cv.take<double>(4 * D3);
+    B = cv.take<double>(4 * D3);
+    slots.assign(d.nslots, Slot<T>());
+    for (auto& s : slots) {
+        s.Ts = cv.take<double>((long long)d.pmax * d.D4);
+        s.C = cv.take<double>(4 * chi2);
+        s.E = cv.take<double>(4 * E1);
+        s.Tcor = cv.take<T>(4LL * d.pmax * d.D4);
+        s.Tedg = cv.take<T>(4LL * d.pmax * d.D4);
+        s.Vw = cv.take<T>(4 * n * kk);
+        s.spec = cv.take<double>(4LL * d.chi);
+        s.prev = cv.take<double>(4LL * d.chi);
+        s.trunc = cv.take<double>(4);
+        s.delta = cv.take<double>(1);
+    }
+    Cop = cv.take<T>(4 * chi2);
+    Eop = cv.take<T>(4 * E1);
+    X1[0] = cv.take<T>(E1);
+    X1[1] = cv.take<T>(E1);
+    Y1 = cv.take<T>(n2);
+    Yp = cv.take<T>(n2);
+    Zk = cv.take<T>((long long)d.pmax * n2);
+    Qt = cv.take<T>(n2);
+    Q[0] = cv.take<T>(n2);
+    Q[1] = cv.take<T>(n2);
+    Mt = cv.take<T>(n2);
+    V0 = cv.take<T>(n * kk);
+    Z1 = cv.take<T>(n * kk);
+    U = cv.take<T>(n * kk);
+    Z2 = cv.take<T>(n * kk);
+    Vo = cv.take<T>(n * kk);
+    Uf = cv.take<T>(n * kk);
+    G1 = cv.take<T>(kk * kk);
+    W1 = cv.take<T>(kk * kk);
+    G2 = cv.take<T>(kk * kk);
+    W2 = cv.take<T>(kk * kk);
+    L1 = cv.take<T>(kk);
+    L2 = cv.take<T>(kk);
+    isq = cv.take<T>(kk > d.chi ? kk : d.chi);
+    P = cv.take<T>(n * d.chi);
+    PtT = cv.take<T>(n * d.chi);
+    C4E3 = cv.take<T>(n * d.chi);
+    C1n = cv.take<T>(chi2);
+    C4n = cv.take<T>(chi2);
+    E4n = cv.take<T>(E1);
+    dscr = cv.take<double>(8192 + kk * kk);
+    mt1 = cv.take<T>(E1);
+    mt2 = cv.take<T>(E1);
+    mup = cv.take<T>(n2);
+    mdn = cv.take<T>(n2);
+    mupp = cv.take<T>(n2);
+    mdnp = cv.take<T>(n2);
+    mN4 = cv.take<T>((long long)d.D4 * d.D4);
+    N = cv.take<double>((long long)d.D4 * d.D4);
+    const long long mT = 4LL * d.d2;                 // rows of T' as [(sA,aA,u,r)]
+    const long long m = D3;                          // size of R
+    A2 = cv.take<double>(4 * D3);
+    B2 = cv.take<double>(4 * D3);
+    XA = cv.take<double>(4LL * d.D4 * d.d2 * d.D);  // [(o1,o2)][D^4][(ph,k)]
+    R = cv.take<double>(m * m);
+    S = cv.take<double>(m * 4);
+    Xs = cv.take<double>(3LL * 16 * 16 + 64);
+    Tm = cv.take<double>(mT * mT);
+    Gt = cv.take<double>(mT * mT);
+    Wt = cv.take<double>(mT * mT);
+    Lt = cv.take<double>(mT);
+    Gtf = cv.take<float>(mT * mT);
+    Wtf = cv.take<float>(mT * mT);
+    Ltf = cv.take<float>(mT);
+    Xmat = cv.take<double>(m * m + 4 * m);
+    cost = cv.take<double>(64);
+    dwork = cv.take<double>(4 * E1 + 16LL * d.D4 + 64);
+    flags = cv.take<int>(64);
+}
+
+template <typename T>
+size_t Engine<T>::bytes_needed(const kh_config& c) {
+    Engine<T> e;
+    e.cfg = c;
+    e.dm = make_dims(c, sizeof(T) == 8);
+    Carver cv(nullptr, 0);
+    e.layout(cv);
+    return cv.off + 256;
+}
+
+// beta = 0 purification: spin maximally entangled with its ancilla, virtual index 0
+__global__ void init_state_kernel(double* A, double* B, int D) {
+    if (threadIdx.x == 0) {
+        long long D3 = (long long)D * D * D;
+        A[0] = 1.0; A[3 * D3] = 1.0;
+        B[0] = 1.0; B[3 * D3] = 1.0;
+    }
+}
+
+template <typename T>
+Engine<T>::Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s) {
+    cfg = c;
+    st = s;
+    dm = make_dims(c, sizeof(T) == 8);
+    Carver cv(ws, bytes);
+    layout(cv);
+    KH_CUDA(cudaMemsetAsync(ws, 0, cv.off, st));
+    init_state_kernel<<<1, 32, 0, st>>>(A, B, dm.D);
+    KH_LAUNCHED();
+    for (int i = 0; i < dm.nslots; ++i) init_env(i, nullptr);
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <typename T>
+__global__ void identity_kernel(T* V, int n, int k) {
+    long long tot = (long long)n * k;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(i / k), c = (int)(i % k);
+        V[i] = (r == c) ? T(1) : T(0);
+    }
+}
+
+template <typename T>
+__global__ void rand_kernel(T* V, long long tot, uint64_t seed, uint64_t stream) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x)
+        V[i] = (T)rnd_uniform(seed, stream, (uint64_t)i);
+}
+
+// Gram G = Z^T Z (Z: n x k row-major), FP64 accumulation split over row chunks.
+template <typename T>
+__global__ void gram_kernel(const T* __restrict__ Z, int n, int k, double* __restrict__ G, int rows_per) {
+    int i = blockIdx.x * 16 + (threadIdx.x >> 4);
+    int j = blockIdx.y * 16 + (threadIdx.x & 15);
+    int r0 = blockIdx.z * rows_per, r1 = min(n, r0 + rows_per);
+    if (i >= k || j >= k) return;
+    double acc = 0.0;
+    if (sizeof(T) == 8) {
+        for (int r = r0; r < r1; ++r) acc += (double)Z[(long long)r * k + i] * (double)Z[(long long)r * k + j];
+    } else {
+        for (int r = r0; r < r1; r += 8) {
+            float f = 0.f;
+            int re = min(r1, r + 8);
+            for (int q = r; q < re; ++q) f = fmaf((float)Z[(long long)q * k + i], (float)Z[(long long)q * k + j], f);
+            acc += (double)f;
+        }
+    }
+    atomicAdd(&G[i * k + j], acc);
+}
+
+template <typename T>
+static void gram(const T* Z, int n, int k, T* G, double* dtmp, cudaStream_t st) {
+    KH_CUDA(cudaMemsetAsync(dtmp, 0, sizeof(double) * k * k, st));
+    int rows_per = 128;
+    dim3 grid((k + 15) / 16, (k + 15) / 16, (n + rows_per - 1) / rows_per);
+    gram_kernel<T><<<grid, 256, 0, st>>>(Z, n, k, dtmp, rows_per);
+    KH_LAUNCHED();
+    cast<double, T>(dtmp, G, (long long)k * k, st);
+}
+
+// isq[j] = lam_j > cut^2 lam_0 ? 1/sqrt(lam_j) : 0
+template <typename T>
+__global__ void inv_sqrt_cut_kernel(const T* lam, int k, double cut, T* isq) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= k) return;
+    double l0 = (double)lam[0], lj = (double)lam[j];
+    isq[j] = (l0 > 0.0 && lj > cut * cut * l0) ? (T)(1.0 / sqrt(lj)) : T(0);
+}
+
+// spectrum, S^-1/2 with cut-off, discarded weight
+template <typename T>
+__global__ void finalize_spectrum_kernel(const T* lam, int k, int chi, double cut, const double* normM2,
+                                         double* spec, T* isq, double* trunc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int nkeep = min(chi, k);
+    double s0 = sqrt(fmax((double)lam[0], 0.0));
+    double kept = 0.0;
+    for (int j = 0; j < chi; ++j) {
+        double s = (j < nkeep) ? sqrt(fmax((double)lam[j], 0.0)) : 0.0;
+        if (j < nkeep) kept += s * s;
+        bool keep = (s0 > 0.0) && (s > cut * s0);
+        spec[j] = keep ? s : 0.0;
+        isq[j] = keep ? (T)(1.0 / sqrt(s)) : T(0);
+    }
+    double tot = *normM2;
+    double tr = (tot > 0.0) ? (tot - kept) / tot : 0.0;
+    *trunc = tr > 0.0 ? tr : 0.0;
+}
+
+// warm subspace store; dead columns (lam_j <= cut^2 lam_0) re-randomised
+template <typename T>
+__global__ void store_warm_kernel(const T* Vo, const T* lam, int n, int k, double cut, T* Vw, uint64_t seed,
+                                  uint64_t stream) {
+    long long tot = (long long)n * k;
+    double l0 = (double)lam[0];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % k);
+        double lc = (double)lam[c];
+        bool dead = !(l0 > 0.0 && lc > cut * cut * l0);
+        Vw[i] = dead ? (T)rnd_uniform(seed, stream, (uint64_t)i) : Vo[i];
+    }
+}
+
+template <typename T>
+__global__ void store_normalized_kernel(const T* x, long long n, const double* sumsq, double* master, T* op) {
+    double s = *sumsq;
+    double inv = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = (double)x[i] * inv;
+        master[i] = v;
+        op[i] = (T)v;
+    }
+}
+
+__global__ void delta_kernel(const double* spec, double* prev, int chi, int prev_valid, double* delta) {
+    // one block of 32 threads: dir-wise normalised max difference
+    __shared__ double nrm[4];
+    int t = threadIdx.x;
+    if (t < 4) {
+        double s = 0.0;
+        for (int j = 0; j < chi; ++j) s += spec[t * chi + j] * spec[t * chi + j];
+        nrm[t] = s > 0.0 ? sqrt(s) : 1.0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double d = 0.0;
+        for (int q = 0; q < 4; ++q)
+            for (int j = 0; j < chi; ++j) {
+                double v = spec[q * chi + j] / nrm[q];
+                d = fmax(d, fabs(v - prev[q * chi + j]));
+                prev[q * chi + j] = v;
+            }
+        *delta = prev_valid ? d : INFINITY;
+    }
+}
+
+__global__ void init_env_kernel(double* C, double* E, int chi, int d2, const double* edge, int has_edge, int D) {
+    long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
+    long long tot = 4 * chi2 + 4 * E1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < 4 * chi2) {
+            long long j = i % chi2;
+            C[i] = (j == 0) ? 1.0 : 0.0;
+        } else {
+            long long q = i - 4 * chi2;
+            long long j = q % E1;
+            long long x = j / ((long long)d2 * chi), rem = j % ((long long)d2 * chi);
+            long long m = rem / chi, y = rem % chi;
+            double v = 0.0;
+            if (x == 0 && y == 0) {
+                if (has_edge) v = edge[m];
+                else v = ((m / D) == (m % D)) ? 1.0 : 0.0;
+            }
+            E[q] = v;
+        }
+    }
+}
+
+// symmetrise N (n x n) in place: N = (N + N^T)/2
+__global__ void symmetrize_kernel(double* Nm, int n) {
+    long long tot = (long long)n * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int r = (int)(i / n), c = (int)(i % n);
+        if (r < c) {
+            double a = Nm[(long long)r * n + c], b = Nm[(long long)c * n + r];
+            double m = 0.5 * (a + b);
+            Nm[(long long)r * n + c] = m;
+            Nm[(long long)c * n + r] = m;
+        }
+    }
+}
+
+// out = sum_i a[i] * b[perm(i)] in FP64 via strided index maps (small sizes)
+__global__ void dot_kernel(const double* a, const double* b, long long n, double* out) {
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// Z10-type ring closure: sum_{h,m,f} t3[(h*d2+m)*chi+f] * u[(f*d2+m)*chi+h]
+__global__ void ring_close_kernel(const double* t3, const double* u, int chi, int d2, double* out) {
+    long long tot = (long long)chi * d2 * chi;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int h = (int)(i / ((long long)d2 * chi));
+        int m = (int)((i / chi) % d2);
+        int f = (int)(i % chi);
+        s += t3[i] * u[((long long)f * d2 + m) * chi + h];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// Z01-type: sum_{a,m,e} t3[(a*d2+m)*chi+e] * u[e*(d2*chi) + m*chi + a]
+__global__ void ring_close2_kernel(const double* t3, const double* u, int chi, int d2, double* out) {
+    long long tot = (long long)chi * d2 * chi;
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int a = (int)(i / ((long long)d2 * chi));
+        int m = (int)((i / chi) % d2);
+        int e = (int)(i % chi);
+        s += t3[i] * u[(long long)e * d2 * chi + (long long)m * chi + a];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// vals[i] = sum_ab O_i[a][b] X[a][b] / tr X
+__global__ void expval_kernel(const double* ops, int n_ops, int p, const double* X, double* vals) {
+    int i = threadIdx.x;
+    if (i >= n_ops) return;
+    double tr = 0.0, s = 0.0;
+    for (int a = 0; a < p; ++a) tr += X[a * p + a];
+    for (int a = 0; a < p * p; ++a) s += ops[(long long)i * p * p + a] * X[a];
+    vals[i] = s / tr;
+}
+
+// ------------------------------------------------------------------ env management
+
+template <typename T>
+void Engine<T>::init_env(int slot, const double* edge) {
+    Slot<T>& sl = slots[slot];
+    const int d2 = dm.d2;
+    if (edge) KH_CUDA(cudaMemcpyAsync(dscr, edge, sizeof(double) * d2, cudaMemcpyHostToDevice, st));
+    long long tot = 4LL * dm.chi * dm.chi + 4LL * dm.chi * d2 * dm.chi;
+    init_env_kernel<<<grid_for(tot), 256, 0, st>>>(sl.C, sl.E, dm.chi, d2, dscr, edge != nullptr, dm.D);
+    KH_LAUNCHED();
+    sl.env_valid = true;
+    sl.prev_valid = false;
+    for (int q = 0; q < 4; ++q) sl.warm[q] = false;
+    if (edge) KH_CUDA(cudaStreamSynchronize(st));   // dscr is reused
+}
+
+template <typename T>
+void Engine<T>::copy_env(int dst, int src) {
+    Slot<T>& a = slots[dst];
+    Slot<T>& b = slots[src];
+    const long long chi2 = (long long)dm.chi * dm.chi, E1 = (long long)dm.chi * dm.d2 * dm.chi;
+    KH_CUDA(cudaMemcpyAsync(a.C, b.C, sizeof(double) * 4 * chi2, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaMemcpyAsync(a.E, b.E, sizeof(double) * 4 * E1, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaMemcpyAsync(a.Vw, b.Vw, sizeof(T) * 4LL * dm.n * dm.kk, cudaMemcpyDeviceToDevice, st));
+    a.env_valid = b.env_valid;
+    a.prev_valid = false;
+    for (int q = 0; q < 4; ++q) a.warm[q] = b.warm[q];
+}
+
+template <typename T>
+void Engine<T>::refresh_operands(Slot<T>& sl) {
+    cast<double, T>(sl.C, Cop, 4LL * dm.chi * dm.chi, st);
+    cast<double, T>(sl.E, Eop, 4LL * dm.chi * dm.d2 * dm.chi, st);
+}
+
+// ------------------------------------------------------------------ contractions
+
+// Two-layer site contraction: for each of nb blocks,
+//   out[b][(o1k,o2k)][(o1b,o2b)] = sum_p sum TL[(i1k,i2k)][p][(o1k,o2k)]
+//                                  Y[b][(i1b,i2b)][(i1k,i2k)] TL[(i1b,i2b)][p][(o1b,o2b)]
+// with TL = T permuted to [in1][in2][p][out1][out2]: first the ket layer as one
+// GEMM (K = D^2), then the bra layer batched over b (K = p D^2).
+template <typename T>
+void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out) {
+    const int d2 = dm.d2;
+    prof_begin(1);
+    gemm_rm<T>((int)(nb * d2), p * d2, d2, Ybuf, false, TL, false, Zk, st);
+    for (long long b0 = 0; b0 < nb; b0 += 65535) {
+        GemmArgs<T> g;
+        g.M = d2; g.N = d2; g.K = d2 * p;
+        g.batch = (int)((nb - b0) < 65535 ? (nb - b0) : 65535);
+        g.A = Zk + b0 * (long long)d2 * p * d2; g.sAm = 1; g.sAk = d2; g.sAb = (long long)d2 * p * d2;
+        g.B = TL; g.sBk = d2; g.sBn = 1; g.sBb = 0;
+        g.C = out + b0 * (long long)d2 * d2; g.sCm = d2; g.sCn = 1; g.sCb = (long long)d2 * d2;
+        g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
+        gemm<T>(g, st);
+    }
+    prof_end(1, 4.0 * (double)nb * p * d2 * (double)d2 * d2);
+}
+
+template <typename T>
+void Engine<T>::corner(Slot<T>& sl, int f, int which) {
+    const int chi = dm.chi, d2 = dm.d2, D = dm.D;
+    const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
+    const T* C1 = Cop + f * chi2;
+    const T* E1p = Eop + f * E1;
+    const T* E4 = Eop + ((f + 3) & 3) * E1;
+    T* X = X1[which];
+    gemm_rm<T>(chi, d2 * chi, chi, C1, false, E1p, false, X, st);            // [x4][(uk,ub,z)]
+    gemm_rm<T>(chi * d2, d2 * chi, chi, E4, false, X, false, Y1, st);        // [(w,lk,lb)][(uk,ub,z)]
+    permute<T, T>(Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3}, st);  // [w][z][lb][ub][lk][uk]
+    site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt);  // [w][z][rk][dk][rb][db]
+    permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}, st);  // [w][dk][db][z][rk][rb]
+}
+
+template <typename T>
+void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
+    const int n = dm.n, k = dm.kk, chi = dm.chi;
+    const double cut = cfg.svd_cut;
+    const double jtol = sizeof(T) == 8 ? 1e-14 : 2e-6;   // ~sqrt(k) eps rounding floor
+    const T* Qa = Q[0];
+    const T* Qb = Q[1];
+    prof_begin(0);
+    gemm_rm<T>(n, n, n, Qb, false, Qa, false, Mt, st);                        // Mt = Qb Qa = M^T
+    prof_end(0, 2.0 * n * (double)n * n);
+    double* normM2 = dscr + 8000;
+    KH_CUDA(cudaMemsetAsync(normM2, 0, sizeof(double), st));
+    sumsq_kernel<T><<<grid_for((long long)n * n), 256, 0, st>>>(Mt, (long long)n * n, normM2);
+    KH_LAUNCHED();
+    const T* Vin;
+    int q;
+    uint64_t stream = (uint64_t)slot_id * 4 + dir;
+    if (dm.full) {
+        identity_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(V0, n, k);
+        KH_LAUNCHED();
+        Vin = V0;
+        q = 1;
+    } else if (!sl.warm[dir]) {
+        rand_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(V0, (long long)n * k, cfg.seed,
+                                                                  stream * 1000003ULL + (rng_counter++));
+        KH_LAUNCHED();
+        Vin = V0;
+        q = cfg.svd_iters_cold;
+    } else {
+        Vin = sl.Vw + (long long)dir * n * k;
+        q = cfg.svd_iters_warm;
+    }
+    double* dG = dscr + 8192;   // kk*kk doubles
+    for (int it = 0; it < q; ++it) {
+        gemm_rm<T>(n, k, n, Mt, true, Vin, false, Z1, st);                     // Z1 = M Vin
+        gram<T>(Z1, n, k, G1, dG, st);
+        jacobi_eig<T>(G1, k, k, 0, W1, k, 0, L1, 0, 1, cfg.jacobi_max_sweeps, jtol, nullptr, nullptr, st);
+        inv_sqrt_cut_kernel<T><<<(k + 127) / 128, 128, 0, st>>>(L1, k, cut, isq);
+        KH_LAUNCHED();
+        gemm_rm<T>(n, k, k, Z1, false, W1, false, U, st, T(1), T(0), isq);     // U = Z1 W1 L1^-1/2
+        gemm_rm<T>(n, k, n, Mt, false, U, false, Z2, st);                      // Z2 = M^T U
+        gram<T>(Z2, n, k, G2, dG, st);
+        jacobi_eig<T>(G2, k, k, 0, W2, k, 0, L2, 0, 1, cfg.jacobi_max_sweeps, jtol, nullptr, nullptr, st);
+        inv_sqrt_cut_kernel<T><<<(k + 127) / 128, 128, 0, st>>>(L2, k, cut, isq);
+        KH_LAUNCHED();
+        gemm_rm<T>(n, k, k, Z2, false, W2, false, Vo, st, T(1), T(0), isq);    // V = Z2 W2 L2^-1/2
+        gemm_rm<T>(n, k, k, U, false, W2, false, Uf, st);                      // U <- U W2
+        Vin = Vo;
+    }
+    finalize_spectrum_kernel<T><<<1, 32, 0, st>>>(L2, k, chi, cut, normM2, sl.spec + (long long)dir * chi, isq,
+                                                  sl.trunc + dir);
+    KH_LAUNCHED();
+    const int nkeep = chi < k ? chi : k;
+    if (nkeep < chi) {
+        KH_CUDA(cudaMemsetAsync(P, 0, sizeof(T) * (size_t)n * chi, st));
+        KH_CUDA(cudaMemsetAsync(PtT, 0, sizeof(T) * (size_t)n * chi, st));
+    }
+    {   // P = Qb^T V S^-1/2
+        GemmArgs<T> g;
+        g.M = n; g.N = nkeep; g.K = n; g.batch = 1;
+        g.A = Qb; g.sAm = 1; g.sAk = n; g.sAb = 0;
+        g.B = Vo; g.sBk = k; g.sBn = 1; g.sBb = 0;
+        g.C = P; g.sCm = chi; g.sCn = 1; g.sCb = 0;
+        g.alpha = T(1); g.beta = T(0); g.colscale = isq;
+        gemm<T>(g, st);
+    }
+    {   // P~^T = Qa U S^-1/2
+        GemmArgs<T> g;
+        g.M = n; g.N = nkeep; g.K = n; g.batch = 1;
+        g.A = Qa; g.sAm = n; g.sAk = 1; g.sAb = 0;
+        g.B = Uf; g.sBk = k; g.sBn = 1; g.sBb = 0;
+        g.C = PtT; g.sCm = chi; g.sCn = 1; g.sCb = 0;
+        g.alpha = T(1); g.beta = T(0); g.colscale = isq;
+        gemm<T>(g, st);
+    }
+    if (!dm.full) {
+        store_warm_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(
+            Vo, L2, n, k, cut, sl.Vw + (long long)dir * n * k, cfg.seed, stream * 1000003ULL + (rng_counter++));
+        KH_LAUNCHED();
+        sl.warm[dir] = true;
+    }
+}
+
+template <typename T>
+void Engine<T>::absorb(Slot<T>& sl, int s) {
+    const int chi = dm.chi, d2 = dm.d2, D = dm.D, n = dm.n;
+    const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
+    {   // C1n = P^T X1a
+        GemmArgs<T> g;
+        g.M = chi; g.N = chi; g.K = n; g.batch = 1;
+        g.A = P; g.sAm = 1; g.sAk = chi; g.sAb = 0;
+        g.B = X1[0]; g.sBk = chi; g.sBn = 1; g.sBb = 0;
+        g.C = C1n; g.sCm = chi; g.sCn = 1; g.sCb = 0;
+        g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
+        gemm<T>(g, st);
+    }
+    const T* C4 = Cop + ((s + 3) & 3) * chi2;
+    const T* E3 = Eop + ((s + 2) & 3) * E1;
+    const T* E4 = Eop + ((s + 3) & 3) * E1;
+    {   // C4E3[v][y4][(dk,db)] = sum_x3 C4[x3][y4] E3[v][(dk,db)][x3]
+        GemmArgs<T> g;
+        g.M = chi; g.N = d2; g.K = chi; g.batch = chi;
+        g.A = C4; g.sAm = 1; g.sAk = chi; g.sAb = 0;
+        g.B = E3; g.sBk = 1; g.sBn = chi; g.sBb = (long long)d2 * chi;
+        g.C = C4E3; g.sCm = d2; g.sCn = 1; g.sCb = n;
+        g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
+        gemm<T>(g, st);
+    }
+    gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, st);                  // C4n = C4E3 P~^T
+    gemm_rm<T>(d2 * chi, d2 * chi, chi, E4, true, P, false, Y1, st);             // [(lk,lb,x4)][(dk,db,a)]
+    permute<T, T>(Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3}, st);       // [x4][a][lb][db][lk][dk]
+    site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt);     // [x4][a][uk][rk][ub][rb]
+    permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
+    gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st);                 // [a][rk][rb][a_up]
+    double* ns = dscr + 8010;
+    KH_CUDA(cudaMemsetAsync(ns, 0, 3 * sizeof(double), st));
+    sumsq_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C1n, chi2, ns);
+    KH_LAUNCHED();
+    sumsq_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C4n, chi2, ns + 1);
+    KH_LAUNCHED();
+    sumsq_kernel<T><<<grid_for(E1), 256, 0, st>>>(E4n, E1, ns + 2);
+    KH_LAUNCHED();
+    store_normalized_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C1n, chi2, ns, sl.C + s * chi2, Cop + s * chi2);
+    KH_LAUNCHED();
+    store_normalized_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C4n, chi2, ns + 1, sl.C + ((s + 3) & 3) * chi2,
+                                                              Cop + ((s + 3) & 3) * chi2);
+    KH_LAUNCHED();
+    store_normalized_kernel<T><<<grid_for(E1), 256, 0, st>>>(E4n, E1, ns + 2, sl.E + ((s + 3) & 3) * E1,
+                                                            Eop + ((s + 3) & 3) * E1);
+    KH_LAUNCHED();
+}
+
+template <typename T>
+void Engine<T>::move(Slot<T>& sl, int s, int slot_id) {
+    corner(sl, s, 0);
+    corner(sl, (s + 3) & 3, 1);
+    projector(sl, s, slot_id);
+    absorb(sl, s);
+}
+
+template <typename T>
+int Engine<T>::sweep(int slot, int max_sweeps, int min_sweeps, double tol, double* delta_out) {
+    Slot<T>& sl = slots[slot];
+    if (sl.p <= 0) fail(KH_EINVAL, "slot has no site tensor");
+    if (!sl.env_valid) init_env(slot, nullptr);
+    refresh_operands(sl);
+    double delta = INFINITY;
+    int done = 0;
+    for (int it = 1; it <= max_sweeps; ++it) {
+        for (int s = 0; s < 4; ++s) move(sl, s, slot);
+        delta_kernel<<<1, 32, 0, st>>>(sl.spec, sl.prev, dm.chi, sl.prev_valid ? 1 : 0, sl.delta);
+        KH_LAUNCHED();
+        sl.prev_valid = true;
+        done = it;
+        if (tol >= 0.0) {
+            KH_CUDA(cudaMemcpyAsync(&delta, sl.delta, sizeof(double), cudaMemcpyDeviceToHost, st));
+            KH_CUDA(cudaStreamSynchronize(st));
+            if (!(delta == delta)) fail(KH_ENUMERIC, "NaN in CTM spectra");
+            if (it >= min_sweeps && delta < tol) break;
+        }
+    }
+    sl.sweeps_done += done;
+    if (delta_out) *delta_out = delta;
+    return done;
+}
+
+template <typename T>
+void Engine<T>::projectors_out(int slot, int dir, double* spec, double* trunc) {
+    Slot<T>& sl = slots[slot];
+    if (spec)
+        KH_CUDA(cudaMemcpyAsync(spec, sl.spec + (long long)dir * dm.chi, sizeof(double) * dm.chi,
+                                cudaMemcpyDeviceToDevice, st));
+    if (trunc) {
+        KH_CUDA(cudaMemcpyAsync(trunc, sl.trunc + dir, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    KH_CUDA(cudaStreamSynchronize(st));
+}
+
+template <typename T>
+void Engine<T>::get_env(int slot, double* C, double* E) {
+    Slot<T>& sl = slots[slot];
+    const long long chi2 = (long long)dm.chi * dm.chi, E1 = (long long)dm.chi * dm.d2 * dm.chi;
+    if (C) KH_CUDA(cudaMemcpyAsync(C, sl.C, sizeof(double) * 4 * chi2, cudaMemcpyDeviceToDevice, st));
+    if (E) KH_CUDA(cudaMemcpyAsync(E, sl.E, sizeof(double) * 4 * E1, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------ metric, kappa, expval
+
+template <typename T>
+void Engine<T>::compute_metric(Slot<T>& sl, double* N_out) {
+    const int chi = dm.chi, d2 = dm.d2, D = dm.D;
+    const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
+    refresh_operands(sl);
+    const T *C1 = Cop, *C2 = Cop + chi2, *C3 = Cop + 2 * chi2, *C4 = Cop + 3 * chi2;
+    const T *E1p = Eop, *E2 = Eop + E1, *E3 = Eop + 2 * E1, *E4 = Eop + 3 * E1;
+    gemm_rm<T>(chi, d2 * chi, chi, C1, false, E1p, false, mt1, st);          // [h][(u,b)]
+    gemm_rm<T>(chi * d2, chi, chi, mt1, false, C2, false, mt2, st);           // [(h,u)][c]
+    gemm_rm<T>(chi * d2, d2 * chi, chi, mt2, false, E2, false, mup, st);      // [(h,u)][(r,e)]
+    gemm_rm<T>(chi, d2 * chi, chi, C3, false, E3, false, mt1, st);           // [e][(d,g)]
+    gemm_rm<T>(chi * d2, chi, chi, mt1, false, C4, false, mt2, st);           // [(e,d)][i]
+    gemm_rm<T>(chi * d2, d2 * chi, chi, mt2, false, E4, false, mdn, st);      // [(e,d)][(l,h)]
+    permute<T, T>(mup, mupp, {chi, D, D, D, D, chi}, {1, 2, 3, 4, 0, 5}, st);  // [uk][ub][rk][rb][h][e]
+    permute<T, T>(mdn, mdnp, {chi, D, D, D, D, chi}, {5, 0, 1, 2, 3, 4}, st);  // [h][e][dk][db][lk][lb]
+    gemm_rm<T>(d2 * d2, d2 * d2, chi * chi, mupp, false, mdnp, false, mN4, st);
+    permute<T, double>(mN4, N_out, {D, D, D, D, D, D, D, D}, {6, 0, 2, 4, 7, 1, 3, 5}, st);
+    symmetrize_kernel<<<grid_for((long long)dm.D4 * dm.D4), 256, 0, st>>>(N_out, dm.D4);
+    KH_LAUNCHED();
+}
+
+template <typename T>
+void Engine<T>::metric(int slot, double* N_out) {
+    compute_metric(slots[slot], N);
+    KH_CUDA(cudaMemcpyAsync(N_out, N, sizeof(double) * dm.D4 * dm.D4, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+}
+
+template <typename T>
+double Engine<T>::kappa(int slot) {
+    Slot<T>& sl = slots[slot];
+    const int chi = dm.chi, d2 = dm.d2, p = sl.p, D4 = dm.D4;
+    const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
+    compute_metric(sl, N);
+    double* z = dscr + 8020;    // Z11, Z00, Z10, Z01
+    KH_CUDA(cudaMemsetAsync(z, 0, 4 * sizeof(double), st));
+    double* w1 = dwork;
+    double* w2 = dwork + E1;
+    double* w3 = dwork + 2 * E1;
+    double* w4 = dwork + 3 * E1;
+    // Z11 = sum_p T_p N T_p
+    gemm_rm<double>(p, D4, D4, sl.Ts, false, N, false, w1, st);
+    dot_kernel<<<grid_for((long long)p * D4), 256, 0, st>>>(w1, sl.Ts, (long long)p * D4, z);
+    KH_LAUNCHED();
+    const double *C1 = sl.C, *C2 = sl.C + chi2, *C3 = sl.C + 2 * chi2, *C4 = sl.C + 3 * chi2;
+    const double *E1p = sl.E, *E2 = sl.E + E1, *E3 = sl.E + 2 * E1, *E4 = sl.E + 3 * E1;
+    // Z00 = Tr(C1 C2 C3 C4)
+    gemm_rm<double>(chi, chi, chi, C1, false, C2, false, w1, st);
+    gemm_rm<double>(chi, chi, chi, w1, false, C3, false, w2, st);
+    // Tr(w2 C4) = sum_ij w2[i][j] (C4^T)[i][j]
+    permute<double, double>(C4, w4, {chi, chi}, {1, 0}, st);
+    dot_kernel<<<grid_for(chi2), 256, 0, st>>>(w2, w4, chi2, z + 1);
+    KH_LAUNCHED();
+    // Z10 = C1 E1 C2 C3 E3 C4 with E1.m = E3.m
+    gemm_rm<double>(chi, d2 * chi, chi, C1, false, E1p, false, w1, st);      // [h][(m,b)]
+    gemm_rm<double>(chi * d2, chi, chi, w1, false, C2, false, w2, st);       // [(h,m)][c]
+    gemm_rm<double>(chi * d2, chi, chi, w2, false, C3, false, w3, st);       // [(h,m)][f]
+    gemm_rm<double>(chi * d2, chi, chi, E3, false, C4, false, w4, st);       // [(f,m)][h]
+    ring_close_kernel<<<grid_for(E1), 256, 0, st>>>(w3, w4, chi, d2, z + 2);
+    KH_LAUNCHED();
+    // Z01 = C1 C2 E2 C3 C4 E4 with E2.m = E4.m
+    gemm_rm<double>(chi, chi, chi, C1, false, C2, false, w1, st);             // [a][c]
+    gemm_rm<double>(chi, d2 * chi, chi, w1, false, E2, false, w2, st);        // [a][(m,d)]
+    gemm_rm<double>(chi * d2, chi, chi, w2, false, C3, false, w3, st);       // [(a,m)][e]
+    gemm_rm<double>(chi, d2 * chi, chi, C4, false, E4, false, w4, st);        // [e][(m,a)]
+    ring_close2_kernel<<<grid_for(E1), 256, 0, st>>>(w3, w4, chi, d2, z + 3);
+    KH_LAUNCHED();
+    double h[4];
+    KH_CUDA(cudaMemcpyAsync(h, z, sizeof(h), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+    return h[0] * h[1] / (h[2] * h[3]);
+}
+
+template <typename T>
+void Engine<T>::expval(int slot, const double* ops, int n_ops, double* vals) {
+    Slot<T>& sl = slots[slot];
+    const int p = sl.p, D4 = dm.D4;
+    if (n_ops < 1 || n_ops > 16) fail(KH_EINVAL, "n_ops must be in [1, 16]");
+    compute_metric(sl, N);
+    double* X = Xs;
+    double* TN = dwork;
+    gemm_rm<double>(p, D4, D4, sl.Ts, false, N, false, TN, st);
+    gemm_rm<double>(p, p, D4, TN, false, sl.Ts, true, X, st);
+    double* dops = dscr;
+    double* dvals = dscr + 4096;
+    KH_CUDA(cudaMemcpyAsync(dops, ops, sizeof(double) * n_ops * p * p, cudaMemcpyHostToDevice, st));
+    expval_kernel<<<1, 32, 0, st>>>(dops, n_ops, p, X, dvals);
+    KH_LAUNCHED();
+    KH_CUDA(cudaMemcpyAsync(vals, dvals, sizeof(double) * n_ops, cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+}
+
+template struct Engine<double>;
+template struct Engine<float>;
+
+}  // namespace kh

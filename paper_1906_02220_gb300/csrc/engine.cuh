@@ -1,0 +1,168 @@
+// eeFU engine: context layout and the declarations shared by the CTMRG
+// (ctm.cu), bond-update (bond.cu) and C-ABI (abi.cu) translation units.
+#pragma once
+#include "common.cuh"
+#include "jacobi.cuh"
+
+namespace kh {
+
+// ------------------------------------------------------------------ per-slot state
+
+template <typename T>
+struct Slot {
+    double* Ts = nullptr;     // master site tensor [p][D^4]
+    int p = 0;                // physical dimension of the loaded tensor (0 = none)
+    double* C = nullptr;      // 4 x chi x chi
+    double* E = nullptr;      // 4 x chi x D^2 x chi
+    T* Tcor = nullptr;        // 4 frames x [l][u][p][r][d]  (corner layer operand)
+    T* Tedg = nullptr;        // 4 frames x [l][d][p][u][r]  (edge layer operand)
+    T* Vw = nullptr;          // 4 dirs x n x kk  (warm projector subspaces)
+    double* spec = nullptr;   // 4 x chi  last kept spectra (descending)
+    double* prev = nullptr;   // 4 x chi  normalised spectra of the previous sweep
+    double* trunc = nullptr;  // 4        discarded weight per move
+    double* delta = nullptr;  // 1        last sweep's spectrum change
+    bool env_valid = false;   // environment initialised
+    bool prev_valid = false;  // prev holds a sweep
+    bool warm[4] = {false, false, false, false};
+    int sweeps_done = 0;
+};
+
+struct Dims {
+    int D, d2, D4, chi, n, kk, pmax, nslots;
+    bool full;                 // kk == n: exact Rayleigh-Ritz on the whole space
+};
+
+// ------------------------------------------------------------------ engine
+
+// CUDA-event timing of kernel categories (bench instrumentation only):
+// 0 = half-system product Mt = Q_{s+3} Q_s, 1 = two-layer site contractions.
+struct ProfCat {
+    std::vector<cudaEvent_t> a, b;
+    int used = 0;
+    double flops = 0.0;
+};
+
+struct EngineBase {
+    virtual ~EngineBase() {
+        for (auto& c : prof)
+            for (size_t i = 0; i < c.a.size(); ++i) { cudaEventDestroy(c.a[i]); cudaEventDestroy(c.b[i]); }
+    }
+    bool prof_on = false;
+    ProfCat prof[2];
+    void prof_begin(int cat) {
+        if (!prof_on) return;
+        ProfCat& c = prof[cat];
+        if (c.used == (int)c.a.size()) {
+            cudaEvent_t x, y;
+            KH_CUDA(cudaEventCreate(&x));
+            KH_CUDA(cudaEventCreate(&y));
+            c.a.push_back(x);
+            c.b.push_back(y);
+        }
+        KH_CUDA(cudaEventRecord(c.a[c.used], st));
+    }
+    void prof_end(int cat, double flops) {
+        if (!prof_on) return;
+        ProfCat& c = prof[cat];
+        KH_CUDA(cudaEventRecord(c.b[c.used], st));
+        c.used++;
+        c.flops += flops;
+    }
+    kh_config cfg;
+    Dims dm;
+    cudaStream_t st = 0;
+    std::string err;
+    virtual void set_state(const double* A, const double* B) = 0;
+    virtual void get_state(double* A, double* B) = 0;
+    virtual void set_tensor(int slot, const double* Tin, int p) = 0;
+    virtual void build_composite(int slot, int gamma, const double* gate) = 0;
+    virtual void init_env(int slot, const double* edge) = 0;
+    virtual void copy_env(int dst, int src) = 0;
+    virtual int sweep(int slot, int max_sweeps, int min_sweeps, double tol, double* delta) = 0;
+    virtual void projectors_out(int slot, int dir, double* spec, double* trunc) = 0;
+    virtual void get_env(int slot, double* C, double* E) = 0;
+    virtual void metric(int slot, double* N_out) = 0;
+    virtual double kappa(int slot) = 0;
+    virtual void expval(int slot, const double* ops, int n_ops, double* vals) = 0;
+    virtual void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) = 0;
+    virtual void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
+                             double* out) = 0;
+};
+
+template <typename T>
+struct Engine : EngineBase {
+    // persistent
+    double* A = nullptr;       // 4 D^3 site tensors
+    double* B = nullptr;
+    std::vector<Slot<T>> slots;
+    // operand copies of the environment of the slot being swept
+    T *Cop = nullptr, *Eop = nullptr;
+    // CTM scratch
+    T *X1[2] = {nullptr, nullptr}, *Y1 = nullptr, *Yp = nullptr, *Zk = nullptr, *Qt = nullptr;
+    T *Q[2] = {nullptr, nullptr}, *Mt = nullptr;
+    T *V0 = nullptr, *Z1 = nullptr, *U = nullptr, *Z2 = nullptr, *Vo = nullptr, *Uf = nullptr;
+    T *G1 = nullptr, *W1 = nullptr, *L1 = nullptr, *G2 = nullptr, *W2 = nullptr, *L2 = nullptr;
+    T *isq = nullptr, *P = nullptr, *PtT = nullptr, *C4E3 = nullptr;
+    T *C1n = nullptr, *C4n = nullptr, *E4n = nullptr;
+    double* dscr = nullptr;    // small FP64 scratch (norms etc.)
+    // metric / bond scratch (FP64 unless noted)
+    T *mt1 = nullptr, *mt2 = nullptr, *mup = nullptr, *mdn = nullptr, *mupp = nullptr, *mdnp = nullptr, *mN4 = nullptr;
+    double *N = nullptr, *Tp = nullptr, *A2 = nullptr, *B2 = nullptr, *XA = nullptr, *R = nullptr,
+           *S = nullptr, *Xs = nullptr, *Tm = nullptr, *Gt = nullptr, *Wt = nullptr, *Lt = nullptr,
+           *Xmat = nullptr, *cost = nullptr, *dwork = nullptr;
+    float *Gtf = nullptr, *Wtf = nullptr, *Ltf = nullptr;
+    int* flags = nullptr;
+    unsigned long long rng_counter = 0;
+
+    Engine() {}
+    Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s);
+    static size_t bytes_needed(const kh_config& c);
+    void layout(Carver& cv);
+
+    // CTM internals
+    void refresh_operands(Slot<T>& sl);
+    void corner(Slot<T>& sl, int frame, int which);
+    void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out);
+    void projector(Slot<T>& sl, int dir, int slot_id);
+    void absorb(Slot<T>& sl, int s);
+    void move(Slot<T>& sl, int s, int slot_id);
+    void compute_metric(Slot<T>& sl, double* N_out);
+    void build_derived(Slot<T>& sl);
+
+    // bond internals
+    int als_run(int gamma, double* rel_cost);
+    void gauge_and_store(int gamma);
+
+    // API
+    void set_state(const double* A, const double* B) override;
+    void get_state(double* A, double* B) override;
+    void set_tensor(int slot, const double* Tin, int p) override;
+    void build_composite(int slot, int gamma, const double* gate) override;
+    void init_env(int slot, const double* edge) override;
+    void copy_env(int dst, int src) override;
+    int sweep(int slot, int max_sweeps, int min_sweeps, double tol, double* delta) override;
+    void projectors_out(int slot, int dir, double* spec, double* trunc) override;
+    void get_env(int slot, double* C, double* E) override;
+    void metric(int slot, double* N_out) override;
+    double kappa(int slot) override;
+    void expval(int slot, const double* ops, int n_ops, double* vals) override;
+    void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) override;
+    void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
+                     double* out) override;
+};
+
+Dims make_dims(const kh_config& c, bool fp64);
+void validate(const kh_config& c);
+
+// ------------------------------------------------------------------ small kernels
+
+// counter-based uniform(-1,1): splitmix64 of (seed, stream, index)
+__device__ __forceinline__ double rnd_uniform(uint64_t seed, uint64_t stream, uint64_t i) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ULL * (stream * 0x100000001B3ULL + i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+}  // namespace kh

@@ -1,0 +1,73 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point
+declared in include/eefu.h, sizes its workspace, and its host-side gate
+builders agree with the oracle.  No GPU compute is called here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_1906_02220_gb300", "libeefu_gb300.so")
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not os.path.exists(LIB):
+        from paper_1906_02220_gb300 import build
+        build.build()
+    import paper_1906_02220_gb300 as pkg
+    return pkg
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "eefu.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "defined")))
+
+
+def test_header_declares_the_binding_list(g):
+    assert sorted(g.ABI_FUNCTIONS) == _declared_functions()
+
+
+def test_library_exports_every_declared_symbol(g):
+    import ctypes
+    lib = ctypes.CDLL(LIB)
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+    out = os.popen("nm -D --defined-only %s" % LIB).read()
+    for name in _declared_functions():
+        assert re.search(r"\bT %s\b" % name, out), name
+
+
+def test_workspace_sizing(g):
+    import ctypes
+    c = g.default_config(4, 64, "fp32")
+    b32 = g.lib().kh_workspace_bytes(ctypes.byref(c))
+    c = g.default_config(4, 64, "fp64")
+    b64 = g.lib().kh_workspace_bytes(ctypes.byref(c))
+    assert 0 < b32 < b64 < 2 ** 31
+    for bad in (dict(D=0), dict(chi=0), dict(D=9), dict(prec=7), dict(n_slots=0)):
+        c = g.default_config(2, 8, "fp64")
+        for k, v in bad.items():
+            setattr(c, k, v)
+        assert g.lib().kh_workspace_bytes(ctypes.byref(c)) == 0
+
+
+@pytest.mark.parametrize("gamma", ["x", "y", "z"])
+def test_host_gates_match_oracle(g, gamma):
+    from oracle import model
+    J, K, hA, hB = 0.37, -1.4, 0.2, -0.6
+    bias = (hA, hB) if gamma == "z" else (0.0, 0.0)
+    H = g.bond_hamiltonian(gamma, J, K, *bias)
+    Ho = model.bond_hamiltonian(gamma, J, K, hA=bias[0], hB=bias[1])
+    assert np.abs(H - Ho).max() < 1e-15
+    for tau in (0.0, 0.0025, 0.3):
+        assert np.abs(g.gate(H, tau) - model.gate(gamma, tau, J, K, hA=bias[0], hB=bias[1])).max() < 1e-14
+
+
+def test_status_codes_on_bad_arguments_without_gpu(g):
+    import ctypes
+    assert g.lib().kh_bond_hamiltonian(5, 0.0, 0.0, 0.0, 0.0, None) == g.KH_EINVAL
+    assert g.lib().kh_create(None, None, None, 0, None) == g.KH_EINVAL

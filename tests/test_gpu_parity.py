@@ -1,0 +1,208 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs.  Gauge-invariant quantities only: free energies,
+the normalised environment metric N / ||N||, projector spectra s / ||s||,
+energies and magnetisations, bond costs.
+
+Tolerances: FP64 path 1e-9 (accumulated rounding of CTM iterations plus the
+subspace-iteration vs full-SVD difference at convergence); FP32 path 2e-5
+relative on normalised quantities (single-precision contractions with K up
+to chi^2 terms; bound = 2^-23 * sqrt(K) * a safety factor of ~30)."""
+import numpy as np
+import pytest
+
+import kh_inputs
+from oracle import ctmrg, eefu, exact, model, peps
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_02220_gb300 as pkg
+    return pkg
+
+
+def _t(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+def _nrm(x):
+    x = np.asarray(x, dtype=np.float64)
+    return x / np.linalg.norm(x)
+
+
+def _oracle_ctm(T, chi, sweeps, edge=None):
+    a = ctmrg.double_tensor(T)
+    env = ctmrg.init_env(chi, T.shape[1], edge)
+    specs = None
+    for _ in range(sweeps):
+        specs, truncs = ctmrg.sweep(env, a)
+    return env, specs, truncs
+
+
+# ----------------------------------------------------------------- CTMRG alone
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("Kh,Kv,seed,chi", [(0.3, 0.2, 7, 16), (0.25, 0.25, None, 24), (0.15, 0.36, 11, 13)])
+def test_ising_free_energy(g, prec, Kh, Kv, seed, chi):
+    T = exact.ising_peps(Kh, Kv, gauge_seed=seed)
+    ctx = g.Context(2, chi, prec, p_max=2, n_slots=1, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 300, 3, 1e-11 if prec == "fp64" else 1e-6)
+    lnk = np.log(ctx.ctm_kappa(0))
+    ref = exact.onsager_lnZ(Kh, Kv)
+    assert abs(lnk - ref) < (1e-9 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_yang_magnetisation(g, prec):
+    K = 0.5
+    T = exact.ising_peps(K, K)
+    V = exact.ising_bond_root(K)
+    ctx = g.Context(2, 20, prec, p_max=2, n_slots=1, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_init(0, np.outer(V[0], V[0]).reshape(4))
+    ctx.ctm_sweep(0, 300, 3, 1e-11 if prec == "fp64" else 1e-6)
+    m = ctx.ctm_expval(0, np.diag([1.0, -1.0]))[0]
+    assert abs(m - exact.yang_m(K)) < (1e-9 if prec == "fp64" else 2e-5)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("D,chi", [(2, 8), (3, 20), (3, 14)])
+def test_ctm_metric_and_spectra_match_oracle(g, prec, D, chi):
+    """Converged CTMRG of a seeded composite: metric N/||N|| and the four
+    projector spectra agree with the oracle's converged values.  (3,20) and
+    (3,14) exercise the subspace-iteration path (n = chi D^2 > Jacobi limit in
+    FP64) and ragged tile edges."""
+    A, B = kh_inputs.perturbed_product_state(D, seed=3, eps=0.2)
+    T = peps.composite(A, B, "z")
+    env, specs, _ = _oracle_ctm(T, chi, 0)
+    env, info = ctmrg.ctmrg(ctmrg.double_tensor(T), env, tol=1e-13, max_sweeps=300)
+    N_ref = ctmrg.metric(env, D)
+    ctx = g.Context(D, chi, prec, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 300, 3, 1e-12 if prec == "fp64" else 1e-7, allow_noconv=True)
+    N = ctx.ctm_metric(0).cpu().numpy()
+    tol = TOL[prec]
+    assert np.abs(_nrm(N) - _nrm(N_ref)).max() < tol * 10
+    for d in range(4):
+        s, tr = ctx.ctm_projectors(0, d)
+        s = s.cpu().numpy()
+        ref = info["spectra"][d]
+        assert np.abs(_nrm(s) - _nrm(ref)).max() < tol * 10
+        assert abs(tr - info["trunc"][d]) < max(1e-12, 1e-3 * info["trunc"][d]) + (0 if prec == "fp64" else 1e-6)
+
+
+def test_ctm_single_sweep_is_deterministic_and_exact_for_small_n(g):
+    """With n = chi D^2 within the Jacobi limit the projector SVD is exact, so
+    ONE sweep from the traced boundary matches the oracle's single sweep."""
+    D, chi = 2, 6
+    T = kh_inputs.random_composite(D, 5)
+    env, specs, truncs = _oracle_ctm(T, chi, 1)
+    ctx = g.Context(D, chi, "fp64")
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 1)
+    N = ctx.ctm_metric(0).cpu().numpy()
+    assert np.abs(_nrm(N) - _nrm(ctmrg.metric(env, D))).max() < 1e-12
+    for d in range(4):
+        s, tr = ctx.ctm_projectors(0, d)
+        assert np.abs(s.cpu().numpy() - specs[d]).max() < 1e-12 * max(1.0, specs[d][0])
+        assert abs(tr - truncs[d]) < 1e-12
+
+
+def test_edge_cases(g):
+    # chi = 1, D = 1 product tensor (exact), p = 1
+    T = np.array([0.7]).reshape(1, 1, 1, 1, 1)
+    ctx = g.Context(1, 1, "fp64", p_max=1, n_slots=1)
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 3)
+    s, tr = ctx.ctm_projectors(0, 0)
+    assert tr < 1e-28
+    assert abs(ctx.ctm_kappa(0) - 0.49) < 1e-14
+    # invalid configuration / arguments return status codes, not crashes
+    with pytest.raises(g.KhError):
+        g.Context(0, 4, "fp64")
+    with pytest.raises(g.KhError):
+        ctx.ctm_sweep(3, 1)
+    # zero sweeps requested is rejected
+    with pytest.raises(g.KhError):
+        ctx.ctm_sweep(0, 0)
+
+
+# ----------------------------------------------------------------- eeFU pipeline
+
+def _oracle_state(D, chi, J, K, A=None, B=None, **kw):
+    prm = eefu.Params(D=D, chi=chi, J=J, K=K, **kw)
+    if A is None:
+        A, B = peps.product_state(D)
+    return eefu.State(A, B, prm)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_layer_dimer_exact(g, prec):
+    J, K = model.couplings(0.3 * np.pi)
+    D = 4
+    ctx = g.Context(D, 8, prec, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    A, B = peps.product_state(D)
+    ctx.set_state(_t(A), _t(B))
+    db = 0.2
+    H = g.bond_hamiltonian("x", J, K)
+    info = ctx.eefu_apply_gate("x", g.gate(H, db / 4))
+    Hs = [g.bond_hamiltonian(gm, J, K) for gm in "xyz"]
+    r = ctx.observables(Hs)
+    want = exact.dimer_energy(J, K, db / 2)
+    assert abs(r["Hx"] - want) < TOL[prec]
+    assert abs(r["Hy"]) < TOL[prec] and abs(r["Hz"]) < TOL[prec]
+    assert abs(r["E_site"] - 0.5 * want) < TOL[prec]
+    assert info["rel_cost"] < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_kz_only_closed_form(g, prec):
+    Kz = 1.3
+    ctx = g.Context(2, 6, prec, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    for n in range(8):
+        ctx.eefu_trotter_step(0.0, [0.0, 0.0, Kz], 0.05)
+    Hs = [g.bond_hamiltonian(gm, 0.0, k) for gm, k in zip("xyz", [0.0, 0.0, Kz])]
+    r = ctx.observables(Hs)
+    assert abs(r["E_site"] - exact.kz_only_energy(Kz, 0.4)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("D,chi,steps", [(2, 16, 4), (3, 12, 2)])
+def test_trotter_steps_match_oracle(g, prec, D, chi, steps):
+    """KH model at phi = 0.3 pi from a seeded perturbed product state (bias on):
+    per-layer relative costs, and after the steps E/site, <H^gamma> and the
+    sublattice magnetisations agree with the oracle."""
+    J, K = model.couplings(0.3 * np.pi)
+    hA, hB = 0.3, -0.1
+    A, B = kh_inputs.perturbed_product_state(D, seed=11, eps=0.05)
+    cut = 1e-12 if prec == "fp64" else 1e-6
+    st = _oracle_state(D, chi, J, K, A, B, hA=hA, hB=hB, svd_cut=cut, ctm_tol=1e-12)
+    ctx = g.Context(D, chi, prec, svd_cut=cut)
+    ctx.set_state(_t(A), _t(B))
+    ctol = 1e-12 if prec == "fp64" else 1e-7
+    dbeta = 0.02
+    for n in range(steps):
+        oinf = eefu.trotter_step(st, dbeta)
+        ginf = ctx.eefu_trotter_step(J, [K, K, K], dbeta, hA, hB, ctm_max_sweeps=200, ctm_tol=ctol)
+        worst = max(i["rel_cost"] for i in oinf)
+        assert abs(ginf["rel_cost"] - worst) < 1e-6 * max(worst, 1e-12) + (1e-12 if prec == "fp64" else 1e-7)
+    ro = eefu.measure(st)
+    Hs = [g.bond_hamiltonian(gm, J, K) for gm in "xyz"]
+    r = ctx.observables(Hs, hA, hB, ctm_max_sweeps=200, ctm_tol=ctol)
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    for key in ("E_site", "Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+        assert abs(r[key] - ro[key]) < tol * max(1.0, abs(ro[key])), (key, r[key], ro[key])
+    # site tensors agree up to the bond gauge: compare gauge-invariant T
+    Ag, Bg = ctx.get_state()
+    for gm in "xyz":
+        To = peps.composite(st.A, st.B, gm)
+        Tg = peps.composite(Ag.cpu().numpy(), Bg.cpu().numpy(), gm)
+        assert np.abs(_nrm(Tg) - _nrm(To)).max() < (1e-8 if prec == "fp64" else 1e-4)
