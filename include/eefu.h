@@ -208,6 +208,31 @@ unsigned long long kh_launch_count(void);
  * category 1 (two-layer site contractions, 4 nb p D^6 flops per call). */
 kh_status kh_profile(kh_ctx* ctx, int enable, double* host_out);
 
+/* --- kernel self-tests (test hooks; no counterpart in the paper) ----------- */
+
+/* Scratch bytes the self-tests below need for an M x K by K x N product. */
+size_t kh_selftest_bytes(int M, int N, int K);
+
+/* dev_C (M x N) = dev_A (M x K) dev_B (K x N), all row-major FP64 device
+ * arrays, computed by the library's contraction GEMM for precision prec
+ * (operands converted to its input type, result converted back).  dev_scratch
+ * holds at least kh_selftest_bytes(M, N, K) bytes.  Synchronises stream. */
+kh_status kh_selftest_gemm(int prec, int M, int N, int K, const double* dev_A, const double* dev_B,
+                           double* dev_C, void* dev_scratch, size_t scratch_bytes, void* stream);
+
+/* Eigen-decomposition of a symmetric k x k FP64 matrix by the library's
+ * Jacobi kernel in FP64 (prec = KH_FP64) or FP32 (otherwise): dev_evals
+ * descending, column j of dev_W its eigenvector.  Scratch as above with
+ * M = N = K = k.  Synchronises stream. */
+kh_status kh_selftest_symeig(int prec, int k, const double* dev_G, double* dev_W, double* dev_evals,
+                             void* dev_scratch, size_t scratch_bytes, void* stream);
+
+/* One-sided Jacobi SVD of a k x k FP64 matrix X (row-major) by the library
+ * kernel used in the projector Rayleigh-Ritz step, in FP64 or FP32:
+ * X Q = L S with dev_S descending (k), dev_L, dev_Q k x k (columns = vectors). */
+kh_status kh_selftest_svd(int prec, int k, const double* dev_X, double* dev_S, double* dev_L, double* dev_Q,
+                          void* dev_scratch, size_t scratch_bytes, void* stream);
+
 /* Library build information (static string). */
 const char* kh_version(void);
 

@@ -24,7 +24,8 @@ ABI_FUNCTIONS = [
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
-    "eefu_trotter_step", "kh_launch_count", "kh_profile",
+    "eefu_trotter_step", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
+    "kh_selftest_symeig", "kh_selftest_svd",
 ]
 
 
@@ -78,6 +79,10 @@ def load_library(path=LIB_PATH):
         "eefu_trotter_step": (I, [P, D, dp, D, D, D, I, I, D, dp]),
         "kh_launch_count": (ctypes.c_ulonglong, []),
         "kh_profile": (I, [P, I, dp]),
+        "kh_selftest_bytes": (S, [I, I, I]),
+        "kh_selftest_gemm": (I, [I, I, I, I, P, P, P, P, S, P]),
+        "kh_selftest_symeig": (I, [I, I, P, P, P, P, S, P]),
+        "kh_selftest_svd": (I, [I, I, P, P, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -94,6 +99,55 @@ def lib():
     if _LIB is None:
         _LIB = load_library()
     return _LIB
+
+
+def selftest_gemm(A, B, prec="fp64"):
+    """C = A @ B (FP64 CUDA tensors) through the library's contraction GEMM."""
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    nb = lib().kh_selftest_bytes(M, N, K)
+    scr = torch.empty(nb + 256, dtype=torch.uint8, device=A.device)
+    base = (scr.data_ptr() + 255) // 256 * 256
+    st = lib().kh_selftest_gemm(PREC[prec], M, N, K, _tptr(A.contiguous()), _tptr(B.contiguous()), _tptr(C),
+                                ctypes.c_void_p(base), nb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_gemm")
+    return C
+
+
+def selftest_symeig(G, prec="fp64"):
+    """(evals descending, eigenvectors as columns) of a symmetric FP64 CUDA tensor."""
+    import torch
+    k = G.shape[0]
+    W = torch.empty((k, k), dtype=torch.float64, device=G.device)
+    E = torch.empty(k, dtype=torch.float64, device=G.device)
+    nb = lib().kh_selftest_bytes(k, k, k)
+    scr = torch.empty(nb + 256, dtype=torch.uint8, device=G.device)
+    base = (scr.data_ptr() + 255) // 256 * 256
+    st = lib().kh_selftest_symeig(PREC[prec], k, _tptr(G.contiguous()), _tptr(W), _tptr(E), ctypes.c_void_p(base), nb,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_symeig")
+    return E, W
+
+
+def selftest_svd(X, prec="fp64"):
+    """(S descending, L, Q) with X Q = L S, by the library's one-sided Jacobi kernel."""
+    import torch
+    k = X.shape[0]
+    S = torch.empty(k, dtype=torch.float64, device=X.device)
+    L = torch.empty((k, k), dtype=torch.float64, device=X.device)
+    Q = torch.empty((k, k), dtype=torch.float64, device=X.device)
+    nb = lib().kh_selftest_bytes(k, k, k)
+    scr = torch.empty(nb + 256, dtype=torch.uint8, device=X.device)
+    base = (scr.data_ptr() + 255) // 256 * 256
+    st = lib().kh_selftest_svd(PREC[prec], k, _tptr(X.contiguous()), _tptr(S), _tptr(L), _tptr(Q),
+                               ctypes.c_void_p(base), nb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_svd")
+    return S, L, Q
 
 
 def launch_count():

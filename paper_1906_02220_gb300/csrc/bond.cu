@@ -500,16 +500,13 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     gemm_rm<double>(mT, mT, mT, Tm, false, Tm, true, Gt, st);               // Tm Tm^T
     double* colsc = dwork;
     double* Wd = dwork + 64;
-    if (mT <= jacobi_kmax<double>()) {
-        jacobi_eig<double>(Gt, mT, mT, 0, Wt, mT, 0, Lt, 0, 1, 60, 1e-15, nullptr, nullptr, st);
-        svd_init_kernel<double><<<grid_for(mT * D), 256, 0, st>>>(Wt, Lt, mT, D, A2, colsc, Wd);
-        KH_LAUNCHED();
-    } else {
-        cast<double, float>(Gt, Gtf, (long long)mT * mT, st);
-        jacobi_eig<float>(Gtf, mT, mT, 0, Wtf, mT, 0, Ltf, 0, 1, 60, 1e-7, nullptr, nullptr, st);
-        svd_init_kernel<float><<<grid_for(mT * D), 256, 0, st>>>(Wtf, Ltf, mT, D, A2, colsc, Wd);
-        KH_LAUNCHED();
-    }
+    // The start only seeds the ALS, which then converges to tolerance in
+    // FP64, so its eigenvectors are taken from the FP32 Jacobi (FP64 Jacobi
+    // on one SM is ~60x slower on this part).
+    cast<double, float>(Gt, Gtf, (long long)mT * mT, st);
+    jacobi_eig<float>(Gtf, mT, mT, 0, Wtf, mT, 0, Ltf, 0, 1, 60, 2e-6, nullptr, nullptr, st);
+    svd_init_kernel<float><<<grid_for(mT * D), 256, 0, st>>>(Wtf, Ltf, mT, D, A2, colsc, Wd);
+    KH_LAUNCHED();
     // B''[(sB,aB,d,l)][k] = sum_i Tm[i][.] Wd[i][k] colsc[k]
     gemm_rm<double>(mT, D, mT, Tm, true, Wd, false, B2, st, 1.0, 0.0, colsc);
     // initial cost with (A'', B'') from the start: B-side normal equations from A''

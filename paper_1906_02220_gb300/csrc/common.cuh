@@ -24,7 +24,8 @@ struct Error {
     do {                                                                              \
         cudaError_t _e = (call);                                                      \
         if (_e != cudaSuccess) {                                                      \
-            throw ::kh::Error{KH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)}; \
+            throw ::kh::Error{KH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e) + " at " + \
+                              __FILE__ + ":" + std::to_string(__LINE__)};                        \
         }                                                                             \
     } while (0)
 

@@ -14,6 +14,7 @@
 //   P = Q_{s+3}^T V S^-1/2, P~^T = Q_s U S^-1/2;
 //   C1 <- P^T (C1 E1), C4 <- (C4 E3) P~^T, E4 <- P^T (E4 T T) P~^T,
 //   each divided by its Frobenius norm (FP64).
+#define KH_JACOBI_KERNEL
 #include "engine.cuh"
 
 namespace kh {
@@ -73,6 +74,7 @@ void Engine<T>::layout(Carver& cv) {
         s.prev = cv.take<double>(4LL * d.chi);
         s.trunc = cv.take<double>(4);
         s.delta = cv.take<double>(1);
+        s.live = cv.take<int>(4LL * d.kk);
     }
     Cop = cv.take<T>(4 * chi2);
     Eop = cv.take<T>(4 * E1);
@@ -97,6 +99,11 @@ void Engine<T>::layout(Carver& cv) {
     W2 = cv.take<T>(kk * kk);
     L1 = cv.take<T>(kk);
     L2 = cv.take<T>(kk);
+    Xk = cv.take<T>(kk * kk);
+    Hk = cv.take<T>(kk * kk);
+    Lk = cv.take<T>(kk * kk);
+    Qk = cv.take<T>(kk * kk);
+    Sk = cv.take<T>(kk);
     isq = cv.take<T>(kk > d.chi ? kk : d.chi);
     P = cv.take<T>(n * d.chi);
     PtT = cv.take<T>(n * d.chi);
@@ -207,34 +214,24 @@ __global__ void gram_kernel(const T* __restrict__ Z, int n, int k, double* __res
 }
 
 template <typename T>
-static void gram(const T* Z, int n, int k, T* G, double* dtmp, cudaStream_t st) {
-    KH_CUDA(cudaMemsetAsync(dtmp, 0, sizeof(double) * k * k, st));
+static void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
+    KH_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * k * k, st));
     int rows_per = 128;
     dim3 grid((k + 15) / 16, (k + 15) / 16, (n + rows_per - 1) / rows_per);
-    gram_kernel<T><<<grid, 256, 0, st>>>(Z, n, k, dtmp, rows_per);
+    gram_kernel<T><<<grid, 256, 0, st>>>(Z, n, k, dG, rows_per);
     KH_LAUNCHED();
-    cast<double, T>(dtmp, G, (long long)k * k, st);
 }
 
-// isq[j] = lam_j > cut^2 lam_0 ? 1/sqrt(lam_j) : 0
+// spectrum (first chi values, zero-padded), S^-1/2 with cut-off, discarded weight
 template <typename T>
-__global__ void inv_sqrt_cut_kernel(const T* lam, int k, double cut, T* isq) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    double l0 = (double)lam[0], lj = (double)lam[j];
-    isq[j] = (l0 > 0.0 && lj > cut * cut * l0) ? (T)(1.0 / sqrt(lj)) : T(0);
-}
-
-// spectrum, S^-1/2 with cut-off, discarded weight
-template <typename T>
-__global__ void finalize_spectrum_kernel(const T* lam, int k, int chi, double cut, const double* normM2,
+__global__ void finalize_spectrum_kernel(const T* sv, int k, int chi, double cut, const double* normM2,
                                          double* spec, T* isq, double* trunc) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int nkeep = min(chi, k);
-    double s0 = sqrt(fmax((double)lam[0], 0.0));
+    double s0 = fmax((double)sv[0], 0.0);
     double kept = 0.0;
     for (int j = 0; j < chi; ++j) {
-        double s = (j < nkeep) ? sqrt(fmax((double)lam[j], 0.0)) : 0.0;
+        double s = (j < nkeep) ? fmax((double)sv[j], 0.0) : 0.0;
         if (j < nkeep) kept += s * s;
         bool keep = (s0 > 0.0) && (s > cut * s0);
         spec[j] = keep ? s : 0.0;
@@ -243,21 +240,6 @@ __global__ void finalize_spectrum_kernel(const T* lam, int k, int chi, double cu
     double tot = *normM2;
     double tr = (tot > 0.0) ? (tot - kept) / tot : 0.0;
     *trunc = tr > 0.0 ? tr : 0.0;
-}
-
-// warm subspace store; dead columns (lam_j <= cut^2 lam_0) re-randomised
-template <typename T>
-__global__ void store_warm_kernel(const T* Vo, const T* lam, int n, int k, double cut, T* Vw, uint64_t seed,
-                                  uint64_t stream) {
-    long long tot = (long long)n * k;
-    double l0 = (double)lam[0];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
-         i += (long long)gridDim.x * blockDim.x) {
-        int c = (int)(i % k);
-        double lc = (double)lam[c];
-        bool dead = !(l0 > 0.0 && lc > cut * cut * l0);
-        Vw[i] = dead ? (T)rnd_uniform(seed, stream, (uint64_t)i) : Vo[i];
-    }
 }
 
 template <typename T>
@@ -457,11 +439,73 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
     permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}, st);  // [w][dk][db][z][rk][rb]
 }
 
+// Orthonormal basis of the columns of Y (n x k) by two passes of the ordered
+// Cholesky-QR (cholqr_factor): dropped directions become zero columns.
+template <typename T>
+void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
+    (void)G; (void)W; (void)L;
+    const double tau = sizeof(T) == 8 ? 1e-12 : 1e-5;
+    double* dG = dscr + 8192;
+    // CholQR2: two passes of the ordered Cholesky-QR (the second pass restores
+    // orthogonality lost to the conditioning of the first)
+    gram<T>(Y, n, k, dG, st);
+    cholqr_factor<T>(dG, k, cfg.svd_cut, tau, Xk, st);
+    gemm_rm<T>(n, k, k, Y, false, Xk, false, Qt, st);
+    gram<T>(Qt, n, k, dG, st);
+    cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st);
+    gemm_rm<T>(n, k, k, Qt, false, Xk, false, Uo, st);
+}
+
+// Mask kernel for the warm subspace basis: live columns to Vl, dead columns
+// (live[c] == 0) to R as fresh random vectors.
+template <typename T>
+__global__ void warm_split_kernel(const T* Vw, const int* live, int n, int k, T* Vl, T* Rr, uint64_t seed,
+                                  uint64_t stream) {
+    long long tot = (long long)n * k;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        int c = (int)(i % k);
+        bool lv = live[c] != 0;
+        Vl[i] = lv ? Vw[i] : T(0);
+        Rr[i] = lv ? T(0) : (T)rnd_uniform(seed, stream, (uint64_t)i);
+    }
+}
+
+__global__ void live_mask_kernel(const void* sv, int is_double, int k, double cut, int* live) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double s0 = is_double ? ((const double*)sv)[0] : ((const float*)sv)[0];
+        double sc = is_double ? ((const double*)sv)[c] : ((const float*)sv)[c];
+        live[c] = (s0 > 0.0 && sc > cut * s0) ? 1 : 0;
+    }
+}
+
+// b <- a * alpha + b
+template <typename T>
+__global__ void axpby_kernel(const T* a, T* b, long long n, T alpha) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] += alpha * a[i];
+}
+
+template <typename T>
+__global__ void add_kernel(const T* a, T* b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] += a[i];
+}
+
+// Top-chi SVD of M = Mt^T, written into (Sk, V = Z1, U = Uf).
+//  full mode (n within the Jacobi limit): one-sided Jacobi SVD of Y = M V_w
+//    (V_w the previous right vectors, identity when cold): Y Q = L S, so
+//    M = L S (V_w Q)^T exactly; singular values to ~eps s_1 absolute.  V is
+//    kept orthonormal by one Newton-Schulz step V <- V (3 - V^T V)/2.
+//  subspace mode: Y = M V, U = orth(Y), Z = M^T U, V' = orth(Z), then the
+//    one-sided Jacobi SVD of H = V'^T Z gives M ~ (U Q) S (V' L)^T.  The warm
+//    basis keeps its live columns and replaces dead ones by random vectors
+//    projected off the live span, so new tail directions are picked up.
 template <typename T>
 void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
     const int n = dm.n, k = dm.kk, chi = dm.chi;
     const double cut = cfg.svd_cut;
-    const double jtol = sizeof(T) == 8 ? 1e-14 : 2e-6;   // ~sqrt(k) eps rounding floor
+    const double jtol = sizeof(T) == 8 ? 1e-14 : 2e-6;   // a few times the rounding floor sqrt(k) eps
     const T* Qa = Q[0];
     const T* Qb = Q[1];
     prof_begin(0);
@@ -471,42 +515,66 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
     KH_CUDA(cudaMemsetAsync(normM2, 0, sizeof(double), st));
     sumsq_kernel<T><<<grid_for((long long)n * n), 256, 0, st>>>(Mt, (long long)n * n, normM2);
     KH_LAUNCHED();
-    const T* Vin;
-    int q;
     uint64_t stream = (uint64_t)slot_id * 4 + dir;
+    T* Vw = sl.Vw + (long long)dir * n * k;
+    int* live = sl.live + dir * k;
     if (dm.full) {
-        identity_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(V0, n, k);
+        if (!sl.warm[dir]) {
+            identity_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(Vw, n, k);
+            KH_LAUNCHED();
+        }
+        gemm_rm<T>(n, n, n, Mt, true, Vw, false, Y1, st);                      // Y = M V_w
+        svd_jacobi<T>(Y1, n, Sk, Uf, Lk, cfg.jacobi_max_sweeps, jtol, 0.0, st);   // Y Q = L S
+        gemm_rm<T>(n, n, n, Vw, false, Lk, false, Z1, st);                     // V = V_w Q
+        gemm_rm<T>(n, n, n, Z1, true, Z1, false, Y1, st);                      // V^T V
+        gemm_rm<T>(n, n, n, Z1, false, Y1, false, Z2, st, T(-0.5), T(0));      // Newton-Schulz:
+        // V <- 1.5 V - V (V^T V)/2
+        axpby_kernel<T><<<grid_for((long long)n * n), 256, 0, st>>>(Z1, Z2, (long long)n * n, T(1.5));
         KH_LAUNCHED();
-        Vin = V0;
-        q = 1;
-    } else if (!sl.warm[dir]) {
-        rand_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(V0, (long long)n * k, cfg.seed,
-                                                                  stream * 1000003ULL + (rng_counter++));
-        KH_LAUNCHED();
-        Vin = V0;
-        q = cfg.svd_iters_cold;
+        KH_CUDA(cudaMemcpyAsync(Vw, Z2, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
+        KH_CUDA(cudaMemcpyAsync(Z1, Z2, sizeof(T) * (size_t)n * n, cudaMemcpyDeviceToDevice, st));
+        sl.warm[dir] = true;
     } else {
-        Vin = sl.Vw + (long long)dir * n * k;
-        q = cfg.svd_iters_warm;
-    }
-    double* dG = dscr + 8192;   // kk*kk doubles
-    for (int it = 0; it < q; ++it) {
-        gemm_rm<T>(n, k, n, Mt, true, Vin, false, Z1, st);                     // Z1 = M Vin
-        gram<T>(Z1, n, k, G1, dG, st);
-        jacobi_eig<T>(G1, k, k, 0, W1, k, 0, L1, 0, 1, cfg.jacobi_max_sweeps, jtol, nullptr, nullptr, st);
-        inv_sqrt_cut_kernel<T><<<(k + 127) / 128, 128, 0, st>>>(L1, k, cut, isq);
+        const T* Vin;
+        int q;
+        if (!sl.warm[dir]) {
+            rand_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(V0, (long long)n * k, cfg.seed,
+                                                                      stream * 1000003ULL + (rng_counter++));
+            KH_LAUNCHED();
+            orth(V0, n, k, U, G1, W1, L1);
+            Vin = U;
+            q = cfg.svd_iters_cold;
+        } else {
+            warm_split_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(
+                Vw, live, n, k, Vo, Z2, cfg.seed, stream * 1000003ULL + (rng_counter++));
+            KH_LAUNCHED();
+            for (int r = 0; r < 2; ++r) {                                       // R <- R - Vl (Vl^T R), twice
+                gemm_rm<T>(k, k, n, Vo, true, Z2, false, Xk, st);
+                gemm_rm<T>(n, k, k, Vo, false, Xk, false, Z2, st, T(-1), T(1));
+            }
+            add_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(Vo, Z2, (long long)n * k);
+            KH_LAUNCHED();
+            orth(Z2, n, k, V0, G1, W1, L1);
+            Vin = V0;
+            q = cfg.svd_iters_warm;
+        }
+        for (int it = 0; it < q; ++it) {
+            gemm_rm<T>(n, k, n, Mt, true, Vin, false, Z1, st);                 // Y = M V
+            orth(Z1, n, k, U, G1, W1, L1);                                     // U = orth(Y)
+            gemm_rm<T>(n, k, n, Mt, false, U, false, Z2, st);                  // Z = M^T U
+            orth(Z2, n, k, Vo, G2, W2, L2);                                    // V' = orth(Z)
+            Vin = Vo;
+        }
+        gemm_rm<T>(k, k, n, Vo, true, Z2, false, Hk, st);                      // H = V'^T Z
+        svd_jacobi<T>(Hk, k, Sk, Lk, Qk, cfg.jacobi_max_sweeps, jtol, 0.0, st);   // H Q = L S
+        gemm_rm<T>(n, k, k, Vo, false, Lk, false, Z1, st);                     // right vectors of M
+        gemm_rm<T>(n, k, k, U, false, Qk, false, Uf, st);                      // left vectors of M
+        KH_CUDA(cudaMemcpyAsync(Vw, Z1, sizeof(T) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
+        live_mask_kernel<<<1, 256, 0, st>>>(Sk, sizeof(T) == 8, k, cut, live);
         KH_LAUNCHED();
-        gemm_rm<T>(n, k, k, Z1, false, W1, false, U, st, T(1), T(0), isq);     // U = Z1 W1 L1^-1/2
-        gemm_rm<T>(n, k, n, Mt, false, U, false, Z2, st);                      // Z2 = M^T U
-        gram<T>(Z2, n, k, G2, dG, st);
-        jacobi_eig<T>(G2, k, k, 0, W2, k, 0, L2, 0, 1, cfg.jacobi_max_sweeps, jtol, nullptr, nullptr, st);
-        inv_sqrt_cut_kernel<T><<<(k + 127) / 128, 128, 0, st>>>(L2, k, cut, isq);
-        KH_LAUNCHED();
-        gemm_rm<T>(n, k, k, Z2, false, W2, false, Vo, st, T(1), T(0), isq);    // V = Z2 W2 L2^-1/2
-        gemm_rm<T>(n, k, k, U, false, W2, false, Uf, st);                      // U <- U W2
-        Vin = Vo;
+        sl.warm[dir] = true;
     }
-    finalize_spectrum_kernel<T><<<1, 32, 0, st>>>(L2, k, chi, cut, normM2, sl.spec + (long long)dir * chi, isq,
+    finalize_spectrum_kernel<T><<<1, 32, 0, st>>>(Sk, k, chi, cut, normM2, sl.spec + (long long)dir * chi, isq,
                                                   sl.trunc + dir);
     KH_LAUNCHED();
     const int nkeep = chi < k ? chi : k;
@@ -518,7 +586,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         GemmArgs<T> g;
         g.M = n; g.N = nkeep; g.K = n; g.batch = 1;
         g.A = Qb; g.sAm = 1; g.sAk = n; g.sAb = 0;
-        g.B = Vo; g.sBk = k; g.sBn = 1; g.sBb = 0;
+        g.B = Z1; g.sBk = k; g.sBn = 1; g.sBb = 0;
         g.C = P; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
         gemm<T>(g, st);
@@ -531,12 +599,6 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         g.C = PtT; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
         gemm<T>(g, st);
-    }
-    if (!dm.full) {
-        store_warm_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(
-            Vo, L2, n, k, cut, sl.Vw + (long long)dir * n * k, cfg.seed, stream * 1000003ULL + (rng_counter++));
-        KH_LAUNCHED();
-        sl.warm[dir] = true;
     }
 }
 
@@ -737,6 +799,55 @@ void Engine<T>::expval(int slot, const double* ops, int n_ops, double* vals) {
     KH_CUDA(cudaMemcpyAsync(vals, dvals, sizeof(double) * n_ops, cudaMemcpyDeviceToHost, st));
     KH_CUDA(cudaStreamSynchronize(st));
 }
+
+template <typename T>
+void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long long sW, T* evals, long long sE,
+                int batch, int max_sweeps, double tol, int* sweeps, const int* skip, cudaStream_t st) {
+    if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "jacobi: k beyond limit");
+    size_t sm = jacobi_smem<T>(k);
+    static size_t attr_set = 0;      // dynamic shared memory opted in so far (per T)
+    if (sm > 48 * 1024 && sm > attr_set) {
+        KH_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set = sm;
+    }
+    jacobi_eig_kernel<T><<<batch, kJacobiThreads, sm, st>>>(G, k, ldg, sG, W, ldw, sW, evals, sE, max_sweeps, tol,
+                                                           sweeps, skip);
+    KH_LAUNCHED();
+}
+template <typename T>
+void svd_jacobi(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double tol, double cut, cudaStream_t st) {
+    if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "svd_jacobi: k beyond limit");
+    size_t sm = jacobi_smem<T>(k);
+    static size_t attr_set = 0;
+    if (sm > 48 * 1024 && sm > attr_set) {
+        KH_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set = sm;
+    }
+    svd_jacobi_kernel<T><<<1, kJacobiThreads, sm, st>>>(X, k, sv, L, Qm, max_sweeps, tol, cut);
+    KH_LAUNCHED();
+}
+template <typename T>
+void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st) {
+    if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
+    size_t sm = (size_t)2 * k * k * sizeof(T);
+    static size_t attr_set = 0;
+    if (sm > 48 * 1024 && sm > attr_set) {
+        KH_CUDA(cudaFuncSetAttribute(cholqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set = sm;
+    }
+    cholqr_kernel<T><<<1, kJacobiThreads, sm, st>>>(dG, k, cut_abs, tau, X);
+    KH_LAUNCHED();
+}
+template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t);
+template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t);
+
+template void svd_jacobi<float>(const float*, int, float*, float*, float*, int, double, double, cudaStream_t);
+template void svd_jacobi<double>(const double*, int, double*, double*, double*, int, double, double, cudaStream_t);
+
+template void jacobi_eig<float>(const float*, int, int, long long, float*, int, long long, float*, long long, int, int,
+                                double, int*, const int*, cudaStream_t);
+template void jacobi_eig<double>(const double*, int, int, long long, double*, int, long long, double*, long long, int,
+                                 int, double, int*, const int*, cudaStream_t);
 
 template struct Engine<double>;
 template struct Engine<float>;

@@ -21,6 +21,7 @@ struct Slot {
     double* prev = nullptr;   // 4 x chi  normalised spectra of the previous sweep
     double* trunc = nullptr;  // 4        discarded weight per move
     double* delta = nullptr;  // 1        last sweep's spectrum change
+    int* live = nullptr;      // 4 x kk   live columns of the warm subspaces
     bool env_valid = false;   // environment initialised
     bool prev_valid = false;  // prev holds a sweep
     bool warm[4] = {false, false, false, false};
@@ -102,6 +103,7 @@ struct Engine : EngineBase {
     T *Q[2] = {nullptr, nullptr}, *Mt = nullptr;
     T *V0 = nullptr, *Z1 = nullptr, *U = nullptr, *Z2 = nullptr, *Vo = nullptr, *Uf = nullptr;
     T *G1 = nullptr, *W1 = nullptr, *L1 = nullptr, *G2 = nullptr, *W2 = nullptr, *L2 = nullptr;
+    T *Xk = nullptr, *Hk = nullptr, *Lk = nullptr, *Qk = nullptr, *Sk = nullptr;
     T *isq = nullptr, *P = nullptr, *PtT = nullptr, *C4E3 = nullptr;
     T *C1n = nullptr, *C4n = nullptr, *E4n = nullptr;
     double* dscr = nullptr;    // small FP64 scratch (norms etc.)
@@ -124,6 +126,7 @@ struct Engine : EngineBase {
     void corner(Slot<T>& sl, int frame, int which);
     void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out);
     void projector(Slot<T>& sl, int dir, int slot_id);
+    void orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L);
     void absorb(Slot<T>& sl, int s);
     void move(Slot<T>& sl, int s, int slot_id);
     void compute_metric(Slot<T>& sl, double* N_out);

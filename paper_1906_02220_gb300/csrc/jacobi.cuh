@@ -35,6 +35,7 @@ __device__ __forceinline__ void round_robin_pair(int r, int i, int kp, int& p, i
 // eigenvalue -1 (after scaling) and is dropped.  sweeps_out[b] (nullable)
 // records the sweeps used.  skip (nullable device flag): if *skip != 0 the
 // kernel returns immediately (used to freeze converged iterations on device).
+#ifdef KH_JACOBI_KERNEL
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads)
 jacobi_eig_kernel(const T* __restrict__ G, int k, int ldg, long long sG, T* __restrict__ W, int ldw,
@@ -81,16 +82,17 @@ jacobi_eig_kernel(const T* __restrict__ G, int k, int ldg, long long sG, T* __re
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         // convergence: off-diagonal Frobenius vs diagonal
-        double off = 0.0, dg = 0.0;
+        T offT = T(0), dgT = T(0);
         for (int e = tid; e < kp * kp; e += nt) {
             int i = e / kp, j = e % kp;
-            double v = (double)A[e];
-            if (i == j) dg += v * v; else off += v * v;
+            T v = A[e];
+            if (i == j) dgT = fma(v, v, dgT); else offT = fma(v, v, offT);
         }
         for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            dg += __shfl_xor_sync(0xffffffffu, dg, o);
+            offT += __shfl_xor_sync(0xffffffffu, offT, o);
+            dgT += __shfl_xor_sync(0xffffffffu, dgT, o);
         }
+        double off = (double)offT, dg = (double)dgT;
         if ((tid & 31) == 0) red[tid >> 5] = off;
         __syncthreads();
         if (tid == 0) {
@@ -168,6 +170,8 @@ jacobi_eig_kernel(const T* __restrict__ G, int k, int ldg, long long sG, T* __re
     }
 }
 
+#endif  // KH_JACOBI_KERNEL
+
 template <typename T>
 inline size_t jacobi_smem(int k) {
     int kp = (k + 1) & ~1;
@@ -177,22 +181,194 @@ inline size_t jacobi_smem(int k) {
 template <typename T>
 inline int jacobi_kmax() { return sizeof(T) == 8 ? 112 : 160; }
 
+// Launch wrapper, defined once (ctm.cu) for T = float, double.
 template <typename T>
-inline void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long long sW,
-                       T* evals, long long sE, int batch, int max_sweeps, double tol, int* sweeps,
-                       const int* skip, cudaStream_t st) {
-    if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "jacobi: k beyond limit");
-    size_t sm = jacobi_smem<T>(k);
-    static bool attr_set[2] = {false, false};
-    int ti = sizeof(T) == 8 ? 1 : 0;
-    if (!attr_set[ti]) {
-        KH_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(227 * 1024)));
-        attr_set[ti] = true;
+void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long long sW, T* evals, long long sE,
+                int batch, int max_sweeps, double tol, int* sweeps, const int* skip, cudaStream_t st);
+
+
+// One-sided (Hestenes) Jacobi SVD of a small dense k x k matrix X, one CTA:
+// columns of X are rotated pairwise (round-robin ordering, one warp per pair)
+// until mutually orthogonal; then X Q = L S with s_j = |column j|.  Singular
+// values come out with absolute error ~ eps |X| (no squaring of the condition
+// number, unlike a Gram-matrix eigensolve).  Outputs sorted descending:
+// s (k), L (k x k, column j = X q_j / s_j, zero when s_j <= cut s_0), Q (k x k).
+template <typename T>
+void svd_jacobi(const T* X, int k, T* s, T* L, T* Q, int max_sweeps, double tol, double cut, cudaStream_t st);
+
+#ifdef KH_JACOBI_KERNEL
+template <typename T>
+__global__ void __launch_bounds__(kJacobiThreads)
+svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __restrict__ L_out,
+                  T* __restrict__ Q_out, int max_sweeps, double tol, double cut) {
+    extern __shared__ unsigned char smem_raw[];
+    const int kp = (k + 1) & ~1;
+    T* Xc = reinterpret_cast<T*>(smem_raw);   // column-major: Xc[c * kp + r]
+    T* Qc = Xc + kp * kp;
+    __shared__ int s_rot;
+    __shared__ double s_norm[160];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int e = tid; e < kp * kp; e += nt) {
+        int c = e / kp, r = e % kp;
+        Xc[e] = (r < k && c < k) ? Xin[(long long)r * k + c] : T(0);
+        Qc[e] = (r == c) ? T(1) : T(0);
     }
-    jacobi_eig_kernel<T><<<batch, kJacobiThreads, sm, st>>>(G, k, ldg, sG, W, ldw, sW, evals, sE,
-                                                           max_sweeps, tol, sweeps, skip);
-    KH_LAUNCHED();
+    __syncthreads();
+    for (int sw = 0; sw < max_sweeps; ++sw) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int r = 0; r < kp - 1; ++r) {
+            for (int i = warp; i < kp / 2; i += nw) {
+                int p, q;
+                round_robin_pair<T>(r, i, kp, p, q);
+                T* xp = Xc + p * kp;
+                T* xq = Xc + q * kp;
+                T a = T(0), b = T(0), g = T(0);
+                for (int row = lane; row < kp; row += 32) {
+                    T u = xp[row], v = xq[row];
+                    a = fma(u, u, a); b = fma(v, v, b); g = fma(u, v, g);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                }
+                // converged pair (sqrt(a) sqrt(b), not sqrt(a b): no underflow for tiny columns)
+                if (g == T(0) || fabs(g) <= (T)tol * (sqrt(a) * sqrt(b))) continue;   // warp-uniform
+                T zeta = (b - a) / (T(2) * g);
+                T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                T cT = T(1) / sqrt(T(1) + t * t), sT = cT * t;
+                T* qp = Qc + p * kp;
+                T* qq = Qc + q * kp;
+                for (int row = lane; row < kp; row += 32) {
+                    T u = xp[row], v = xq[row];
+                    xp[row] = cT * u - sT * v;
+                    xq[row] = sT * u + cT * v;
+                    T qu = qp[row], qv = qq[row];
+                    qp[row] = cT * qu - sT * qv;
+                    qq[row] = sT * qu + cT * qv;
+                }
+                if (lane == 0) atomicAdd(&s_rot, 1);
+            }
+            __syncthreads();
+        }
+        if (s_rot == 0) break;
+        __syncthreads();
+    }
+    // column norms, ranks, outputs
+    for (int c = warp; c < kp; c += nw) {
+        T a = T(0);
+        for (int row = lane; row < kp; row += 32) { T u = Xc[c * kp + row]; a = fma(u, u, a); }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) s_norm[c] = (c < k) ? (double)sqrt(a) : -1.0;
+    }
+    __syncthreads();
+    double smax = 0.0;
+    for (int c = 0; c < k; ++c) smax = fmax(smax, s_norm[c]);
+    for (int c = warp; c < k; c += nw) {
+        double sc = s_norm[c];
+        int rank = 0;
+        for (int j = 0; j < k; ++j) rank += (s_norm[j] > sc) || (s_norm[j] == sc && j < c);
+        double inv = (smax > 0.0 && sc > cut * smax) ? 1.0 / sc : 0.0;
+        for (int row = lane; row < k; row += 32) {
+            L_out[(long long)row * k + rank] = (T)((double)Xc[c * kp + row] * inv);
+            Q_out[(long long)row * k + rank] = Qc[c * kp + row];
+        }
+        if (lane == 0) s_out[rank] = (T)sc;
+    }
 }
+#endif  // KH_JACOBI_KERNEL
+
+
+// Ordered Cholesky-QR factor for orthonormalising the columns of Y (n x k)
+// from its FP64 Gram dG: columns sorted by norm (largest, most trusted,
+// first), scaled to unit norm, dead columns (norm <= cut_abs max) and
+// pivots <= tau dropped; X (k x k) such that Q = Y X has orthonormal columns
+// (in sorted order, dropped ones zero).  Unlike a symmetric (Loewdin)
+// orthogonalisation, a weak column nearly parallel to a strong one never
+// rotates the strong one.
+template <typename T>
+void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st);
+
+#ifdef KH_JACOBI_KERNEL
+template <typename T>
+__global__ void __launch_bounds__(kJacobiThreads)
+cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X) {
+    extern __shared__ unsigned char smem_raw[];
+    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x k, row-major
+    T* Li = Lm + k * k;
+    __shared__ double s_inv[160];
+    __shared__ int s_perm[160];
+    __shared__ int s_keep[160];
+    __shared__ double s_max;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (tid == 0) {
+        double m = 0.0;
+        for (int j = 0; j < k; ++j) m = fmax(m, G[(long long)j * k + j]);
+        s_max = sqrt(fmax(m, 0.0));
+    }
+    __syncthreads();
+    for (int j = tid; j < k; j += nt) {
+        double nj = sqrt(fmax(G[(long long)j * k + j], 0.0));
+        s_inv[j] = (s_max > 0.0 && nj > cut_abs * s_max) ? 1.0 / nj : 0.0;
+        int rank = 0;
+        for (int i = 0; i < k; ++i) {
+            double ni = G[(long long)i * k + i];
+            double nn = G[(long long)j * k + j];
+            rank += (ni > nn) || (ni == nn && i < j);
+        }
+        s_perm[rank] = j;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {
+        int a = e / k, b = e % k;
+        int pa = s_perm[a], pb = s_perm[b];
+        Lm[e] = (T)(G[(long long)pa * k + pb] * s_inv[pa] * s_inv[pb]);
+        Li[e] = T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < k; ++j) {
+        T d = Lm[j * k + j];
+        bool keep = (double)d > tau;                      // same value in every thread
+        if (keep) {
+            T ljj = sqrt(d);
+            for (int i = j + 1 + tid; i < k; i += nt) Lm[i * k + j] /= ljj;
+            __syncthreads();
+            if (tid == 0) { Lm[j * k + j] = ljj; s_keep[j] = 1; }
+            int rows = k - j - 1;
+            for (int e = tid; e < rows * rows; e += nt) {
+                int i = j + 1 + e / rows, c = j + 1 + e % rows;
+                if (c <= i) Lm[i * k + c] -= Lm[i * k + j] * Lm[c * k + j];
+            }
+        } else {
+            __syncthreads();
+            for (int i = j + tid; i < k; i += nt) Lm[i * k + j] = T(0);
+            if (tid == 0) s_keep[j] = 0;
+        }
+        __syncthreads();
+    }
+    // Li = L^-1 on the kept index set, one warp per column
+    for (int j = warp; j < k; j += nw) {
+        if (!s_keep[j]) continue;
+        if (lane == 0) Li[j * k + j] = T(1) / Lm[j * k + j];
+        __syncwarp();
+        for (int i = j + 1; i < k; ++i) {
+            if (!s_keep[i]) continue;
+            T sum = T(0);
+            for (int m = j + lane; m < i; m += 32) sum = fma(Lm[i * k + m], Li[m * k + j], sum);
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) Li[i * k + j] = -sum / Lm[i * k + i];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // X[perm a][b] = inv[perm a] * Li[b][a]   (Q = Y_s L^-T)
+    for (int e = tid; e < k * k; e += nt) {
+        int a = e / k, b = e % k;
+        int pa = s_perm[a];
+        X[(long long)pa * k + b] = (T)(s_inv[pa] * (double)Li[b * k + a]);
+    }
+}
+#endif  // KH_JACOBI_KERNEL
 
 }  // namespace kh

@@ -1,0 +1,103 @@
+// Kernel self-test entry points (test hooks; the paper has no counterpart):
+// run one library kernel on caller-provided device data so that tests can
+// pin it directly against a host reference.
+#include "engine.cuh"
+
+namespace {
+
+template <typename T>
+void run_gemm(int M, int N, int K, const double* A, const double* B, double* C, void* scratch, size_t bytes,
+              cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    T* a = cv.take<T>((size_t)M * K);
+    T* b = cv.take<T>((size_t)K * N);
+    T* c = cv.take<T>((size_t)M * N);
+    kh::cast<double, T>(A, a, (long long)M * K, st);
+    kh::cast<double, T>(B, b, (long long)K * N, st);
+    kh::gemm_rm<T>(M, N, K, a, false, b, false, c, st);
+    kh::cast<T, double>(c, C, (long long)M * N, st);
+}
+
+template <typename T>
+void run_eig(int k, const double* G, double* W, double* E, void* scratch, size_t bytes, cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    T* g = cv.take<T>((size_t)k * k);
+    T* w = cv.take<T>((size_t)k * k);
+    T* e = cv.take<T>((size_t)k);
+    kh::cast<double, T>(G, g, (long long)k * k, st);
+    kh::jacobi_eig<T>(g, k, k, 0, w, k, 0, e, 0, 1, 60, sizeof(T) == 8 ? 1e-14 : 2e-6, nullptr, nullptr, st);
+    kh::cast<T, double>(w, W, (long long)k * k, st);
+    kh::cast<T, double>(e, E, (long long)k, st);
+}
+
+template <typename T>
+void run_svd(int k, const double* X, double* S, double* L, double* Qm, void* scratch, size_t bytes, cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    T* x = cv.take<T>((size_t)k * k);
+    T* l = cv.take<T>((size_t)k * k);
+    T* q = cv.take<T>((size_t)k * k);
+    T* sv = cv.take<T>((size_t)k);
+    kh::cast<double, T>(X, x, (long long)k * k, st);
+    kh::svd_jacobi<T>(x, k, sv, l, q, 60, sizeof(T) == 8 ? 1e-15 : 1e-6, 0.0, st);
+    kh::cast<T, double>(sv, S, (long long)k, st);
+    kh::cast<T, double>(l, L, (long long)k * k, st);
+    kh::cast<T, double>(q, Qm, (long long)k * k, st);
+}
+
+template <typename F>
+kh_status run(F&& f) {
+    try {
+        f();
+        return KH_OK;
+    } catch (const kh::Error& e) {
+        fprintf(stderr, "eefu selftest: %s\n", e.msg.c_str());
+        return e.st;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kh_selftest_bytes(int M, int N, int K) {
+    return 8 * ((size_t)M * K + (size_t)K * N + (size_t)M * N) * 2 + 4096;
+}
+
+kh_status kh_selftest_gemm(int prec, int M, int N, int K, const double* A, const double* B, double* C,
+                           void* scratch, size_t bytes, void* stream) {
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || !scratch) return KH_EINVAL;
+    if (bytes < kh_selftest_bytes(M, N, K)) return KH_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] {
+        if (prec == KH_FP64) run_gemm<double>(M, N, K, A, B, C, scratch, bytes, st);
+        else if (prec == KH_FP32) run_gemm<float>(M, N, K, A, B, C, scratch, bytes, st);
+        else kh::fail(KH_EINVAL, "precision not built");
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+kh_status kh_selftest_symeig(int prec, int k, const double* G, double* W, double* E, void* scratch, size_t bytes,
+                             void* stream) {
+    if (k < 1 || !G || !W || !E || !scratch) return KH_EINVAL;
+    if (bytes < kh_selftest_bytes(k, k, k)) return KH_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] {
+        if (prec == KH_FP64) run_eig<double>(k, G, W, E, scratch, bytes, st);
+        else run_eig<float>(k, G, W, E, scratch, bytes, st);
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+kh_status kh_selftest_svd(int prec, int k, const double* X, double* S, double* L, double* Qm, void* scratch,
+                          size_t bytes, void* stream) {
+    if (k < 1 || !X || !S || !L || !Qm || !scratch) return KH_EINVAL;
+    if (bytes < kh_selftest_bytes(k, k, k)) return KH_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] {
+        if (prec == KH_FP64) run_svd<double>(k, X, S, L, Qm, scratch, bytes, st);
+        else run_svd<float>(k, X, S, L, Qm, scratch, bytes, st);
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+"""Kernel-level GPU tests through the self-test entry points: the contraction
+GEMM (every precision built) and the Jacobi eigensolver against numpy in
+float64, on ragged shapes that span several tiles."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1906_02220_gb300 as pkg
+    return pkg
+
+
+GEMM_TOL = {"fp64": 1e-13, "fp32": 3e-6}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (16, 16, 16), (17, 33, 65), (128, 16, 256), (16, 128, 40),
+                                   (300, 257, 129), (1024, 96, 1024)])
+def test_gemm_against_numpy(g, prec, M, N, K):
+    import torch
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    C = g.selftest_gemm(torch.as_tensor(A, device="cuda:0"), torch.as_tensor(B, device="cuda:0"), prec).cpu().numpy()
+    ref = A @ B
+    scale = np.sqrt(K) * np.abs(A).max() * np.abs(B).max()
+    assert np.abs(C - ref).max() <= GEMM_TOL[prec] * scale
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1, 2, 7, 24, 64, 81, 112])
+def test_jacobi_symeig(g, prec, k):
+    import torch
+    rng = np.random.default_rng(k)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    lam = np.sort(np.abs(rng.standard_normal(k)) * np.logspace(0, -6, k))[::-1]
+    lam[k // 2:] = 0.0 if k > 3 else lam[k // 2:]          # a null block
+    G = (Q * lam) @ Q.T
+    G = 0.5 * (G + G.T)
+    E, W = g.selftest_symeig(torch.as_tensor(G, device="cuda:0"), prec)
+    E, W = E.cpu().numpy(), W.cpu().numpy()
+    eps = 1e-15 if prec == "fp64" else 3e-7
+    ref = np.sort(np.linalg.eigvalsh(G))[::-1]
+    assert np.all(np.diff(E) <= 0)
+    assert np.abs(E - ref).max() <= 50 * eps * k * lam.max()
+    assert np.abs(W.T @ W - np.eye(k)).max() <= 50 * eps * k
+    assert np.abs(W @ np.diag(E) @ W.T - G).max() <= 50 * eps * k * lam.max()
+
+
+def test_jacobi_near_diagonal_relative_accuracy(g):
+    """Warm-start regime: a near-diagonal Gram matrix with a 1e-10 dynamic range
+    keeps every eigenvalue to high relative accuracy, even in FP32."""
+    import torch
+    k = 80
+    rng = np.random.default_rng(3)
+    d = np.logspace(0, -10, k)
+    G = np.diag(d) + 1e-4 * np.sqrt(np.outer(d, d)) * rng.standard_normal((k, k))
+    G = 0.5 * (G + G.T)
+    ref = np.sort(np.linalg.eigvalsh(G))[::-1]
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        E, W = g.selftest_symeig(torch.as_tensor(G, device="cuda:0"), prec)
+        assert np.max(np.abs(E.cpu().numpy() - ref) / ref) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,decades", [(1, 0), (6, 3), (24, 9), (80, 12), (113, 6)])
+def test_one_sided_jacobi_svd(g, prec, k, decades):
+    """Singular values to absolute accuracy ~eps * s_1 (no squaring), also for
+    a matrix with a null block; X Q = L S and Q orthogonal."""
+    import torch
+    if prec == "fp64" and k > 112:
+        pytest.skip("beyond the FP64 Jacobi limit")
+    rng = np.random.default_rng(k + decades)
+    U, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    s = np.logspace(0, -decades, k)
+    s[(3 * k) // 4:] = 0.0 if k > 4 else s[(3 * k) // 4:]
+    X = (U * s) @ V.T
+    S, L, Q = (t.cpu().numpy() for t in g.selftest_svd(torch.as_tensor(X, device="cuda:0"), prec))
+    eps = 2.3e-16 if prec == "fp64" else 1.2e-7
+    ref = np.linalg.svd(X, compute_uv=False)
+    assert np.abs(S - ref).max() <= 30 * eps * k * s[0]
+    assert np.abs(Q.T @ Q - np.eye(k)).max() <= 30 * eps * k
+    assert np.abs(X @ Q - L * S).max() <= 30 * eps * k * s[0]

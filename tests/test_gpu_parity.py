@@ -40,7 +40,7 @@ def _nrm(x):
 def _oracle_ctm(T, chi, sweeps, edge=None):
     a = ctmrg.double_tensor(T)
     env = ctmrg.init_env(chi, T.shape[1], edge)
-    specs = None
+    specs, truncs = None, None
     for _ in range(sweeps):
         specs, truncs = ctmrg.sweep(env, a)
     return env, specs, truncs
@@ -96,7 +96,9 @@ def test_ctm_metric_and_spectra_match_oracle(g, prec, D, chi):
         s = s.cpu().numpy()
         ref = info["spectra"][d]
         assert np.abs(_nrm(s) - _nrm(ref)).max() < tol * 10
-        assert abs(tr - info["trunc"][d]) < max(1e-12, 1e-3 * info["trunc"][d]) + (0 if prec == "fp64" else 1e-6)
+        # the discarded weight is (|M|^2 - sum_kept s^2)/|M|^2: resolvable down to
+        # ~k eps of the arithmetic (FP64 1e-12, FP32 ~1e-5)
+        assert abs(tr - info["trunc"][d]) < max(1e-12, 1e-3 * info["trunc"][d]) + (0 if prec == "fp64" else 1e-5)
 
 
 def test_ctm_single_sweep_is_deterministic_and_exact_for_small_n(g):
@@ -110,10 +112,11 @@ def test_ctm_single_sweep_is_deterministic_and_exact_for_small_n(g):
     ctx.ctm_sweep(0, 1)
     N = ctx.ctm_metric(0).cpu().numpy()
     assert np.abs(_nrm(N) - _nrm(ctmrg.metric(env, D))).max() < 1e-12
-    for d in range(4):
-        s, tr = ctx.ctm_projectors(0, d)
-        assert np.abs(s.cpu().numpy() - specs[d]).max() < 1e-12 * max(1.0, specs[d][0])
-        assert abs(tr - truncs[d]) < 1e-12
+    got = [ctx.ctm_projectors(0, d) for d in range(4)]
+    errs = [np.abs(s.cpu().numpy() - specs[d]).max() for d, (s, tr) in enumerate(got)]
+    terrs = [abs(tr - truncs[d]) for d, (s, tr) in enumerate(got)]
+    assert max(errs) < 1e-12 * max(1.0, specs[0][0]), errs
+    assert max(terrs) < 1e-12, terrs
 
 
 def test_edge_cases(g):
