@@ -158,7 +158,8 @@ def peaks():
 
 def roofline_for(prec, prof, pk, pk_src):
     """Dominant timed kernel category -> achieved vs peak."""
-    cat = max(prof, key=lambda k: prof[k]["ms"])
+    kernels = {k: v for k, v in prof.items() if v["flops"] > 0}
+    cat = max(kernels, key=lambda k: kernels[k]["ms"])
     c = prof[cat]
     if c["launches"] == 0 or c["ms"] <= 0:
         return None, cat

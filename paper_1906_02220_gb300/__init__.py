@@ -240,11 +240,11 @@ class Context:
         self._check(lib().kh_profile(self._ctx, 1, None))
 
     def profile_stop(self):
-        out = np.zeros(6)
+        out = np.zeros(21)
         o, op = _dptr(out)
         self._check(lib().kh_profile(self._ctx, 0, op))
-        names = ["half_system_product", "site_layer"]
-        return {names[k]: dict(launches=int(o[3 * k]), ms=o[3 * k + 1], flops=o[3 * k + 2]) for k in range(2)}
+        names = ["half_system_product", "site_layer", "corners", "projector_svd", "absorb", "metric", "als_gauge"]
+        return {names[k]: dict(launches=int(o[3 * k]), ms=o[3 * k + 1], flops=o[3 * k + 2]) for k in range(7)}
 
     # ---- state
     def set_state(self, A, B):

@@ -137,8 +137,7 @@ kh_status kh_create(kh_ctx** out, const kh_config* c, void* ws, size_t bytes, vo
         if ((uintptr_t)ws % 256 != 0) kh::fail(KH_EINVAL, "workspace must be 256-byte aligned");
         size_t need = kh_workspace_bytes(c);
         if (bytes < need) kh::fail(KH_ENOMEM, "workspace smaller than kh_workspace_bytes()");
-        if (c->prec != KH_FP64 && c->prec != KH_FP32)
-            kh::fail(KH_EINVAL, "precision not built in this library version");
+        if (c->prec == KH_BF16) kh::fail(KH_EINVAL, "precision not built in this library version");
         cudaStream_t st = (cudaStream_t)stream;
         if (c->prec == KH_FP64) ctx->eng = new kh::Engine<double>(*c, ws, bytes, st);
         else ctx->eng = new kh::Engine<float>(*c, ws, bytes, st);
@@ -322,7 +321,7 @@ kh_status kh_profile(kh_ctx* ctx, int enable, double* out) {
         }
         KH_CUDA(cudaStreamSynchronize(e->st));
         e->prof_on = false;
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kh::EngineBase::kProfCats; ++k) {
             double ms = 0.0;
             for (int i = 0; i < e->prof[k].used; ++i) {
                 float t = 0.f;

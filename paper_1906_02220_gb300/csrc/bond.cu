@@ -567,8 +567,10 @@ void Engine<T>::apply_gate(int gamma, const double* gate, int mx, int mn, double
     int sw = sweep(gamma, mx, mn, tol, &delta);
     compute_metric(slots[gamma], N);
     double rel = 0.0;
+    prof_begin(6);
     int it = als_run(gamma, &rel);
     gauge_and_store(gamma);
+    prof_end(6, 0.0);
     if (info) {
         double tr[4];
         KH_CUDA(cudaMemcpyAsync(tr, slots[gamma].trunc, sizeof(tr), cudaMemcpyDeviceToHost, st));

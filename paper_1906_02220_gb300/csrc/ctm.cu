@@ -139,6 +139,7 @@ void Engine<T>::layout(Carver& cv) {
     cost = cv.take<double>(64);
     dwork = cv.take<double>(4 * E1 + 16LL * d.D4 + 64);
     flags = cv.take<int>(64);
+    tc_err = cv.take<int>(64);
 }
 
 template <typename T>
@@ -165,6 +166,7 @@ Engine<T>::Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s) {
     cfg = c;
     st = s;
     dm = make_dims(c, sizeof(T) == 8);
+    tc_npass = (c.prec == KH_TF32) ? 1 : (c.prec == KH_TF32X3 ? 3 : 0);
     Carver cv(ws, bytes);
     layout(cv);
     KH_CUDA(cudaMemsetAsync(ws, 0, cv.off, st));
@@ -436,7 +438,10 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
     gemm_rm<T>(chi * d2, d2 * chi, chi, E4, false, X, false, Y1, st);        // [(w,lk,lb)][(uk,ub,z)]
     permute<T, T>(Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3}, st);  // [w][z][lb][ub][lk][uk]
     site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt);  // [w][z][rk][dk][rb][db]
-    permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}, st);  // [w][dk][db][z][rk][rb]
+    if (which == 0 && tc_npass)   // Q_s^T [(z,rk,rb)][(w,dk,db)]: K-major operand of Mt = Q_{s+3} Q_s
+        permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {1, 2, 4, 0, 3, 5}, st);
+    else
+        permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}, st);  // [w][dk][db][z][rk][rb]
 }
 
 // Orthonormal basis of the columns of Y (n x k) by two passes of the ordered
@@ -454,6 +459,29 @@ void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
     gram<T>(Qt, n, k, dG, st);
     cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st);
     gemm_rm<T>(n, k, k, Qt, false, Xk, false, Uo, st);
+}
+
+// Half-system product Mt = Q_{s+3} Q_s (= M^T), the largest single GEMM of a
+// move: on tensor cores (TF32 or 3xTF32) when the precision asks for it.
+template <typename T>
+void Engine<T>::half_system_product(int n) {
+    prof_begin(0);
+    if (tc_npass && sizeof(T) == 4 && n % 4 == 0) {     // TMA rows must be 16-byte multiples
+        const float* Qb = (const float*)Q[1];
+        const float* QaT = (const float*)Q[0];
+        TcOperand a{Qb, nullptr, n}, b{QaT, nullptr, n};
+        if (tc_npass == 3) {
+            float *ah = (float*)mup, *al = (float*)mdn, *bh = (float*)mupp, *bl = (float*)mdnp;
+            tc_split(Qb, ah, al, (long long)n * n, st);
+            tc_split(QaT, bh, bl, (long long)n * n, st);
+            a = TcOperand{ah, al, n};
+            b = TcOperand{bh, bl, n};
+        }
+        tc_gemm(a, b, (float*)Mt, n, n, n, n, 1.f, 0.f, nullptr, tc_npass, tc_err, st);
+    } else {
+        gemm_rm<T>(n, n, n, Q[1], false, Q[0], false, Mt, st);
+    }
+    prof_end(0, 2.0 * n * (double)n * n);
 }
 
 // Mask kernel for the warm subspace basis: live columns to Vl, dead columns
@@ -508,9 +536,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
     const double jtol = sizeof(T) == 8 ? 1e-14 : 2e-6;   // a few times the rounding floor sqrt(k) eps
     const T* Qa = Q[0];
     const T* Qb = Q[1];
-    prof_begin(0);
-    gemm_rm<T>(n, n, n, Qb, false, Qa, false, Mt, st);                        // Mt = Qb Qa = M^T
-    prof_end(0, 2.0 * n * (double)n * n);
+    half_system_product(n);
     double* normM2 = dscr + 8000;
     KH_CUDA(cudaMemsetAsync(normM2, 0, sizeof(double), st));
     sumsq_kernel<T><<<grid_for((long long)n * n), 256, 0, st>>>(Mt, (long long)n * n, normM2);
@@ -591,10 +617,10 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
         gemm<T>(g, st);
     }
-    {   // P~^T = Qa U S^-1/2
+    {   // P~^T = Qa U S^-1/2  (Qa stored transposed when tensor cores are used)
         GemmArgs<T> g;
         g.M = n; g.N = nkeep; g.K = n; g.batch = 1;
-        g.A = Qa; g.sAm = n; g.sAk = 1; g.sAb = 0;
+        g.A = Qa; g.sAm = tc_npass ? 1 : n; g.sAk = tc_npass ? n : 1; g.sAb = 0;
         g.B = Uf; g.sBk = k; g.sBn = 1; g.sBb = 0;
         g.C = PtT; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
@@ -653,10 +679,16 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
 
 template <typename T>
 void Engine<T>::move(Slot<T>& sl, int s, int slot_id) {
+    prof_begin(2);
     corner(sl, s, 0);
     corner(sl, (s + 3) & 3, 1);
+    prof_end(2, 0.0);
+    prof_begin(3);
     projector(sl, s, slot_id);
+    prof_end(3, 0.0);
+    prof_begin(4);
     absorb(sl, s);
+    prof_end(4, 0.0);
 }
 
 template <typename T>
@@ -675,7 +707,10 @@ int Engine<T>::sweep(int slot, int max_sweeps, int min_sweeps, double tol, doubl
         done = it;
         if (tol >= 0.0) {
             KH_CUDA(cudaMemcpyAsync(&delta, sl.delta, sizeof(double), cudaMemcpyDeviceToHost, st));
+            int terr = 0;
+            if (tc_npass) KH_CUDA(cudaMemcpyAsync(&terr, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
             KH_CUDA(cudaStreamSynchronize(st));
+            if (terr) fail(KH_ETIMEOUT, "tensor-core kernel wait timed out (flag " + std::to_string(terr) + ")");
             if (!(delta == delta)) fail(KH_ENUMERIC, "NaN in CTM spectra");
             if (it >= min_sweeps && delta < tol) break;
         }
@@ -710,6 +745,7 @@ void Engine<T>::get_env(int slot, double* C, double* E) {
 
 template <typename T>
 void Engine<T>::compute_metric(Slot<T>& sl, double* N_out) {
+    prof_begin(5);
     const int chi = dm.chi, d2 = dm.d2, D = dm.D;
     const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
     refresh_operands(sl);
@@ -727,6 +763,7 @@ void Engine<T>::compute_metric(Slot<T>& sl, double* N_out) {
     permute<T, double>(mN4, N_out, {D, D, D, D, D, D, D, D}, {6, 0, 2, 4, 7, 1, 3, 5}, st);
     symmetrize_kernel<<<grid_for((long long)dm.D4 * dm.D4), 256, 0, st>>>(N_out, dm.D4);
     KH_LAUNCHED();
+    prof_end(5, 0.0);
 }
 
 template <typename T>

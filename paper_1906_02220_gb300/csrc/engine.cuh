@@ -36,7 +36,9 @@ struct Dims {
 // ------------------------------------------------------------------ engine
 
 // CUDA-event timing of kernel categories (bench instrumentation only):
-// 0 = half-system product Mt = Q_{s+3} Q_s, 1 = two-layer site contractions.
+// 0 = half-system product Mt = Q_{s+3} Q_s, 1 = two-layer site contractions,
+// 2 = enlarged corners (all), 3 = projector SVD (excluding Mt),
+// 4 = absorption, 5 = environment metric, 6 = ALS + gauge.
 struct ProfCat {
     std::vector<cudaEvent_t> a, b;
     int used = 0;
@@ -49,7 +51,8 @@ struct EngineBase {
             for (size_t i = 0; i < c.a.size(); ++i) { cudaEventDestroy(c.a[i]); cudaEventDestroy(c.b[i]); }
     }
     bool prof_on = false;
-    ProfCat prof[2];
+    static constexpr int kProfCats = 7;
+    ProfCat prof[kProfCats];
     void prof_begin(int cat) {
         if (!prof_on) return;
         ProfCat& c = prof[cat];
@@ -114,7 +117,10 @@ struct Engine : EngineBase {
            *Xmat = nullptr, *cost = nullptr, *dwork = nullptr;
     float *Gtf = nullptr, *Wtf = nullptr, *Ltf = nullptr;
     int* flags = nullptr;
+    int* tc_err = nullptr;     // tensor-core kernels' time-out flag
+    int tc_npass = 0;          // 0: CUDA-core GEMMs; 1: TF32; 3: 3xTF32
     unsigned long long rng_counter = 0;
+    void half_system_product(int n);
 
     Engine() {}
     Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s);
@@ -153,6 +159,18 @@ struct Engine : EngineBase {
     void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                      double* out) override;
 };
+
+// Tensor-core GEMM (tcgen05.cu): C = alpha colscale (A B^T) + beta C with A
+// (M x K) and B (N x K) row-major FP32 read as TF32; npass = 3 uses the
+// hi/lo split operands (lo may be null for npass = 1).
+struct TcOperand {
+    const float* hi;
+    const float* lo;
+    long long ld;
+};
+void tc_gemm(const TcOperand& A, const TcOperand& B, float* C, int M, int N, int K, long long ldc, float alpha,
+             float beta, const float* colscale, int npass, int* err, cudaStream_t st);
+void tc_split(const float* x, float* hi, float* lo, long long n, cudaStream_t st);
 
 Dims make_dims(const kh_config& c, bool fp64);
 void validate(const kh_config& c);

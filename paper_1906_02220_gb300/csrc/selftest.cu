@@ -18,6 +18,36 @@ void run_gemm(int M, int N, int K, const double* A, const double* B, double* C, 
     kh::cast<T, double>(c, C, (long long)M * N, st);
 }
 
+// tensor-core path: B^T made K-major by a permutation, optional hi/lo split
+void run_tc_gemm(int npass, int M, int N, int K, const double* A, const double* B, double* C, void* scratch,
+                 size_t bytes, cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    float* a = cv.take<float>((size_t)M * K);
+    float* bt = cv.take<float>((size_t)K * N);
+    float* c = cv.take<float>((size_t)M * N);
+    float* ah = cv.take<float>((size_t)M * K);
+    float* al = cv.take<float>((size_t)M * K);
+    float* bh = cv.take<float>((size_t)K * N);
+    float* bl = cv.take<float>((size_t)K * N);
+    int* err = cv.take<int>(64);
+    KH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    kh::cast<double, float>(A, a, (long long)M * K, st);
+    kh::permute<double, float>(B, bt, {K, N}, {1, 0}, st);
+    kh::TcOperand oa{a, nullptr, K}, ob{bt, nullptr, K};
+    if (npass == 3) {
+        kh::tc_split(a, ah, al, (long long)M * K, st);
+        kh::tc_split(bt, bh, bl, (long long)K * N, st);
+        oa = kh::TcOperand{ah, al, K};
+        ob = kh::TcOperand{bh, bl, K};
+    }
+    kh::tc_gemm(oa, ob, c, M, N, K, N, 1.f, 0.f, nullptr, npass, err, st);
+    kh::cast<float, double>(c, C, (long long)M * N, st);
+    int h = 0;
+    KH_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+    if (h) kh::fail(KH_ETIMEOUT, "tensor-core GEMM wait timed out");
+}
+
 template <typename T>
 void run_eig(int k, const double* G, double* W, double* E, void* scratch, size_t bytes, cudaStream_t st) {
     kh::Carver cv(scratch, bytes);
@@ -60,7 +90,7 @@ kh_status run(F&& f) {
 extern "C" {
 
 size_t kh_selftest_bytes(int M, int N, int K) {
-    return 8 * ((size_t)M * K + (size_t)K * N + (size_t)M * N) * 2 + 4096;
+    return 8 * ((size_t)M * K + (size_t)K * N + (size_t)M * N) * 3 + 8192;
 }
 
 kh_status kh_selftest_gemm(int prec, int M, int N, int K, const double* A, const double* B, double* C,
@@ -71,6 +101,8 @@ kh_status kh_selftest_gemm(int prec, int M, int N, int K, const double* A, const
     return run([&] {
         if (prec == KH_FP64) run_gemm<double>(M, N, K, A, B, C, scratch, bytes, st);
         else if (prec == KH_FP32) run_gemm<float>(M, N, K, A, B, C, scratch, bytes, st);
+        else if (prec == KH_TF32) run_tc_gemm(1, M, N, K, A, B, C, scratch, bytes, st);
+        else if (prec == KH_TF32X3) run_tc_gemm(3, M, N, K, A, B, C, scratch, bytes, st);
         else kh::fail(KH_EINVAL, "precision not built");
         KH_CUDA(cudaStreamSynchronize(st));
     });

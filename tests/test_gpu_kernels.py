@@ -16,7 +16,7 @@ def g():
     return pkg
 
 
-GEMM_TOL = {"fp64": 1e-13, "fp32": 3e-6}
+GEMM_TOL = {"fp64": 1e-13, "fp32": 3e-6, "tf32": 4e-3, "tf32x3": 1e-5}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -88,3 +88,21 @@ def test_one_sided_jacobi_svd(g, prec, k, decades):
     assert np.abs(S - ref).max() <= 30 * eps * k * s[0]
     assert np.abs(Q.T @ Q - np.eye(k)).max() <= 30 * eps * k
     assert np.abs(X @ Q - L * S).max() <= 30 * eps * k * s[0]
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x3"])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (256, 256, 16), (200, 300, 96), (512, 16, 256),
+                                   (130, 40, 1028), (1024, 1024, 1024)])
+def test_tensor_core_gemm(g, prec, M, N, K):
+    """tcgen05 GEMM (TMA + TMEM) against numpy: ragged M/N tiles, K below one
+    32-wide K block (zero-filled by TMA), N = 16 tiles, K spanning many stages.
+    TF32 bound: operand truncation 2^-10 each, random-sign accumulation."""
+    import torch
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    C = g.selftest_gemm(torch.as_tensor(A, device="cuda:0"), torch.as_tensor(B, device="cuda:0"), prec).cpu().numpy()
+    ref = A @ B
+    scale = np.sqrt(K) * np.abs(A).max() * np.abs(B).max()
+    err = np.abs(C - ref).max()
+    assert err <= GEMM_TOL[prec] * scale, (err, scale)

@@ -15,7 +15,8 @@ from oracle import ctmrg, eefu, exact, model, peps
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-9, "fp32": 2e-5}
+TOL = {"fp64": 1e-9, "fp32": 2e-5, "tf32x3": 2e-5, "tf32": 2e-3}
+CUT = {"fp64": 1e-12, "fp32": 1e-6, "tf32x3": 1e-6, "tf32": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -48,16 +49,16 @@ def _oracle_ctm(T, chi, sweeps, edge=None):
 
 # ----------------------------------------------------------------- CTMRG alone
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32"])
 @pytest.mark.parametrize("Kh,Kv,seed,chi", [(0.3, 0.2, 7, 16), (0.25, 0.25, None, 24), (0.15, 0.36, 11, 13)])
 def test_ising_free_energy(g, prec, Kh, Kv, seed, chi):
     T = exact.ising_peps(Kh, Kv, gauge_seed=seed)
-    ctx = g.Context(2, chi, prec, p_max=2, n_slots=1, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    ctx = g.Context(2, chi, prec, p_max=2, n_slots=1, svd_cut=CUT[prec])
     ctx.ctm_set_tensor(0, _t(T))
-    ctx.ctm_sweep(0, 300, 3, 1e-11 if prec == "fp64" else 1e-6)
+    ctx.ctm_sweep(0, 300, 3, 1e-11 if prec == "fp64" else 10 * TOL[prec], allow_noconv=prec == "tf32")
     lnk = np.log(ctx.ctm_kappa(0))
     ref = exact.onsager_lnZ(Kh, Kv)
-    assert abs(lnk - ref) < (1e-9 if prec == "fp64" else 2e-5)
+    assert abs(lnk - ref) < (1e-9 if prec == "fp64" else TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -177,7 +178,7 @@ def test_kz_only_closed_form(g, prec):
     assert abs(r["E_site"] - exact.kz_only_energy(Kz, 0.4)) < TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("D,chi,steps", [(2, 16, 4), (3, 12, 2)])
 def test_trotter_steps_match_oracle(g, prec, D, chi, steps):
     """KH model at phi = 0.3 pi from a seeded perturbed product state (bias on):
@@ -186,7 +187,7 @@ def test_trotter_steps_match_oracle(g, prec, D, chi, steps):
     J, K = model.couplings(0.3 * np.pi)
     hA, hB = 0.3, -0.1
     A, B = kh_inputs.perturbed_product_state(D, seed=11, eps=0.05)
-    cut = 1e-12 if prec == "fp64" else 1e-6
+    cut = CUT[prec]
     st = _oracle_state(D, chi, J, K, A, B, hA=hA, hB=hB, svd_cut=cut, ctm_tol=1e-12)
     ctx = g.Context(D, chi, prec, svd_cut=cut)
     ctx.set_state(_t(A), _t(B))
@@ -208,4 +209,6 @@ def test_trotter_steps_match_oracle(g, prec, D, chi, steps):
     for gm in "xyz":
         To = peps.composite(st.A, st.B, gm)
         Tg = peps.composite(Ag.cpu().numpy(), Bg.cpu().numpy(), gm)
-        assert np.abs(_nrm(Tg) - _nrm(To)).max() < (1e-8 if prec == "fp64" else 1e-4)
+        # gauge-covariant (fixed by the balanced-SVD convention), hence looser
+        # than the invariants above
+        assert np.abs(_nrm(Tg) - _nrm(To)).max() < (1e-7 if prec == "fp64" else 1e-4)
