@@ -201,13 +201,16 @@ kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* host_K_xyz, dou
 /* Number of kernels this library has launched since it was loaded. */
 unsigned long long kh_launch_count(void);
 
-/* enable != 0: reset and start CUDA-event timing of seven categories on the
- * context's stream; enable == 0: synchronise, stop, and write host_out[21] =
+/* enable != 0: reset and start CUDA-event timing of ten categories on the
+ * context's stream; enable == 0: synchronise, stop, and write host_out[30] =
  * {launches, milliseconds, algorithmic flops} per category: 0 half-system
  * product Mt = Q_{s+3} Q_s (2 n^3 flops, n = chi D^2), 1 two-layer site
  * contractions (4 nb p D^6 flops per call), 2 enlarged corners, 3 projector
- * SVD without Mt, 4 absorption, 5 environment metric, 6 ALS and gauge
- * (categories 2-6 report 0 flops; 2 contains 1 and 4 contains 1). */
+ * SVD without Mt, 4 absorption, 5 environment metric, 6 ALS and gauge,
+ * 7 one-sided Jacobi SVD, 8 CholQR orthonormalisation, 9 subspace products
+ * M V and M^T U (2 n^2 k flops).  Categories without a flop model report 0,
+ * except 7, whose third entry is the total number of Jacobi sweeps;
+ * nested categories overlap (2 and 4 contain 1; 3 contains 7, 8, 9). */
 kh_status kh_profile(kh_ctx* ctx, int enable, double* host_out);
 
 /* --- kernel self-tests (test hooks; no counterpart in the paper) ----------- */

@@ -17,6 +17,8 @@ KH_OK, KH_EINVAL, KH_ENOMEM, KH_ENOCONV, KH_ENUMERIC, KH_ETIMEOUT, KH_ECUDA = ra
 STATUS_NAMES = ["KH_OK", "KH_EINVAL", "KH_ENOMEM", "KH_ENOCONV", "KH_ENUMERIC", "KH_ETIMEOUT", "KH_ECUDA"]
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4}
 GAMMA = {"x": 0, "y": 1, "z": 2}
+PROFILE_NAMES = ["half_system_product", "site_layer", "corners", "projector_svd", "absorb", "metric", "als_gauge",
+                 "svd_jacobi", "cholqr_orth", "subspace_gemm"]
 
 # every entry point of include/eefu.h (checked by the CPU symbol test)
 ABI_FUNCTIONS = [
@@ -158,6 +160,10 @@ def default_config(D, chi, prec="fp64", **kw):
     c = KhConfig()
     lib().kh_config_defaults(ctypes.byref(c))
     c.D, c.chi, c.prec = D, chi, PREC[prec] if isinstance(prec, str) else int(prec)
+    if c.prec != PREC["fp64"]:
+        # single-precision paths: the Rayleigh-Ritz SVD is capped (its residual
+        # is below the FP32-level accuracy of the contractions well before)
+        c.jacobi_max_sweeps = 8
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -240,11 +246,11 @@ class Context:
         self._check(lib().kh_profile(self._ctx, 1, None))
 
     def profile_stop(self):
-        out = np.zeros(21)
+        out = np.zeros(3 * len(PROFILE_NAMES))
         o, op = _dptr(out)
         self._check(lib().kh_profile(self._ctx, 0, op))
-        names = ["half_system_product", "site_layer", "corners", "projector_svd", "absorb", "metric", "als_gauge"]
-        return {names[k]: dict(launches=int(o[3 * k]), ms=o[3 * k + 1], flops=o[3 * k + 2]) for k in range(7)}
+        return {nm: dict(launches=int(o[3 * k]), ms=o[3 * k + 1], flops=o[3 * k + 2])
+                for k, nm in enumerate(PROFILE_NAMES)}
 
     # ---- state
     def set_state(self, A, B):

@@ -109,7 +109,7 @@ void kh_config_defaults(kh_config* c) {
     c->svd_oversample = 16;
     c->svd_iters_cold = 4;
     c->svd_iters_warm = 1;
-    c->jacobi_max_sweeps = 40;
+    c->jacobi_max_sweeps = 40;    // per Rayleigh-Ritz SVD; converged environments need 2-3
     c->svd_cut = 1e-12;
     c->als_tol = 1e-12;
     c->als_max_iter = 50;
@@ -317,6 +317,7 @@ kh_status kh_profile(kh_ctx* ctx, int enable, double* out) {
         if (enable) {
             for (auto& c : e->prof) { c.used = 0; c.flops = 0.0; }
             e->prof_on = true;
+            e->reset_counters();
             return;
         }
         KH_CUDA(cudaStreamSynchronize(e->st));
@@ -334,6 +335,7 @@ kh_status kh_profile(kh_ctx* ctx, int enable, double* out) {
                 out[3 * k + 2] = e->prof[k].flops;
             }
         }
+        if (out) out[3 * 7 + 2] = e->read_counter();   // one-sided Jacobi: total sweeps
     });
 }
 

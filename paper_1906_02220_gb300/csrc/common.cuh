@@ -142,6 +142,8 @@ struct GemmArgs {
     T* C; long long sCm, sCn, sCb;
     T alpha, beta;
     const T* colscale;   // nullable, length N
+    T* sk = nullptr;     // optional split-K scratch (for few output tiles and long K)
+    long long sk_elems = 0;
 };
 
 constexpr int GT_K = 16;
@@ -221,21 +223,86 @@ inline void gemm_launch(const GemmArgs<T>& g, cudaStream_t st) {
     KH_LAUNCHED();
 }
 
+// out[i] = alpha * colscale[col] * sum_s part[s][i] + beta * out   (split-K reduction)
 template <typename T>
-inline void gemm(const GemmArgs<T>& g, cudaStream_t st) {
-    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
-    if (g.batch > 65535) fail(KH_EINVAL, "gemm batch > 65535");
+__global__ void splitk_reduce_kernel(const T* __restrict__ part, int splits, int M, int N, T* C, long long sCm,
+                                     long long sCn, T alpha, T beta, const T* colscale) {
+    long long tot = (long long)M * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        T acc = T(0);
+        for (int s = 0; s < splits; ++s) acc += part[s * tot + i];
+        int m = (int)(i / N), n = (int)(i % N);
+        T v = alpha * acc;
+        if (colscale) v *= colscale[n];
+        T* dst = C + m * sCm + n * sCn;
+        if (beta != T(0)) v += beta * (*dst);
+        *dst = v;
+    }
+}
+
+template <typename T>
+inline void gemm_dispatch(const GemmArgs<T>& g, cudaStream_t st) {
     if (g.M <= 16 && g.N <= 16) gemm_launch<T, 16, 16, 1, 1>(g, st);
     else if (g.N <= 16) gemm_launch<T, 128, 16, 2, 4>(g, st);
     else if (g.M <= 16) gemm_launch<T, 16, 128, 4, 2>(g, st);
     else gemm_launch<T, 64, 64, 4, 4>(g, st);
 }
 
+template <typename T>
+inline void gemm(const GemmArgs<T>& g, cudaStream_t st) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+    if (g.batch > 65535) fail(KH_EINVAL, "gemm batch > 65535");
+    // few output tiles and a long K: split K over CTAs into the scratch,
+    // then reduce in a fixed order (deterministic)
+    const long long tiles = (long long)((g.M + 63) / 64) * ((g.N + 63) / 64);
+    if (g.batch == 1 && g.sk && tiles < 76 && g.K >= 256) {
+        int splits = (int)((152 + tiles - 1) / tiles);
+        int maxs = g.K / 128;
+        if (splits > maxs) splits = maxs;
+        if (splits > 32) splits = 32;
+        const long long mn = (long long)g.M * g.N;
+        if (splits >= 2 && splits * mn <= g.sk_elems) {
+            const int kchunk = ((g.K + splits - 1) / splits + GT_K - 1) / GT_K * GT_K;
+            splits = (g.K + kchunk - 1) / kchunk;
+            GemmArgs<T> p = g;
+            p.K = kchunk;
+            p.batch = splits;
+            p.sAb = kchunk * g.sAk;            // batch b = K range [b*kchunk, ...)
+            p.sBb = kchunk * g.sBk;
+            p.C = g.sk; p.sCm = g.N; p.sCn = 1; p.sCb = mn;
+            p.alpha = T(1); p.beta = T(0); p.colscale = nullptr; p.sk = nullptr;
+            // the last chunk may overrun K: handled by a separate launch with the remainder
+            const int last = g.K - (splits - 1) * kchunk;
+            if (last == kchunk) {
+                gemm_dispatch<T>(p, st);
+            } else {
+                p.batch = splits - 1;
+                gemm_dispatch<T>(p, st);
+                GemmArgs<T> r = p;
+                r.batch = 1; r.K = last;
+                r.A = g.A + (long long)(splits - 1) * kchunk * g.sAk;
+                r.B = g.B + (long long)(splits - 1) * kchunk * g.sBk;
+                r.C = g.sk + (long long)(splits - 1) * mn;
+                gemm_dispatch<T>(r, st);
+            }
+            splitk_reduce_kernel<T><<<grid_for(mn), 256, 0, st>>>(g.sk, splits, g.M, g.N, g.C, g.sCm, g.sCn, g.alpha,
+                                                                  g.beta, g.colscale);
+            KH_LAUNCHED();
+            return;
+        }
+    }
+    gemm_dispatch<T>(g, st);
+}
+
 // Plain row-major C(MxN) = A(MxK) B(KxN) [+beta C]; transposes by flags.
 template <typename T>
 inline void gemm_rm(int M, int N, int K, const T* A, bool tA, const T* B, bool tB, T* C,
-                    cudaStream_t st, T alpha = T(1), T beta = T(0), const T* colscale = nullptr) {
+                    cudaStream_t st, T alpha = T(1), T beta = T(0), const T* colscale = nullptr,
+                    T* sk = nullptr, long long sk_elems = 0) {
     GemmArgs<T> g;
+    g.sk = sk;
+    g.sk_elems = sk_elems;
     g.M = M; g.N = N; g.K = K; g.batch = 1;
     g.A = A; g.sAm = tA ? 1 : K; g.sAk = tA ? M : 1; g.sAb = 0;
     g.B = B; g.sBk = tB ? 1 : N; g.sBn = tB ? K : 1; g.sBb = 0;

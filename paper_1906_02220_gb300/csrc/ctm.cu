@@ -140,6 +140,8 @@ void Engine<T>::layout(Carver& cv) {
     dwork = cv.take<double>(4 * E1 + 16LL * d.D4 + 64);
     flags = cv.take<int>(64);
     tc_err = cv.take<int>(64);
+    sk_elems = 16LL * n * (kk > d.chi ? kk : d.chi);
+    skbuf = cv.take<T>(sk_elems);
 }
 
 template <typename T>
@@ -451,6 +453,7 @@ void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
     (void)G; (void)W; (void)L;
     const double tau = sizeof(T) == 8 ? 1e-12 : 1e-5;
     double* dG = dscr + 8192;
+    prof_begin(8);
     // CholQR2: two passes of the ordered Cholesky-QR (the second pass restores
     // orthogonality lost to the conditioning of the first)
     gram<T>(Y, n, k, dG, st);
@@ -459,6 +462,7 @@ void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
     gram<T>(Qt, n, k, dG, st);
     cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st);
     gemm_rm<T>(n, k, k, Qt, false, Xk, false, Uo, st);
+    prof_end(8, 0.0);
 }
 
 // Half-system product Mt = Q_{s+3} Q_s (= M^T), the largest single GEMM of a
@@ -499,11 +503,17 @@ __global__ void warm_split_kernel(const T* Vw, const int* live, int n, int k, T*
     }
 }
 
-__global__ void live_mask_kernel(const void* sv, int is_double, int k, double cut, int* live) {
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double s0 = is_double ? ((const double*)sv)[0] : ((const float*)sv)[0];
-        double sc = is_double ? ((const double*)sv)[c] : ((const float*)sv)[c];
-        live[c] = (s0 > 0.0 && sc > cut * s0) ? 1 : 0;
+// A warm-basis column is kept unless it is (near) zero, i.e. its direction
+// was dropped by the orthonormalisation: kept tail directions keep
+// converging by power iteration instead of restarting from random vectors.
+template <typename T>
+__global__ void live_mask_kernel(const T* __restrict__ V, int n, int k, int* live) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = warp; c < k; c += nw) {
+        T a = T(0);
+        for (int r = lane; r < n; r += 32) { T v = V[(long long)r * k + c]; a = fma(v, v, a); }
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) live[c] = (a > T(0.25)) ? 1 : 0;
     }
 }
 
@@ -550,7 +560,9 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
             KH_LAUNCHED();
         }
         gemm_rm<T>(n, n, n, Mt, true, Vw, false, Y1, st);                      // Y = M V_w
-        svd_jacobi<T>(Y1, n, Sk, Uf, Lk, cfg.jacobi_max_sweeps, jtol, 0.0, st);   // Y Q = L S
+        prof_begin(7);
+        svd_jacobi<T>(Y1, n, Sk, Uf, Lk, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, chi + 8);   // Y Q = L S
+        prof_end(7, 0.0);
         gemm_rm<T>(n, n, n, Vw, false, Lk, false, Z1, st);                     // V = V_w Q
         gemm_rm<T>(n, n, n, Z1, true, Z1, false, Y1, st);                      // V^T V
         gemm_rm<T>(n, n, n, Z1, false, Y1, false, Z2, st, T(-0.5), T(0));      // Newton-Schulz:
@@ -575,28 +587,36 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
                 Vw, live, n, k, Vo, Z2, cfg.seed, stream * 1000003ULL + (rng_counter++));
             KH_LAUNCHED();
             for (int r = 0; r < 2; ++r) {                                       // R <- R - Vl (Vl^T R), twice
-                gemm_rm<T>(k, k, n, Vo, true, Z2, false, Xk, st);
+                gemm_rm<T>(k, k, n, Vo, true, Z2, false, Xk, st, T(1), T(0), nullptr, skbuf, sk_elems);
                 gemm_rm<T>(n, k, k, Vo, false, Xk, false, Z2, st, T(-1), T(1));
             }
             add_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(Vo, Z2, (long long)n * k);
             KH_LAUNCHED();
-            orth(Z2, n, k, V0, G1, W1, L1);
-            Vin = V0;
+            // no orthonormalisation needed: only span(M V) matters, and with
+            // the complement projected off the live span, M V keeps the
+            // trusted (large) columns first for the ordered CholQR below
+            Vin = Z2;
             q = cfg.svd_iters_warm;
         }
         for (int it = 0; it < q; ++it) {
-            gemm_rm<T>(n, k, n, Mt, true, Vin, false, Z1, st);                 // Y = M V
+            prof_begin(9);
+            gemm_rm<T>(n, k, n, Mt, true, Vin, false, Z1, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // Y = M V
+            prof_end(9, 2.0 * n * (double)n * k);
             orth(Z1, n, k, U, G1, W1, L1);                                     // U = orth(Y)
-            gemm_rm<T>(n, k, n, Mt, false, U, false, Z2, st);                  // Z = M^T U
+            prof_begin(9);
+            gemm_rm<T>(n, k, n, Mt, false, U, false, Z2, st, T(1), T(0), nullptr, skbuf, sk_elems);                  // Z = M^T U
+            prof_end(9, 2.0 * n * (double)n * k);
             orth(Z2, n, k, Vo, G2, W2, L2);                                    // V' = orth(Z)
             Vin = Vo;
         }
-        gemm_rm<T>(k, k, n, Vo, true, Z2, false, Hk, st);                      // H = V'^T Z
-        svd_jacobi<T>(Hk, k, Sk, Lk, Qk, cfg.jacobi_max_sweeps, jtol, 0.0, st);   // H Q = L S
+        gemm_rm<T>(k, k, n, Vo, true, Z2, false, Hk, st, T(1), T(0), nullptr, skbuf, sk_elems);                      // H = V'^T Z
+        prof_begin(7);
+        svd_jacobi<T>(Hk, k, Sk, Lk, Qk, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, chi + 8);   // H Q = L S
+        prof_end(7, 0.0);
         gemm_rm<T>(n, k, k, Vo, false, Lk, false, Z1, st);                     // right vectors of M
         gemm_rm<T>(n, k, k, U, false, Qk, false, Uf, st);                      // left vectors of M
         KH_CUDA(cudaMemcpyAsync(Vw, Z1, sizeof(T) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
-        live_mask_kernel<<<1, 256, 0, st>>>(Sk, sizeof(T) == 8, k, cut, live);
+        live_mask_kernel<T><<<1, 512, 0, st>>>(Z1, n, k, live);
         KH_LAUNCHED();
         sl.warm[dir] = true;
     }
@@ -615,6 +635,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         g.B = Z1; g.sBk = k; g.sBn = 1; g.sBb = 0;
         g.C = P; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
+        g.sk = skbuf; g.sk_elems = sk_elems;
         gemm<T>(g, st);
     }
     {   // P~^T = Qa U S^-1/2  (Qa stored transposed when tensor cores are used)
@@ -624,6 +645,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         g.B = Uf; g.sBk = k; g.sBn = 1; g.sBb = 0;
         g.C = PtT; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
+        g.sk = skbuf; g.sk_elems = sk_elems;
         gemm<T>(g, st);
     }
 }
@@ -639,6 +661,7 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
         g.B = X1[0]; g.sBk = chi; g.sBn = 1; g.sBb = 0;
         g.C = C1n; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
+        g.sk = skbuf; g.sk_elems = sk_elems;
         gemm<T>(g, st);
     }
     const T* C4 = Cop + ((s + 3) & 3) * chi2;
@@ -653,12 +676,12 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
         g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
         gemm<T>(g, st);
     }
-    gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, st);                  // C4n = C4E3 P~^T
+    gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                  // C4n = C4E3 P~^T
     gemm_rm<T>(d2 * chi, d2 * chi, chi, E4, true, P, false, Y1, st);             // [(lk,lb,x4)][(dk,db,a)]
     permute<T, T>(Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3}, st);       // [x4][a][lb][db][lk][dk]
     site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt);     // [x4][a][uk][rk][ub][rb]
     permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
-    gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st);                 // [a][rk][rb][a_up]
+    gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // [a][rk][rb][a_up]
     double* ns = dscr + 8010;
     KH_CUDA(cudaMemsetAsync(ns, 0, 3 * sizeof(double), st));
     sumsq_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C1n, chi2, ns);
@@ -852,21 +875,23 @@ void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long lo
     KH_LAUNCHED();
 }
 template <typename T>
-void svd_jacobi(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double tol, double cut, cudaStream_t st) {
+void svd_jacobi(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double tol, double cut, cudaStream_t st,
+                int* sweep_count, int nrel) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "svd_jacobi: k beyond limit");
-    size_t sm = jacobi_smem<T>(k);
+    const int kp = (k + 1) & ~1;
+    size_t sm = (size_t)2 * kp * (kp + 1) * sizeof(T);
     static size_t attr_set = 0;
     if (sm > 48 * 1024 && sm > attr_set) {
         KH_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set = sm;
     }
-    svd_jacobi_kernel<T><<<1, kJacobiThreads, sm, st>>>(X, k, sv, L, Qm, max_sweeps, tol, cut);
+    svd_jacobi_kernel<T><<<1, kJacobiThreads, sm, st>>>(X, k, sv, L, Qm, max_sweeps, tol, cut, sweep_count, nrel);
     KH_LAUNCHED();
 }
 template <typename T>
 void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
-    size_t sm = (size_t)2 * k * k * sizeof(T);
+    size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
     static size_t attr_set = 0;
     if (sm > 48 * 1024 && sm > attr_set) {
         KH_CUDA(cudaFuncSetAttribute(cholqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -878,8 +903,10 @@ void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cu
 template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t);
 template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t);
 
-template void svd_jacobi<float>(const float*, int, float*, float*, float*, int, double, double, cudaStream_t);
-template void svd_jacobi<double>(const double*, int, double*, double*, double*, int, double, double, cudaStream_t);
+template void svd_jacobi<float>(const float*, int, float*, float*, float*, int, double, double, cudaStream_t, int*,
+                                int);
+template void svd_jacobi<double>(const double*, int, double*, double*, double*, int, double, double, cudaStream_t,
+                                 int*, int);
 
 template void jacobi_eig<float>(const float*, int, int, long long, float*, int, long long, float*, long long, int, int,
                                 double, int*, const int*, cudaStream_t);

@@ -38,7 +38,8 @@ struct Dims {
 // CUDA-event timing of kernel categories (bench instrumentation only):
 // 0 = half-system product Mt = Q_{s+3} Q_s, 1 = two-layer site contractions,
 // 2 = enlarged corners (all), 3 = projector SVD (excluding Mt),
-// 4 = absorption, 5 = environment metric, 6 = ALS + gauge.
+// 4 = absorption, 5 = environment metric, 6 = ALS + gauge,
+// 7 = one-sided Jacobi SVD, 8 = CholQR orthonormalisation, 9 = subspace GEMMs.
 struct ProfCat {
     std::vector<cudaEvent_t> a, b;
     int used = 0;
@@ -51,7 +52,7 @@ struct EngineBase {
             for (size_t i = 0; i < c.a.size(); ++i) { cudaEventDestroy(c.a[i]); cudaEventDestroy(c.b[i]); }
     }
     bool prof_on = false;
-    static constexpr int kProfCats = 7;
+    static constexpr int kProfCats = 10;
     ProfCat prof[kProfCats];
     void prof_begin(int cat) {
         if (!prof_on) return;
@@ -78,6 +79,8 @@ struct EngineBase {
     std::string err;
     virtual void set_state(const double* A, const double* B) = 0;
     virtual void get_state(double* A, double* B) = 0;
+    virtual void reset_counters() = 0;
+    virtual double read_counter() = 0;
     virtual void set_tensor(int slot, const double* Tin, int p) = 0;
     virtual void build_composite(int slot, int gamma, const double* gate) = 0;
     virtual void init_env(int slot, const double* edge) = 0;
@@ -118,6 +121,8 @@ struct Engine : EngineBase {
     float *Gtf = nullptr, *Wtf = nullptr, *Ltf = nullptr;
     int* flags = nullptr;
     int* tc_err = nullptr;     // tensor-core kernels' time-out flag
+    T* skbuf = nullptr;        // split-K partial sums of skinny GEMMs
+    long long sk_elems = 0;
     int tc_npass = 0;          // 0: CUDA-core GEMMs; 1: TF32; 3: 3xTF32
     unsigned long long rng_counter = 0;
     void half_system_product(int n);
@@ -145,6 +150,13 @@ struct Engine : EngineBase {
     // API
     void set_state(const double* A, const double* B) override;
     void get_state(double* A, double* B) override;
+    void reset_counters() override { KH_CUDA(cudaMemsetAsync(flags + 48, 0, sizeof(int), st)); }
+    double read_counter() override {
+        int h = 0;
+        KH_CUDA(cudaMemcpyAsync(&h, flags + 48, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KH_CUDA(cudaStreamSynchronize(st));
+        return h;
+    }
     void set_tensor(int slot, const double* Tin, int p) override;
     void build_composite(int slot, int gamma, const double* gate) override;
     void init_env(int slot, const double* edge) override;

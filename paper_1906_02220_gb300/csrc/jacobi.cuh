@@ -194,53 +194,93 @@ void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long lo
 // number, unlike a Gram-matrix eigensolve).  Outputs sorted descending:
 // s (k), L (k x k, column j = X q_j / s_j, zero when s_j <= cut s_0), Q (k x k).
 template <typename T>
-void svd_jacobi(const T* X, int k, T* s, T* L, T* Q, int max_sweeps, double tol, double cut, cudaStream_t st);
+void svd_jacobi(const T* X, int k, T* s, T* L, T* Q, int max_sweeps, double tol, double cut, cudaStream_t st,
+                int* sweep_count = nullptr, int nrel = 0);
 
 #ifdef KH_JACOBI_KERNEL
+// 8-lane groups, one column pair per group (64 groups = every pair of a
+// round in flight for k <= 128); columns stored contiguously with an odd
+// stride.  A sweep ends the iteration when no pair needed a rotation, or when
+// the largest pair cosine stops falling quadratically while already below
+// 1e3 * eps (the rounding floor of the column dot products).
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads)
 svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __restrict__ L_out,
-                  T* __restrict__ Q_out, int max_sweeps, double tol, double cut) {
+                  T* __restrict__ Q_out, int max_sweeps, double tol, double cut, int* sweep_count, int nrel) {
     extern __shared__ unsigned char smem_raw[];
     const int kp = (k + 1) & ~1;
-    T* Xc = reinterpret_cast<T*>(smem_raw);   // column-major: Xc[c * kp + r]
-    T* Qc = Xc + kp * kp;
+    const int ld = kp + 1;                     // odd column stride
+    T* Xc = reinterpret_cast<T*>(smem_raw);   // Xc[c * ld + r]
+    T* Qc = Xc + kp * ld;
     __shared__ int s_rot;
+    __shared__ float s_cmax;
     __shared__ double s_norm[160];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    __shared__ T s_cn[160];
+    __shared__ unsigned char s_top[160];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int grp = tid >> 3, gl = tid & 7, ngrp = nt >> 3;
+    const unsigned gmask = 0xFFu << (tid & 24);
+    const double eps = sizeof(T) == 8 ? 1.1e-16 : 6e-8;
     for (int e = tid; e < kp * kp; e += nt) {
         int c = e / kp, r = e % kp;
-        Xc[e] = (r < k && c < k) ? Xin[(long long)r * k + c] : T(0);
-        Qc[e] = (r == c) ? T(1) : T(0);
+        Xc[c * ld + r] = (r < k && c < k) ? Xin[(long long)r * k + c] : T(0);
+        Qc[c * ld + r] = (r == c) ? T(1) : T(0);
     }
-    __syncthreads();
-    for (int sw = 0; sw < max_sweeps; ++sw) {
-        if (tid == 0) s_rot = 0;
+    // the cosine of two columns is only known to ~k eps (dot-product rounding)
+    const T tol_eff = (T)fmax(tol, 2.0 * k * eps);
+    float prev_cmax = 1e30f;
+    int sw = 0;
+    if (nrel <= 0 || nrel > kp) nrel = kp;
+    for (; sw < max_sweeps; ++sw) {
+        if (tid == 0) { s_rot = 0; s_cmax = 0.f; }
+        if (nrel < kp) {
+            // columns among the nrel largest must converge; tail-tail pairs are
+            // still rotated but do not keep the sweep loop alive
+            const int w0 = tid >> 5, l0 = tid & 31, nw0 = nt >> 5;
+            for (int c = w0; c < kp; c += nw0) {
+                T a = T(0);
+                for (int row = l0; row < kp; row += 32) { T u = Xc[c * ld + row]; a = fma(u, u, a); }
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (l0 == 0) s_cn[c] = a;
+            }
+            __syncthreads();
+            for (int c = tid; c < kp; c += nt) {
+                int rank = 0;
+                for (int j = 0; j < kp; ++j) rank += (s_cn[j] > s_cn[c]) || (s_cn[j] == s_cn[c] && j < c);
+                s_top[c] = rank < nrel;
+            }
+        } else {
+            for (int c = tid; c < kp; c += nt) s_top[c] = 1;
+        }
         __syncthreads();
         for (int r = 0; r < kp - 1; ++r) {
-            for (int i = warp; i < kp / 2; i += nw) {
+            for (int i = grp; i < kp / 2; i += ngrp) {
                 int p, q;
                 round_robin_pair<T>(r, i, kp, p, q);
-                T* xp = Xc + p * kp;
-                T* xq = Xc + q * kp;
+                T* xp = Xc + p * ld;
+                T* xq = Xc + q * ld;
                 T a = T(0), b = T(0), g = T(0);
-                for (int row = lane; row < kp; row += 32) {
+                for (int row = gl; row < kp; row += 8) {
                     T u = xp[row], v = xq[row];
                     a = fma(u, u, a); b = fma(v, v, b); g = fma(u, v, g);
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    a += __shfl_xor_sync(0xffffffffu, a, o);
-                    b += __shfl_xor_sync(0xffffffffu, b, o);
-                    g += __shfl_xor_sync(0xffffffffu, g, o);
+                for (int o = 4; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(gmask, a, o);
+                    b += __shfl_xor_sync(gmask, b, o);
+                    g += __shfl_xor_sync(gmask, g, o);
                 }
-                // converged pair (sqrt(a) sqrt(b), not sqrt(a b): no underflow for tiny columns)
-                if (g == T(0) || fabs(g) <= (T)tol * (sqrt(a) * sqrt(b))) continue;   // warp-uniform
+                T den = sqrt(a) * sqrt(b);
+                if (g == T(0) || den == T(0)) continue;            // group-uniform
+                const bool rel = s_top[p] || s_top[q];
+                float cosv = (float)(fabs(g) / den);
+                if (gl == 0 && rel) atomicMax((int*)&s_cmax, __float_as_int(cosv));
+                if (fabs(g) <= tol_eff * den) continue;
                 T zeta = (b - a) / (T(2) * g);
                 T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                 T cT = T(1) / sqrt(T(1) + t * t), sT = cT * t;
-                T* qp = Qc + p * kp;
-                T* qq = Qc + q * kp;
-                for (int row = lane; row < kp; row += 32) {
+                T* qp = Qc + p * ld;
+                T* qq = Qc + q * ld;
+                for (int row = gl; row < kp; row += 8) {
                     T u = xp[row], v = xq[row];
                     xp[row] = cT * u - sT * v;
                     xq[row] = sT * u + cT * v;
@@ -248,17 +288,22 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
                     qp[row] = cT * qu - sT * qv;
                     qq[row] = sT * qu + cT * qv;
                 }
-                if (lane == 0) atomicAdd(&s_rot, 1);
+                if (gl == 0 && rel) atomicAdd(&s_rot, 1);
             }
             __syncthreads();
         }
-        if (s_rot == 0) break;
+        const float cmax = s_cmax;
+        const int rot = s_rot;
         __syncthreads();
+        if (rot == 0) break;
+        if (cmax < 1e3f * (float)eps && cmax > 0.25f * prev_cmax) break;   // stagnated at the floor
+        prev_cmax = cmax;
     }
-    // column norms, ranks, outputs
+    if (sweep_count && tid == 0) atomicAdd(sweep_count, sw + 1);
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     for (int c = warp; c < kp; c += nw) {
         T a = T(0);
-        for (int row = lane; row < kp; row += 32) { T u = Xc[c * kp + row]; a = fma(u, u, a); }
+        for (int row = lane; row < kp; row += 32) { T u = Xc[c * ld + row]; a = fma(u, u, a); }
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (lane == 0) s_norm[c] = (c < k) ? (double)sqrt(a) : -1.0;
     }
@@ -269,10 +314,10 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
         double sc = s_norm[c];
         int rank = 0;
         for (int j = 0; j < k; ++j) rank += (s_norm[j] > sc) || (s_norm[j] == sc && j < c);
-        double inv = (smax > 0.0 && sc > cut * smax) ? 1.0 / sc : 0.0;
+        T inv = (smax > 0.0 && sc > cut * smax) ? (T)(1.0 / sc) : T(0);
         for (int row = lane; row < k; row += 32) {
-            L_out[(long long)row * k + rank] = (T)((double)Xc[c * kp + row] * inv);
-            Q_out[(long long)row * k + rank] = Qc[c * kp + row];
+            L_out[(long long)row * k + rank] = Xc[c * ld + row] * inv;
+            Q_out[(long long)row * k + rank] = Qc[c * ld + row];
         }
         if (lane == 0) s_out[rank] = (T)sc;
     }
@@ -295,54 +340,53 @@ template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads)
 cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X) {
     extern __shared__ unsigned char smem_raw[];
-    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x k, row-major
-    T* Li = Lm + k * k;
-    __shared__ double s_inv[160];
+    const int ld = k | 1;                          // odd row stride: conflict-free column walks
+    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x ld, row-major
+    T* Li = Lm + k * ld;
+    __shared__ T s_inv[160];
     __shared__ int s_perm[160];
     __shared__ int s_keep[160];
+    __shared__ double s_diag[160];
     __shared__ double s_max;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int j = tid; j < k; j += nt) s_diag[j] = G[(long long)j * k + j];
+    __syncthreads();
     if (tid == 0) {
         double m = 0.0;
-        for (int j = 0; j < k; ++j) m = fmax(m, G[(long long)j * k + j]);
+        for (int j = 0; j < k; ++j) m = fmax(m, s_diag[j]);
         s_max = sqrt(fmax(m, 0.0));
     }
     __syncthreads();
     for (int j = tid; j < k; j += nt) {
-        double nj = sqrt(fmax(G[(long long)j * k + j], 0.0));
-        s_inv[j] = (s_max > 0.0 && nj > cut_abs * s_max) ? 1.0 / nj : 0.0;
+        double nj = sqrt(fmax(s_diag[j], 0.0));
+        s_inv[j] = (s_max > 0.0 && nj > cut_abs * s_max) ? (T)(1.0 / nj) : T(0);
         int rank = 0;
-        for (int i = 0; i < k; ++i) {
-            double ni = G[(long long)i * k + i];
-            double nn = G[(long long)j * k + j];
-            rank += (ni > nn) || (ni == nn && i < j);
-        }
+        for (int i = 0; i < k; ++i) rank += (s_diag[i] > s_diag[j]) || (s_diag[i] == s_diag[j] && i < j);
         s_perm[rank] = j;
     }
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {
         int a = e / k, b = e % k;
         int pa = s_perm[a], pb = s_perm[b];
-        Lm[e] = (T)(G[(long long)pa * k + pb] * s_inv[pa] * s_inv[pb]);
-        Li[e] = T(0);
+        Lm[a * ld + b] = (T)G[(long long)pa * k + pb] * s_inv[pa] * s_inv[pb];
+        Li[a * ld + b] = T(0);
     }
     __syncthreads();
     for (int j = 0; j < k; ++j) {
-        T d = Lm[j * k + j];
-        bool keep = (double)d > tau;                      // same value in every thread
+        const T d = Lm[j * ld + j];
+        const bool keep = (double)d > tau;        // same value in every thread
         if (keep) {
-            T ljj = sqrt(d);
-            for (int i = j + 1 + tid; i < k; i += nt) Lm[i * k + j] /= ljj;
+            const T ljj = sqrt(d);
+            for (int i = j + 1 + tid; i < k; i += nt) Lm[i * ld + j] /= ljj;
             __syncthreads();
-            if (tid == 0) { Lm[j * k + j] = ljj; s_keep[j] = 1; }
-            int rows = k - j - 1;
-            for (int e = tid; e < rows * rows; e += nt) {
-                int i = j + 1 + e / rows, c = j + 1 + e % rows;
-                if (c <= i) Lm[i * k + c] -= Lm[i * k + j] * Lm[c * k + j];
+            if (tid == 0) { Lm[j * ld + j] = ljj; s_keep[j] = 1; }
+            for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
+                const T lij = Lm[i * ld + j];
+                for (int c = j + 1 + lane; c <= i; c += 32) Lm[i * ld + c] -= lij * Lm[c * ld + j];
             }
         } else {
             __syncthreads();
-            for (int i = j + tid; i < k; i += nt) Lm[i * k + j] = T(0);
+            for (int i = j + tid; i < k; i += nt) Lm[i * ld + j] = T(0);
             if (tid == 0) s_keep[j] = 0;
         }
         __syncthreads();
@@ -350,14 +394,14 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
     // Li = L^-1 on the kept index set, one warp per column
     for (int j = warp; j < k; j += nw) {
         if (!s_keep[j]) continue;
-        if (lane == 0) Li[j * k + j] = T(1) / Lm[j * k + j];
+        if (lane == 0) Li[j * ld + j] = T(1) / Lm[j * ld + j];
         __syncwarp();
         for (int i = j + 1; i < k; ++i) {
             if (!s_keep[i]) continue;
             T sum = T(0);
-            for (int m = j + lane; m < i; m += 32) sum = fma(Lm[i * k + m], Li[m * k + j], sum);
+            for (int m = j + lane; m < i; m += 32) sum = fma(Lm[i * ld + m], Li[m * ld + j], sum);
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) Li[i * k + j] = -sum / Lm[i * k + i];
+            if (lane == 0) Li[i * ld + j] = -sum / Lm[i * ld + i];
             __syncwarp();
         }
     }
@@ -366,7 +410,7 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
     for (int e = tid; e < k * k; e += nt) {
         int a = e / k, b = e % k;
         int pa = s_perm[a];
-        X[(long long)pa * k + b] = (T)(s_inv[pa] * (double)Li[b * k + a]);
+        X[(long long)pa * k + b] = s_inv[pa] * Li[b * ld + a];
     }
 }
 #endif  // KH_JACOBI_KERNEL

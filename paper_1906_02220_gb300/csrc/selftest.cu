@@ -12,9 +12,11 @@ void run_gemm(int M, int N, int K, const double* A, const double* B, double* C, 
     T* a = cv.take<T>((size_t)M * K);
     T* b = cv.take<T>((size_t)K * N);
     T* c = cv.take<T>((size_t)M * N);
+    const long long skn = 8LL * M * N;                 // split-K scratch (up to 8 partial products)
+    T* sk = (cv.off + skn * sizeof(T) + 256 <= bytes) ? cv.take<T>((size_t)skn) : nullptr;
     kh::cast<double, T>(A, a, (long long)M * K, st);
     kh::cast<double, T>(B, b, (long long)K * N, st);
-    kh::gemm_rm<T>(M, N, K, a, false, b, false, c, st);
+    kh::gemm_rm<T>(M, N, K, a, false, b, false, c, st, T(1), T(0), nullptr, sk, sk ? skn : 0);
     kh::cast<T, double>(c, C, (long long)M * N, st);
 }
 
@@ -90,7 +92,7 @@ kh_status run(F&& f) {
 extern "C" {
 
 size_t kh_selftest_bytes(int M, int N, int K) {
-    return 8 * ((size_t)M * K + (size_t)K * N + (size_t)M * N) * 3 + 8192;
+    return 8 * ((size_t)M * K + (size_t)K * N + (size_t)M * N) * 3 + 8 * 8 * (size_t)M * N + 8192;
 }
 
 kh_status kh_selftest_gemm(int prec, int M, int N, int K, const double* A, const double* B, double* C,

@@ -21,7 +21,7 @@ GEMM_TOL = {"fp64": 1e-13, "fp32": 3e-6, "tf32": 4e-3, "tf32x3": 1e-5}
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("M,N,K", [(1, 1, 1), (16, 16, 16), (17, 33, 65), (128, 16, 256), (16, 128, 40),
-                                   (300, 257, 129), (1024, 96, 1024)])
+                                   (300, 257, 129), (1024, 96, 1024), (80, 80, 1000), (64, 64, 2048)])
 def test_gemm_against_numpy(g, prec, M, N, K):
     import torch
     rng = np.random.default_rng(M * 7 + N * 3 + K)
