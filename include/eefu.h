@@ -238,6 +238,23 @@ kh_status kh_selftest_symeig(int prec, int k, const double* dev_G, double* dev_W
 kh_status kh_selftest_svd(int prec, int k, const double* dev_X, double* dev_S, double* dev_L, double* dev_Q,
                           void* dev_scratch, size_t scratch_bytes, void* stream);
 
+/* --- allocation-free variant (the paper has no counterpart) ---------------- */
+
+/* Same result as kh_selftest_gemm (dev_C = dev_A dev_B, row-major FP64 device
+ * arrays, computed by the library's contraction GEMM for precision prec), for
+ * callers that cannot allocate device memory -- code whose device memory is
+ * owned by another allocator, or loops that cannot afford an allocation's
+ * implicit synchronisation.  Scratch is a static device array of
+ * kh_gemm_noalloc_max_bytes() bytes (16 MiB) that every GPU loading the
+ * library holds until exit; sizes needing more (kh_selftest_bytes(M, N, K))
+ * return KH_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race.  Synchronises stream; no cudaMalloc or cudaFree. */
+size_t kh_gemm_noalloc_max_bytes(void);
+kh_status kh_gemm_noalloc(int prec, int M, int N, int K, const double* dev_A, const double* dev_B, double* dev_C,
+                          void* stream);
+
 /* Library build information (static string). */
 const char* kh_version(void);
 

@@ -27,7 +27,7 @@ ABI_FUNCTIONS = [
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
     "eefu_trotter_step", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
-    "kh_selftest_symeig", "kh_selftest_svd",
+    "kh_selftest_symeig", "kh_selftest_svd", "kh_gemm_noalloc", "kh_gemm_noalloc_max_bytes",
 ]
 
 
@@ -85,6 +85,8 @@ def load_library(path=LIB_PATH):
         "kh_selftest_gemm": (I, [I, I, I, I, P, P, P, P, S, P]),
         "kh_selftest_symeig": (I, [I, I, P, P, P, P, S, P]),
         "kh_selftest_svd": (I, [I, I, P, P, P, P, P, S, P]),
+        "kh_gemm_noalloc": (I, [I, I, I, I, P, P, P, P]),
+        "kh_gemm_noalloc_max_bytes": (S, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -150,6 +152,20 @@ def selftest_svd(X, prec="fp64"):
     if st != KH_OK:
         raise KhError(st, "kh_selftest_svd")
     return S, L, Q
+
+
+def gemm_noalloc(A, B, prec="fp64"):
+    """C = A @ B (FP64 CUDA tensors) through kh_gemm_noalloc: no device memory
+    is allocated by the library; it uses its static scratch array."""
+    import torch
+    M, K = A.shape
+    N = B.shape[1]
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    st = lib().kh_gemm_noalloc(PREC[prec], M, N, K, _tptr(A.contiguous()), _tptr(B.contiguous()), _tptr(C),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_gemm_noalloc")
+    return C
 
 
 def launch_count():

@@ -89,6 +89,21 @@ kh_status run(F&& f) {
 
 }  // namespace
 
+namespace kh {
+// The self-test GEMM body on a given scratch buffer (shared with noalloc.cu).
+kh_status selftest_gemm_on(int prec, int M, int N, int K, const double* A, const double* B, double* C,
+                           void* scratch, size_t bytes, cudaStream_t st) {
+    return run([&] {
+        if (prec == KH_FP64) run_gemm<double>(M, N, K, A, B, C, scratch, bytes, st);
+        else if (prec == KH_FP32) run_gemm<float>(M, N, K, A, B, C, scratch, bytes, st);
+        else if (prec == KH_TF32) run_tc_gemm(1, M, N, K, A, B, C, scratch, bytes, st);
+        else if (prec == KH_TF32X3) run_tc_gemm(3, M, N, K, A, B, C, scratch, bytes, st);
+        else kh::fail(KH_EINVAL, "precision not built");
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+}  // namespace kh
+
 extern "C" {
 
 size_t kh_selftest_bytes(int M, int N, int K) {
