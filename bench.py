@@ -39,12 +39,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32")
+    ap.add_argument("--prec", default="tf32x3")
     ap.add_argument("--ctm-sweeps", type=int, default=4, help="CTM sweeps per gate layer")
     ap.add_argument("--obs-sweeps", type=int, default=2, help="CTM sweeps per mapping in the observables")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: = --steps")
+    ap.add_argument("--kernel", default="", choices=["", "tc_gemm"],
+                    help="profiling mode: run one library kernel on --size^3 operands instead of the bench")
+    ap.add_argument("--size", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -156,32 +159,40 @@ def peaks():
         "fallback"
 
 
-def roofline_for(prec, prof, pk, pk_src):
-    """Dominant timed kernel category -> achieved vs peak."""
-    kernels = {k: v for k, v in prof.items() if v["flops"] > 0}
-    cat = max(kernels, key=lambda k: kernels[k]["ms"])
-    c = prof[cat]
+def _peak(bound, prec, pk, pk_src):
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    if bound == "tensor":
+        if prec == "bf16":
+            return pk["bf16_tflops"], "bf16 %s (MEASURED_PEAKS.json)" % pk_src
+        return pk["bf16_tflops"] * 1.1 / 2.25, "tf32 = bf16 %s x 1.1/2.25 nominal ratio" % pk_src
+    if prec == "fp64":
+        return 1.25, "nominal FP64 1.25 TFLOP/s"
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "FP32 CUDA-core FMA peak 152 SM x 128 x 2 x %.0f MHz" % sm_mhz
+
+
+def roofline_entry(cat, c, bound, prec, pk, pk_src):
     if c["launches"] == 0 or c["ms"] <= 0:
-        return None, cat
+        return None
     per_launch_flops = c["flops"] / c["launches"]
     per_launch_s = c["ms"] * 1e-3 / c["launches"]
     achieved = per_launch_flops / per_launch_s / 1e12
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    if prec == "fp32":
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12            # FP32 CUDA-core FMA peak
-        bound, src = "alu", "FP32 CUDA-core peak 152 SM x 128 FMA x 2 x %.0f MHz" % sm_mhz
-    elif prec == "fp64":
-        peak = 1.25
-        bound, src = "alu", "nominal FP64 1.25 TFLOP/s"
-    elif prec == "bf16":
-        peak = pk["bf16_tflops"]
-        bound, src = "tensor", "bf16 %s" % pk_src
-    else:
-        peak = pk["bf16_tflops"] * 1.1 / 2.25
-        bound, src = "tensor", "tf32 = bf16 %s x 1.1/2.25 nominal ratio" % pk_src
+    peak, src = _peak(bound, prec, pk, pk_src)
     return {"bound": bound, "kernel": cat, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": src,
-            "flops_per_launch": per_launch_flops, "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6}, cat
+            "frac": achieved / peak, "traffic": None, "peak_source": src, "flops_per_launch": per_launch_flops,
+            "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6}
+
+
+def roofline_for(prec, prof, pk, pk_src):
+    """Roofline of the dominant timed kernel category that has an algorithmic
+    flop model, plus the tensor-core kernel's own entry."""
+    tc = prec in ("tf32", "tf32x3", "bf16")
+    bounds = {"half_system_product": "tensor" if tc else "alu", "site_layer": "alu", "subspace_gemm": "alu"}
+    kernels = {k: v for k, v in prof.items() if k in bounds and v["flops"] > 0}
+    cat = max(kernels, key=lambda k: kernels[k]["ms"])
+    main = roofline_entry(cat, kernels[cat], bounds[cat], prec, pk, pk_src)
+    tc_entry = roofline_entry("half_system_product", prof["half_system_product"], bounds["half_system_product"],
+                              prec, pk, pk_src)
+    return main, tc_entry
 
 
 def run_ours(a, rank, world, local, pg):
@@ -265,7 +276,7 @@ def run_ours(a, rank, world, local, pg):
     out = None
     if rank == 0:
         pk, pk_src = peaks()
-        roof, cat = roofline_for(a.prec, prof, pk, pk_src)
+        roof, roof_tc = roofline_for(a.prec, prof, pk, pk_src)
         err = None
         if not a.no_fp64_check and a.prec != "fp64":
             err = fp64_check(a, g, dev, A0, B0, w, Hs, last, a.warmup + a.steps)
@@ -283,6 +294,7 @@ def run_ours(a, rank, world, local, pg):
             "E_site": last["E_site"] if last else None,
             "err_vs_fp64": err,
             "roofline": roof,
+            "roofline_tensor_core": roof_tc,
             "profile": prof,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -358,8 +370,33 @@ def run_reference(a, rank, world):
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_kernel(a):
+    """Profiling mode: the tensor-core contraction GEMM on size^3 operands
+    (inputs larger than L2), timed with CUDA events; one JSON line."""
+    import torch
+    import paper_1906_02220_gb300 as g
+    n = a.size
+    gen = torch.Generator(device="cuda:0").manual_seed(0)
+    A = torch.randn((n, n), dtype=torch.float64, device="cuda:0", generator=gen)
+    B = torch.randn((n, n), dtype=torch.float64, device="cuda:0", generator=gen)
+    for _ in range(a.warmup):
+        g.selftest_gemm(A, B, a.prec)
+    t = []
+    for _ in range(a.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.selftest_gemm(A, B, a.prec)
+        e1.record()
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1))
+    print(json.dumps({"kernel": "tc_gemm", "prec": a.prec, "size": n, "ms_incl_conversions": min(t)}))
+
+
 def main():
     a = parse()
+    if a.kernel:
+        run_kernel(a)
+        return
     rank, world, local, pg = dist_setup(a)
     if a.impl == "reference":
         out = run_reference(a, rank, world)
