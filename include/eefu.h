@@ -238,6 +238,18 @@ kh_status kh_selftest_symeig(int prec, int k, const double* dev_G, double* dev_W
 kh_status kh_selftest_svd(int prec, int k, const double* dev_X, double* dev_S, double* dev_L, double* dev_Q,
                           void* dev_scratch, size_t scratch_bytes, void* stream);
 
+/* Orthonormal basis of the columns of an n x k FP64 matrix Y (row-major) by
+ * the library's ordered CholQR2 (two Cholesky-QR passes, columns taken in
+ * order of decreasing norm), the orthonormalisation step of the projector's
+ * subspace iteration, in FP64 (k <= 112) or FP32 (k <= 160).  Columns of norm
+ * <= cut * (largest norm), and directions whose Cholesky pivot falls below
+ * the rounding floor, come out as zero columns of dev_Q (n x k, row-major);
+ * the others are orthonormal, the first one along the largest column of Y.
+ * Scratch as above with M = n, N = K = k.  KH_EINVAL for k beyond the limit.
+ * Synchronises stream. */
+kh_status kh_selftest_orth(int prec, int n, int k, double cut, const double* dev_Y, double* dev_Q,
+                           void* dev_scratch, size_t scratch_bytes, void* stream);
+
 /* --- allocation-free variant (the paper has no counterpart) ---------------- */
 
 /* Same result as kh_selftest_gemm (dev_C = dev_A dev_B, row-major FP64 device

@@ -27,7 +27,7 @@ ABI_FUNCTIONS = [
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
     "eefu_trotter_step", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
-    "kh_selftest_symeig", "kh_selftest_svd", "kh_gemm_noalloc", "kh_gemm_noalloc_max_bytes",
+    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_orth", "kh_gemm_noalloc", "kh_gemm_noalloc_max_bytes",
 ]
 
 
@@ -85,6 +85,7 @@ def load_library(path=LIB_PATH):
         "kh_selftest_gemm": (I, [I, I, I, I, P, P, P, P, S, P]),
         "kh_selftest_symeig": (I, [I, I, P, P, P, P, S, P]),
         "kh_selftest_svd": (I, [I, I, P, P, P, P, P, S, P]),
+        "kh_selftest_orth": (I, [I, I, I, D, P, P, P, S, P]),
         "kh_gemm_noalloc": (I, [I, I, I, I, P, P, P, P]),
         "kh_gemm_noalloc_max_bytes": (S, []),
     }
@@ -152,6 +153,22 @@ def selftest_svd(X, prec="fp64"):
     if st != KH_OK:
         raise KhError(st, "kh_selftest_svd")
     return S, L, Q
+
+
+def selftest_orth(Y, prec="fp64", cut=1e-12):
+    """Orthonormal basis (n x k, dropped directions as zero columns) of the
+    columns of the FP64 CUDA tensor Y by the library's ordered CholQR2."""
+    import torch
+    n, k = Y.shape
+    Q = torch.empty((n, k), dtype=torch.float64, device=Y.device)
+    nb = lib().kh_selftest_bytes(n, k, k)
+    scr = torch.empty(nb + 256, dtype=torch.uint8, device=Y.device)
+    base = (scr.data_ptr() + 255) // 256 * 256
+    st = lib().kh_selftest_orth(PREC[prec], n, k, float(cut), _tptr(Y.contiguous()), _tptr(Q),
+                                ctypes.c_void_p(base), nb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_orth")
+    return Q
 
 
 def gemm_noalloc(A, B, prec="fp64"):

@@ -81,11 +81,72 @@ __global__ void derived_kernel(const double* __restrict__ Tm, int p, int D, int 
     }
 }
 
+// Original-frame offset (l,u,r,d) of the frame-f legs (L,U,R,D) of T.
+__device__ __forceinline__ int frame_offset(int f, int L, int U, int R, int Dd, int D) {
+    int l = L, u = U, r = R, d = Dd;
+    for (int t = 0; t < f; ++t) {
+        int ol = d, ou = l, orr = u, od = r;
+        l = ol; u = ou; r = orr; d = od;
+    }
+    return ((l * D + u) * D + r) * D + d;
+}
+
+// Double-layer operands of the site contraction, in the K-major layout of a
+// GEMM's second operand: for kind 0 (corner, TL = [L,U][p][R,D]) and kind 1
+// (edge, TL = [L,D][p][U,R]) of frame f,
+//   Wt_f[(ok,ob)][(ib,ik)] = sum_p TL_f[ik][p][ok] TL_f[ib][p][ob]
+// summed in FP64.  With lo != null the value is stored as its TF32 head
+// (13 low mantissa bits cleared) in W and the FP32 remainder in lo.
+template <typename T>
+__global__ void wt_kernel(const double* __restrict__ Tm, int p, int D, T* Wc, T* We, T* Wc_lo, T* We_lo) {
+    const int d2 = D * D, d4 = d2 * d2;
+    const long long per = (long long)d4 * d4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 8 * per;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int kind = (int)(i / (4 * per));
+        const long long rem = i % (4 * per);
+        const int f = (int)(rem / per);
+        const long long idx = rem % per;
+        const int nn = (int)(idx / d4), kk = (int)(idx % d4);
+        const int ok = nn / d2, ob = nn % d2, ib = kk / d2, ik = kk % d2;
+        int ok_, ob_;
+        if (kind == 0) {     // in = (L,U), out = (R,D)
+            ok_ = frame_offset(f, ik / D, ik % D, ok / D, ok % D, D);
+            ob_ = frame_offset(f, ib / D, ib % D, ob / D, ob % D, D);
+        } else {             // in = (L,D), out = (U,R)
+            ok_ = frame_offset(f, ik / D, ok / D, ok % D, ik % D, D);
+            ob_ = frame_offset(f, ib / D, ob / D, ob % D, ib % D, D);
+        }
+        const long long D4 = d4;
+        double sacc = 0.0;
+        for (int pp = 0; pp < p; ++pp) sacc += Tm[pp * D4 + ok_] * Tm[pp * D4 + ob_];
+        T* W = (kind == 0 ? Wc : We) + rem;
+        T* Wl = kind == 0 ? Wc_lo : We_lo;
+        if (Wl) {
+            float v = (float)sacc;
+            float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+            *W = (T)h;
+            Wl[rem] = (T)(v - h);
+        } else {
+            *W = (T)sacc;
+        }
+    }
+}
+
 template <typename T>
 void Engine<T>::build_derived(Slot<T>& sl) {
     int tot = 4 * sl.p * dm.D4;
     derived_kernel<T><<<grid_for(tot), 256, 0, st>>>(sl.Ts, sl.p, dm.D, dm.pmax, sl.Tcor, sl.Tedg);
     KH_LAUNCHED();
+    // the double-layer form costs D^8 per block against 2 p D^6 layer by layer
+    sl.dl = dm.dl_alloc && dm.d2 <= 2 * sl.p;
+    if (sl.dl) {
+        const bool split = sizeof(T) == 4 && tc_npass == 3 && dm.D4 % 4 == 0;
+        const long long tot8 = 8LL * dm.D4 * dm.D4;
+        wt_kernel<T><<<grid_for(tot8), 256, 0, st>>>(sl.Ts, sl.p, dm.D, sl.Wcor, sl.Wedg,
+                                                     split ? sl.Wcor_lo : nullptr, split ? sl.Wedg_lo : nullptr);
+        KH_LAUNCHED();
+    }
 }
 
 template <typename T>

@@ -169,20 +169,47 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
     const bool a_kfast = (g.sAk == 1);
     const bool b_nfast = (g.sBn == 1);
-    for (int k0 = 0; k0 < g.K; k0 += GT_K) {
-        for (int e = tid; e < BM * GT_K; e += 256) {
+    // register double buffering: the next K tile's global loads are issued
+    // before the current tile's FMAs
+    constexpr int NA = BM * GT_K / 256, NB = BN * GT_K / 256;
+    static_assert(NA * 256 == BM * GT_K && NB * 256 == BN * GT_K, "tile/thread mismatch");
+    T ra[NA], rb[NB];
+    auto load_tiles = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < NA; ++t) {
+            const int e = tid + 256 * t;
             int mm, kk;
             if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
-            int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : T(0);
+            const int gm = m0 + mm, gk = k0 + kk;
+            ra[t] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : T(0);
         }
-        for (int e = tid; e < BN * GT_K; e += 256) {
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            const int e = tid + 256 * t;
             int nn, kb;
             if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
-            int gn = n0 + nn, gkb = k0 + kb;
-            Bs[kb][nn] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : T(0);
+            const int gn = n0 + nn, gkb = k0 + kb;
+            rb[t] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : T(0);
+        }
+    };
+    load_tiles(0);
+    for (int k0 = 0; k0 < g.K; k0 += GT_K) {
+#pragma unroll
+        for (int t = 0; t < NA; ++t) {
+            const int e = tid + 256 * t;
+            int mm, kk;
+            if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
+            As[kk][mm] = ra[t];
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            const int e = tid + 256 * t;
+            int nn, kb;
+            if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
+            Bs[kb][nn] = rb[t];
         }
         __syncthreads();
+        if (k0 + GT_K < g.K) load_tiles(k0 + GT_K);
 #pragma unroll
         for (int kk = 0; kk < GT_K; ++kk) {
             T a[TM], bb[TN];

@@ -42,6 +42,7 @@ Dims make_dims(const kh_config& c, bool fp64) {
     d.n = c.chi * d.d2;
     d.pmax = c.p_max;
     d.nslots = c.n_slots;
+    d.dl_alloc = d.d2 <= 2 * c.p_max;
     int kmax = fp64 ? 112 : 160;
     if (d.n <= kmax) {
         d.kk = d.n;
@@ -69,6 +70,15 @@ void Engine<T>::layout(Carver& cv) {
         s.E = cv.take<double>(4 * E1);
         s.Tcor = cv.take<T>(4LL * d.pmax * d.D4);
         s.Tedg = cv.take<T>(4LL * d.pmax * d.D4);
+        if (d.dl_alloc) {
+            const long long w = 4LL * d.D4 * d.D4;
+            s.Wcor = cv.take<T>(w);
+            s.Wedg = cv.take<T>(w);
+            if (sizeof(T) == 4) {
+                s.Wcor_lo = cv.take<T>(w);
+                s.Wedg_lo = cv.take<T>(w);
+            }
+        }
         s.Vw = cv.take<T>(4 * n * kk);
         s.spec = cv.take<double>(4LL * d.chi);
         s.prev = cv.take<double>(4LL * d.chi);
@@ -196,54 +206,75 @@ __global__ void rand_kernel(T* V, long long tot, uint64_t seed, uint64_t stream)
         V[i] = (T)rnd_uniform(seed, stream, (uint64_t)i);
 }
 
-// Gram G = Z^T Z (Z: n x k row-major), FP64 accumulation split over row chunks.
+// Gram G = Z^T Z (Z: n x k row-major, k <= 160): one CTA per chunk of rows,
+// staged in shared memory; thread (ti, tj) of a 16 x 16 grid accumulates
+// G[ti + 16 a][tj + 16 b] over the chunk (in T), chunk sums are added to the
+// FP64 result.
 template <typename T>
-__global__ void gram_kernel(const T* __restrict__ Z, int n, int k, double* __restrict__ G, int rows_per) {
-    int i = blockIdx.x * 16 + (threadIdx.x >> 4);
-    int j = blockIdx.y * 16 + (threadIdx.x & 15);
-    int r0 = blockIdx.z * rows_per, r1 = min(n, r0 + rows_per);
-    if (i >= k || j >= k) return;
-    double acc = 0.0;
-    if (sizeof(T) == 8) {
-        for (int r = r0; r < r1; ++r) acc += (double)Z[(long long)r * k + i] * (double)Z[(long long)r * k + j];
-    } else {
-        for (int r = r0; r < r1; r += 8) {
-            float f = 0.f;
-            int re = min(r1, r + 8);
-            for (int q = r; q < re; ++q) f = fmaf((float)Z[(long long)q * k + i], (float)Z[(long long)q * k + j], f);
-            acc += (double)f;
+__global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int n, int k, double* __restrict__ G,
+                                                   int rows_per) {
+    extern __shared__ unsigned char smem_raw[];
+    T* Ys = reinterpret_cast<T*>(smem_raw);   // rows_per x k
+    const int r0 = blockIdx.x * rows_per, nr = min(rows_per, n - r0);
+    for (int e = threadIdx.x; e < nr * k; e += blockDim.x) Ys[e] = Z[(long long)r0 * k + e];
+    __syncthreads();
+    const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+    for (int i = ti; i < k; i += 16) {
+        T acc[10];
+#pragma unroll
+        for (int bb = 0; bb < 10; ++bb) acc[bb] = T(0);
+        for (int r = 0; r < nr; ++r) {
+            const T yi = Ys[r * k + i];
+#pragma unroll
+            for (int bb = 0; bb < 10; ++bb) {
+                const int j = tj + 16 * bb;
+                if (j < k) acc[bb] = fma(yi, Ys[r * k + j], acc[bb]);
+            }
+        }
+#pragma unroll
+        for (int bb = 0; bb < 10; ++bb) {
+            const int j = tj + 16 * bb;
+            if (j < k) atomicAdd(&G[i * k + j], (double)acc[bb]);
         }
     }
-    atomicAdd(&G[i * k + j], acc);
 }
 
 template <typename T>
-static void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
+void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
+    if (k > 160) fail(KH_EINVAL, "gram: k > 160");
     KH_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * k * k, st));
-    int rows_per = 128;
-    dim3 grid((k + 15) / 16, (k + 15) / 16, (n + rows_per - 1) / rows_per);
-    gram_kernel<T><<<grid, 256, 0, st>>>(Z, n, k, dG, rows_per);
+    const int rows_per = 32;
+    gram_kernel<T><<<(n + rows_per - 1) / rows_per, 256, sizeof(T) * rows_per * k, st>>>(Z, n, k, dG, rows_per);
     KH_LAUNCHED();
 }
 
-// spectrum (first chi values, zero-padded), S^-1/2 with cut-off, discarded weight
+// spectrum (first chi values, zero-padded), S^-1/2 with cut-off, discarded
+// weight.  One block; every element handled by its own thread (a serial loop
+// here would pay a global-memory round trip per value).
 template <typename T>
 __global__ void finalize_spectrum_kernel(const T* sv, int k, int chi, double cut, const double* normM2,
                                          double* spec, T* isq, double* trunc) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int nkeep = min(chi, k);
-    double s0 = fmax((double)sv[0], 0.0);
+    __shared__ double red[32];
+    const int nkeep = min(chi, k);
+    const double s0 = fmax((double)sv[0], 0.0);
     double kept = 0.0;
-    for (int j = 0; j < chi; ++j) {
+    for (int j = threadIdx.x; j < chi; j += blockDim.x) {
         double s = (j < nkeep) ? fmax((double)sv[j], 0.0) : 0.0;
-        if (j < nkeep) kept += s * s;
+        kept += s * s;
         bool keep = (s0 > 0.0) && (s > cut * s0);
         spec[j] = keep ? s : 0.0;
-        isq[j] = keep ? (T)(1.0 / sqrt(s)) : T(0);
+        isq[j] = keep ? (T)rsqrt(s) : T(0);
     }
-    double tot = *normM2;
-    double tr = (tot > 0.0) ? (tot - kept) / tot : 0.0;
-    *trunc = tr > 0.0 ? tr : 0.0;
+    for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = kept;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        double tot = *normM2;
+        double tr = (tot > 0.0) ? (tot - t) / tot : 0.0;
+        *trunc = tr > 0.0 ? tr : 0.0;
+    }
 }
 
 template <typename T>
@@ -259,24 +290,31 @@ __global__ void store_normalized_kernel(const T* x, long long n, const double* s
 }
 
 __global__ void delta_kernel(const double* spec, double* prev, int chi, int prev_valid, double* delta) {
-    // one block of 32 threads: dir-wise normalised max difference
-    __shared__ double nrm[4];
-    int t = threadIdx.x;
-    if (t < 4) {
+    // one block: direction-wise normalised spectra, max |change| against the
+    // previous sweep; warp q < 4 normalises direction q
+    __shared__ double inv[4];
+    __shared__ double red[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (w < 4) {
         double s = 0.0;
-        for (int j = 0; j < chi; ++j) s += spec[t * chi + j] * spec[t * chi + j];
-        nrm[t] = s > 0.0 ? sqrt(s) : 1.0;
+        for (int j = lane; j < chi; j += 32) { double v = spec[w * chi + j]; s += v * v; }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) inv[w] = s > 0.0 ? rsqrt(s) : 1.0;
     }
     __syncthreads();
+    double d = 0.0;
+    for (int e = t; e < 4 * chi; e += blockDim.x) {
+        double v = spec[e] * inv[e / chi];
+        d = fmax(d, fabs(v - prev[e]));
+        prev[e] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if (lane == 0) red[w] = d;
+    __syncthreads();
     if (t == 0) {
-        double d = 0.0;
-        for (int q = 0; q < 4; ++q)
-            for (int j = 0; j < chi; ++j) {
-                double v = spec[q * chi + j] / nrm[q];
-                d = fmax(d, fabs(v - prev[q * chi + j]));
-                prev[q * chi + j] = v;
-            }
-        *delta = prev_valid ? d : INFINITY;
+        double m = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+        *delta = prev_valid ? m : INFINITY;
     }
 }
 
@@ -408,12 +446,32 @@ void Engine<T>::refresh_operands(Slot<T>& sl) {
 // Two-layer site contraction: for each of nb blocks,
 //   out[b][(o1k,o2k)][(o1b,o2b)] = sum_p sum TL[(i1k,i2k)][p][(o1k,o2k)]
 //                                  Y[b][(i1b,i2b)][(i1k,i2k)] TL[(i1b,i2b)][p][(o1b,o2b)]
-// with TL = T permuted to [in1][in2][p][out1][out2]: first the ket layer as one
-// GEMM (K = D^2), then the bra layer batched over b (K = p D^2).
+// with TL = T permuted to [in1][in2][p][out1][out2].
+//  Wt given (D^2 <= 2p): one GEMM with the double-layer tensor,
+//    out[b][(ok,ob)] = sum_{(ib,ik)} Y[b][(ib,ik)] Wt[(ok,ob)][(ib,ik)]   (2 nb D^8 flops),
+//    on the tensor cores when the precision asks for them;
+//  otherwise layer by layer: the ket layer as one GEMM (K = D^2), then the
+//    bra layer batched over b (K = p D^2)                                  (4 nb p D^6 flops).
 template <typename T>
-void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out) {
-    const int d2 = dm.d2;
+void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo) {
+    const int d2 = dm.d2, d4 = dm.D4;
     prof_begin(1);
+    if (Wt) {
+        if (tc_npass && sizeof(T) == 4 && d4 % 4 == 0) {       // TMA rows must be 16-byte multiples
+            TcOperand a{(const float*)Ybuf, nullptr, d4}, b{(const float*)Wt, nullptr, d4};
+            if (tc_npass == 3) {
+                float *yh = (float*)mup, *yl = (float*)mdn;     // nb D^4 = n^2 elements
+                tc_split((const float*)Ybuf, yh, yl, nb * d4, st);
+                a = TcOperand{yh, yl, d4};
+                b = TcOperand{(const float*)Wt, (const float*)Wt_lo, d4};
+            }
+            tc_gemm(a, b, (float*)out, (int)nb, d4, d4, d4, 1.f, 0.f, nullptr, tc_npass, tc_err, st);
+        } else {
+            gemm_rm<T>((int)nb, d4, d4, Ybuf, false, Wt, true, out, st);
+        }
+        prof_end(1, 2.0 * (double)nb * d4 * (double)d4);
+        return;
+    }
     gemm_rm<T>((int)(nb * d2), p * d2, d2, Ybuf, false, TL, false, Zk, st);
     for (long long b0 = 0; b0 < nb; b0 += 65535) {
         GemmArgs<T> g;
@@ -439,7 +497,9 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
     gemm_rm<T>(chi, d2 * chi, chi, C1, false, E1p, false, X, st);            // [x4][(uk,ub,z)]
     gemm_rm<T>(chi * d2, d2 * chi, chi, E4, false, X, false, Y1, st);        // [(w,lk,lb)][(uk,ub,z)]
     permute<T, T>(Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3}, st);  // [w][z][lb][ub][lk][uk]
-    site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt);  // [w][z][rk][dk][rb][db]
+    const long long w4 = (long long)f * dm.D4 * dm.D4;
+    site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wcor + w4 : nullptr,
+               sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr);                 // [w][z][rk][dk][rb][db]
     if (which == 0 && tc_npass)   // Q_s^T [(z,rk,rb)][(w,dk,db)]: K-major operand of Mt = Q_{s+3} Q_s
         permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {1, 2, 4, 0, 3, 5}, st);
     else
@@ -447,21 +507,27 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
 }
 
 // Orthonormal basis of the columns of Y (n x k) by two passes of the ordered
-// Cholesky-QR (cholqr_factor): dropped directions become zero columns.
+// Cholesky-QR (cholqr_factor): Uo = Y X_1 X_2, dropped directions become zero
+// columns.  The second pass, in the first pass's column order, restores the
+// orthogonality that the first loses to the conditioning of Y.  Scratch: tmp (n x k), Xk (k x k), dG (k x k FP64).
+template <typename T>
+void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T* Uo, cudaStream_t st) {
+    const double tau = sizeof(T) == 8 ? 1e-12 : 1e-5;
+    gram<T>(Y, n, k, dG, st);
+    cholqr_factor<T>(dG, k, cut, tau, Xk, st);
+    gemm_rm<T>(n, k, k, Y, false, Xk, false, tmp, st);
+    gram<T>(tmp, n, k, dG, st);
+    cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st, false);
+    gemm_rm<T>(n, k, k, tmp, false, Xk, false, Uo, st);
+}
+template void cholqr2<float>(const float*, int, int, double, float*, float*, double*, float*, cudaStream_t);
+template void cholqr2<double>(const double*, int, int, double, double*, double*, double*, double*, cudaStream_t);
+
 template <typename T>
 void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
     (void)G; (void)W; (void)L;
-    const double tau = sizeof(T) == 8 ? 1e-12 : 1e-5;
-    double* dG = dscr + 8192;
     prof_begin(8);
-    // CholQR2: two passes of the ordered Cholesky-QR (the second pass restores
-    // orthogonality lost to the conditioning of the first)
-    gram<T>(Y, n, k, dG, st);
-    cholqr_factor<T>(dG, k, cfg.svd_cut, tau, Xk, st);
-    gemm_rm<T>(n, k, k, Y, false, Xk, false, Qt, st);
-    gram<T>(Qt, n, k, dG, st);
-    cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st);
-    gemm_rm<T>(n, k, k, Qt, false, Xk, false, Uo, st);
+    cholqr2<T>(Y, n, k, cfg.svd_cut, Qt, Xk, dscr + 8192, Uo, st);
     prof_end(8, 0.0);
 }
 
@@ -506,14 +572,23 @@ __global__ void warm_split_kernel(const T* Vw, const int* live, int n, int k, T*
 // A warm-basis column is kept unless it is (near) zero, i.e. its direction
 // was dropped by the orthonormalisation: kept tail directions keep
 // converging by power iteration instead of restarting from random vectors.
+// One block: thread (part, c) sums rows part, part + parts, ... of column c
+// (consecutive threads read consecutive columns of a row: coalesced).
 template <typename T>
 __global__ void live_mask_kernel(const T* __restrict__ V, int n, int k, int* live) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int c = warp; c < k; c += nw) {
-        T a = T(0);
-        for (int r = lane; r < n; r += 32) { T v = V[(long long)r * k + c]; a = fma(v, v, a); }
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) live[c] = (a > T(0.25)) ? 1 : 0;
+    extern __shared__ float s_part[];                 // parts x k
+    const int parts = blockDim.x / k;
+    const int c = threadIdx.x % k, part = threadIdx.x / k;
+    if (part < parts) {
+        float a = 0.f;
+        for (int r = part; r < n; r += parts) { float v = (float)V[(long long)r * k + c]; a = fmaf(v, v, a); }
+        s_part[part * k + c] = a;
+    }
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < k; cc += blockDim.x) {
+        float a = 0.f;
+        for (int q = 0; q < parts; ++q) a += s_part[q * k + cc];
+        live[cc] = (a > 0.25f) ? 1 : 0;
     }
 }
 
@@ -616,11 +691,14 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         gemm_rm<T>(n, k, k, Vo, false, Lk, false, Z1, st);                     // right vectors of M
         gemm_rm<T>(n, k, k, U, false, Qk, false, Uf, st);                      // left vectors of M
         KH_CUDA(cudaMemcpyAsync(Vw, Z1, sizeof(T) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
-        live_mask_kernel<T><<<1, 512, 0, st>>>(Z1, n, k, live);
+        {
+            const int thr = 1024 / k * k;
+            live_mask_kernel<T><<<1, thr, sizeof(float) * thr, st>>>(Z1, n, k, live);
+        }
         KH_LAUNCHED();
         sl.warm[dir] = true;
     }
-    finalize_spectrum_kernel<T><<<1, 32, 0, st>>>(Sk, k, chi, cut, normM2, sl.spec + (long long)dir * chi, isq,
+    finalize_spectrum_kernel<T><<<1, 128, 0, st>>>(Sk, k, chi, cut, normM2, sl.spec + (long long)dir * chi, isq,
                                                   sl.trunc + dir);
     KH_LAUNCHED();
     const int nkeep = chi < k ? chi : k;
@@ -679,7 +757,9 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
     gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                  // C4n = C4E3 P~^T
     gemm_rm<T>(d2 * chi, d2 * chi, chi, E4, true, P, false, Y1, st);             // [(lk,lb,x4)][(dk,db,a)]
     permute<T, T>(Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3}, st);       // [x4][a][lb][db][lk][dk]
-    site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt);     // [x4][a][uk][rk][ub][rb]
+    const long long w4 = (long long)s * dm.D4 * dm.D4;
+    site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wedg + w4 : nullptr,
+               sl.dl && sl.Wedg_lo ? sl.Wedg_lo + w4 : nullptr);                 // [x4][a][uk][rk][ub][rb]
     permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
     gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // [a][rk][rb][a_up]
     double* ns = dscr + 8010;
@@ -724,7 +804,7 @@ int Engine<T>::sweep(int slot, int max_sweeps, int min_sweeps, double tol, doubl
     int done = 0;
     for (int it = 1; it <= max_sweeps; ++it) {
         for (int s = 0; s < 4; ++s) move(sl, s, slot);
-        delta_kernel<<<1, 32, 0, st>>>(sl.spec, sl.prev, dm.chi, sl.prev_valid ? 1 : 0, sl.delta);
+        delta_kernel<<<1, 256, 0, st>>>(sl.spec, sl.prev, dm.chi, sl.prev_valid ? 1 : 0, sl.delta);
         KH_LAUNCHED();
         sl.prev_valid = true;
         done = it;
@@ -874,22 +954,46 @@ void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long lo
                                                            sweeps, skip);
     KH_LAUNCHED();
 }
+template <typename T, int LP, int R>
+static void svd_jacobi_launch(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double tol, double cut,
+                              cudaStream_t st, int* sweep_count, int nrel) {
+    const int kp = (k + 1) & ~1;
+    size_t sm = (size_t)2 * kp * ((LP * R + 31) & ~31) * sizeof(T);
+    static size_t attr_set = 0;       // per instantiation
+    if (sm > 48 * 1024 && sm > attr_set) {
+        KH_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel<T, LP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sm));
+        attr_set = sm;
+    }
+    const int threads = ((kp / 2) * LP + 31) / 32 * 32;
+    svd_jacobi_kernel<T, LP, R><<<1, threads, sm, st>>>(X, k, sv, L, Qm, max_sweeps, tol, cut, sweep_count, nrel);
+    KH_LAUNCHED();
+}
+
+// Rows per lane chosen at compile time: 8 lanes per column pair, R (even)
+// rows per lane with 8 R >= kp (at most 640 threads).
 template <typename T>
 void svd_jacobi(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double tol, double cut, cudaStream_t st,
                 int* sweep_count, int nrel) {
-    if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "svd_jacobi: k beyond limit");
+    if (k > jacobi_kmax<T>() || k < 1) fail(KH_EINVAL, "svd_jacobi: k beyond limit");
     const int kp = (k + 1) & ~1;
-    size_t sm = (size_t)2 * kp * (kp + 1) * sizeof(T);
-    static size_t attr_set = 0;
-    if (sm > 48 * 1024 && sm > attr_set) {
-        KH_CUDA(cudaFuncSetAttribute(svd_jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_set = sm;
+#define KH_SVDJ(LP, R) svd_jacobi_launch<T, LP, R>(X, k, sv, L, Qm, max_sweeps, tol, cut, st, sweep_count, nrel)
+    if (kp <= 16) KH_SVDJ(8, 2);
+    else if (kp <= 32) KH_SVDJ(8, 4);
+    else if (kp <= 48) KH_SVDJ(8, 6);
+    else if (kp <= 64) KH_SVDJ(8, 8);
+    else if (kp <= 80) KH_SVDJ(8, 10);
+    else if (kp <= 96) KH_SVDJ(8, 12);
+    else if (kp <= 112) KH_SVDJ(8, 14);
+    else if constexpr (sizeof(T) == 4) {     // FP64 stops at k = 112
+        if (kp <= 128) KH_SVDJ(8, 16);
+        else if (kp <= 144) KH_SVDJ(8, 18);
+        else KH_SVDJ(8, 20);
     }
-    svd_jacobi_kernel<T><<<1, kJacobiThreads, sm, st>>>(X, k, sv, L, Qm, max_sweeps, tol, cut, sweep_count, nrel);
-    KH_LAUNCHED();
+#undef KH_SVDJ
 }
 template <typename T>
-void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st) {
+void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
     size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
     static size_t attr_set = 0;
@@ -897,11 +1001,11 @@ void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cu
         KH_CUDA(cudaFuncSetAttribute(cholqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set = sm;
     }
-    cholqr_kernel<T><<<1, kJacobiThreads, sm, st>>>(dG, k, cut_abs, tau, X);
+    cholqr_kernel<T><<<1, kJacobiThreads, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0);
     KH_LAUNCHED();
 }
-template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t);
-template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t);
+template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t, bool);
+template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t, bool);
 
 template void svd_jacobi<float>(const float*, int, float*, float*, float*, int, double, double, cudaStream_t, int*,
                                 int);

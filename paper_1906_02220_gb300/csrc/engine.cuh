@@ -16,6 +16,13 @@ struct Slot {
     double* E = nullptr;      // 4 x chi x D^2 x chi
     T* Tcor = nullptr;        // 4 frames x [l][u][p][r][d]  (corner layer operand)
     T* Tedg = nullptr;        // 4 frames x [l][d][p][u][r]  (edge layer operand)
+    // double-layer operands (when D^2 <= 2p): 4 frames x [(ok,ob)][(ib,ik)],
+    // with their 3xTF32 low parts when the tensor cores run three passes
+    T* Wcor = nullptr;
+    T* Wedg = nullptr;
+    T* Wcor_lo = nullptr;
+    T* Wedg_lo = nullptr;
+    bool dl = false;          // the loaded tensor uses the double-layer operands
     T* Vw = nullptr;          // 4 dirs x n x kk  (warm projector subspaces)
     double* spec = nullptr;   // 4 x chi  last kept spectra (descending)
     double* prev = nullptr;   // 4 x chi  normalised spectra of the previous sweep
@@ -31,6 +38,7 @@ struct Slot {
 struct Dims {
     int D, d2, D4, chi, n, kk, pmax, nslots;
     bool full;                 // kk == n: exact Rayleigh-Ritz on the whole space
+    bool dl_alloc;             // D^2 <= 2 p_max: double-layer operands allocated
 };
 
 // ------------------------------------------------------------------ engine
@@ -135,7 +143,7 @@ struct Engine : EngineBase {
     // CTM internals
     void refresh_operands(Slot<T>& sl);
     void corner(Slot<T>& sl, int frame, int which);
-    void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out);
+    void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo);
     void projector(Slot<T>& sl, int dir, int slot_id);
     void orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L);
     void absorb(Slot<T>& sl, int s);
@@ -183,6 +191,11 @@ struct TcOperand {
 void tc_gemm(const TcOperand& A, const TcOperand& B, float* C, int M, int N, int K, long long ldc, float alpha,
              float beta, const float* colscale, int npass, int* err, cudaStream_t st);
 void tc_split(const float* x, float* hi, float* lo, long long n, cudaStream_t st);
+
+// Orthonormal basis of the columns of Y (n x k, k <= the Jacobi limit) by the
+// ordered CholQR2 (ctm.cu); see Engine::orth.
+template <typename T>
+void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T* Uo, cudaStream_t st);
 
 Dims make_dims(const kh_config& c, bool fp64);
 void validate(const kh_config& c);

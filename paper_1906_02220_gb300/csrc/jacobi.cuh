@@ -18,13 +18,18 @@ constexpr int kJacobiThreads = 512;
 template <typename T>
 __device__ __forceinline__ void round_robin_pair(int r, int i, int kp, int& p, int& q) {
     // circle method: player 0 fixed, players 1..kp-1 rotate with the round
-    int m = kp - 1;
+    // (r < m = kp - 1 and i < kp / 2, so each index wraps at most once)
+    const int m = kp - 1;
     if (i == 0) {
         p = 0;
-        q = 1 + (r % m);
+        q = 1 + r;
     } else {
-        p = 1 + ((r + i) % m);
-        q = 1 + ((r - i + m) % m);
+        int x = r + i;
+        if (x >= m) x -= m;
+        int y = r - i + m;
+        if (y >= m) y -= m;
+        p = 1 + x;
+        q = 1 + y;
     }
     if (p > q) { int t = p; p = q; q = t; }
 }
@@ -198,128 +203,219 @@ void svd_jacobi(const T* X, int k, T* s, T* L, T* Q, int max_sweeps, double tol,
                 int* sweep_count = nullptr, int nrel = 0);
 
 #ifdef KH_JACOBI_KERNEL
-// 8-lane groups, one column pair per group (64 groups = every pair of a
-// round in flight for k <= 128); columns stored contiguously with an odd
-// stride.  A sweep ends the iteration when no pair needed a rotation, or when
-// the largest pair cosine stops falling quadratically while already below
-// 1e3 * eps (the rounding floor of the column dot products).
-template <typename T>
-__global__ void __launch_bounds__(kJacobiThreads)
+// Rotation (c, s) that orthogonalises two columns with squared norms a, b and
+// inner product g (the symmetric 2x2 Schur rotation of [[a, g], [g, b]]).
+// FP32 uses the hardware reciprocal / reciprocal-square-root approximations:
+// c and s stay a rotation to a few ulps, and an inexact angle only leaves a
+// residual that the next sweep removes.
+__device__ __forceinline__ void jacobi_rotation(float a, float b, float g, float& c, float& s) {
+    const float zeta = __fdividef(b - a, 2.f * g);
+    const float az = fabsf(zeta);
+    float t;
+    if (az > 1e15f) {
+        t = __fdividef(0.5f, az);
+    } else {
+        const float r = fmaf(az, az, 1.f);
+        t = __fdividef(1.f, az + r * rsqrtf(r));
+    }
+    t = copysignf(t, zeta);
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = c * t;
+}
+__device__ __forceinline__ void jacobi_rotation(double a, double b, double g, double& c, double& s) {
+    const double zeta = (b - a) / (2.0 * g);
+    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    c = 1.0 / sqrt(1.0 + t * t);
+    s = c * t;
+}
+
+// LP-lane groups (LP = 8), one column pair per group and every pair of a
+// round in flight (kp/2 groups); lane l of a group owns rows l, l + LP, ...,
+// l + (R-1) LP, so all row loops are unrolled at compile time.  The matrix is
+// scaled by a power of two so that its largest entry is O(1) (exact), which
+// lets the convergence test use squared cosines g^2 <= tol^2 a b without
+// square roots.  Columns are stored contiguously with a stride that is a
+// multiple of 32 words, zero below row k; the four groups of a warp walk the
+// row blocks of their columns in orders shifted by their slot, so that a load
+// of block j touches banks 8 ((j + slot) mod R mod 4) + lane: conflict-free
+// except where the shifted order wraps.  A sweep ends the iteration when no pair
+// needed a rotation, or when the largest pair cosine stops falling
+// quadratically while already below 1e3 eps (the rounding floor of the
+// column dot products).
+template <typename T, int LP, int R>
+__global__ void __launch_bounds__(LP * R / 2 * LP)
 svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __restrict__ L_out,
                   T* __restrict__ Q_out, int max_sweeps, double tol, double cut, int* sweep_count, int nrel) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr int RL = LP * R;
+    constexpr bool kPrefetchQ = sizeof(T) * R <= 48;   // keep the Q column pair in registers too
     const int kp = (k + 1) & ~1;
-    const int ld = kp + 1;                     // odd column stride
+    const int ld = (RL + 31) & ~31;            // column stride: whole bank rows
     T* Xc = reinterpret_cast<T*>(smem_raw);   // Xc[c * ld + r]
     T* Qc = Xc + kp * ld;
-    __shared__ int s_rot;
-    __shared__ float s_cmax;
-    __shared__ double s_norm[160];
+    __shared__ T s_wmax[32];
+    __shared__ int s_wrot[32];
+    __shared__ T s_norm[160];
     __shared__ T s_cn[160];
     __shared__ unsigned char s_top[160];
+    __shared__ T s_scale;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int grp = tid >> 3, gl = tid & 7, ngrp = nt >> 3;
-    const unsigned gmask = 0xFFu << (tid & 24);
+    const int grp = tid / LP, gl = tid % LP;
+    const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+    const unsigned gmask = (LP >= 32) ? 0xffffffffu : (((1u << LP) - 1u) << (lane & ~(LP - 1)));
     const double eps = sizeof(T) == 8 ? 1.1e-16 : 6e-8;
-    for (int e = tid; e < kp * kp; e += nt) {
-        int c = e / kp, r = e % kp;
-        Xc[c * ld + r] = (r < k && c < k) ? Xin[(long long)r * k + c] : T(0);
-        Qc[c * ld + r] = (r == c) ? T(1) : T(0);
+    // exact power-of-two scaling: largest |entry| in [1, 2)
+    T mx = T(0);
+    for (int e = tid; e < k * k; e += nt) mx = fmax(mx, fabs(Xin[e]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_wmax[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        T m = T(0);
+        for (int w = 0; w < nw; ++w) m = fmax(m, s_wmax[w]);
+        int ex = 0;
+        if (m > T(0)) frexp(m, &ex);
+        s_scale = (m > T(0)) ? (T)ldexp(1.0, 1 - ex) : T(1);
+    }
+    __syncthreads();
+    const T scale = s_scale;
+    for (int e = tid; e < kp * ld; e += nt) {
+        int c = e / ld, r = e % ld;
+        Xc[e] = (r < k && c < k) ? Xin[(long long)r * k + c] * scale : T(0);
+        Qc[e] = (r == c) ? T(1) : T(0);
     }
     // the cosine of two columns is only known to ~k eps (dot-product rounding)
     const T tol_eff = (T)fmax(tol, 2.0 * k * eps);
-    float prev_cmax = 1e30f;
+    const T tol2 = tol_eff * tol_eff;
+    const T floor2 = (T)(1e6 * eps * eps);
+    T prev2 = T(1e30);
     int sw = 0;
     if (nrel <= 0 || nrel > kp) nrel = kp;
+    const bool active = grp < kp / 2;
+    int offs[R];                               // row-block offsets in this group's order
+    {
+        int jb = (grp % (32 / LP)) % R;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            offs[j] = LP * jb;
+            if (++jb == R) jb = 0;
+        }
+    }
     for (; sw < max_sweeps; ++sw) {
-        if (tid == 0) { s_rot = 0; s_cmax = 0.f; }
+        __syncthreads();
         if (nrel < kp) {
             // columns among the nrel largest must converge; tail-tail pairs are
             // still rotated but do not keep the sweep loop alive
-            const int w0 = tid >> 5, l0 = tid & 31, nw0 = nt >> 5;
-            for (int c = w0; c < kp; c += nw0) {
+            for (int c = warp; c < kp; c += nw) {
                 T a = T(0);
-                for (int row = l0; row < kp; row += 32) { T u = Xc[c * ld + row]; a = fma(u, u, a); }
+                for (int row = lane; row < kp; row += 32) { T u = Xc[c * ld + row]; a = fma(u, u, a); }
                 for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if (l0 == 0) s_cn[c] = a;
+                if (lane == 0) s_cn[c] = a;
             }
             __syncthreads();
             for (int c = tid; c < kp; c += nt) {
                 int rank = 0;
-                for (int j = 0; j < kp; ++j) rank += (s_cn[j] > s_cn[c]) || (s_cn[j] == s_cn[c] && j < c);
+                const T cc = s_cn[c];
+                for (int j = 0; j < kp; ++j) rank += (s_cn[j] > cc) || (s_cn[j] == cc && j < c);
                 s_top[c] = rank < nrel;
             }
         } else {
             for (int c = tid; c < kp; c += nt) s_top[c] = 1;
         }
         __syncthreads();
+        T c2max = T(0);
+        int rot = 0;
         for (int r = 0; r < kp - 1; ++r) {
-            for (int i = grp; i < kp / 2; i += ngrp) {
+            if (active) {
                 int p, q;
-                round_robin_pair<T>(r, i, kp, p, q);
-                T* xp = Xc + p * ld;
-                T* xq = Xc + q * ld;
-                T a = T(0), b = T(0), g = T(0);
-                for (int row = gl; row < kp; row += 8) {
-                    T u = xp[row], v = xq[row];
-                    a = fma(u, u, a); b = fma(v, v, b); g = fma(u, v, g);
+                round_robin_pair<T>(r, grp, kp, p, q);
+                T* xp = Xc + p * ld + gl;
+                T* xq = Xc + q * ld + gl;
+                T* qp = Qc + p * ld + gl;
+                T* qq = Qc + q * ld + gl;
+                T u[R], v[R], qu[R], qv[R];
+#pragma unroll
+                for (int j = 0; j < R; ++j) { u[j] = xp[offs[j]]; v[j] = xq[offs[j]]; }
+                if (kPrefetchQ) {
+#pragma unroll
+                    for (int j = 0; j < R; ++j) { qu[j] = qp[offs[j]]; qv[j] = qq[offs[j]]; }
                 }
-                for (int o = 4; o > 0; o >>= 1) {
+                T a = T(0), b = T(0), g = T(0);
+#pragma unroll
+                for (int j = 0; j < R; ++j) { a = fma(u[j], u[j], a); b = fma(v[j], v[j], b); g = fma(u[j], v[j], g); }
+#pragma unroll
+                for (int o = LP / 2; o > 0; o >>= 1) {
                     a += __shfl_xor_sync(gmask, a, o);
                     b += __shfl_xor_sync(gmask, b, o);
                     g += __shfl_xor_sync(gmask, g, o);
                 }
-                T den = sqrt(a) * sqrt(b);
-                if (g == T(0) || den == T(0)) continue;            // group-uniform
-                const bool rel = s_top[p] || s_top[q];
-                float cosv = (float)(fabs(g) / den);
-                if (gl == 0 && rel) atomicMax((int*)&s_cmax, __float_as_int(cosv));
-                if (fabs(g) <= tol_eff * den) continue;
-                T zeta = (b - a) / (T(2) * g);
-                T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-                T cT = T(1) / sqrt(T(1) + t * t), sT = cT * t;
-                T* qp = Qc + p * ld;
-                T* qq = Qc + q * ld;
-                for (int row = gl; row < kp; row += 8) {
-                    T u = xp[row], v = xq[row];
-                    xp[row] = cT * u - sT * v;
-                    xq[row] = sT * u + cT * v;
-                    T qu = qp[row], qv = qq[row];
-                    qp[row] = cT * qu - sT * qv;
-                    qq[row] = sT * qu + cT * qv;
+                // a, b, g are bitwise equal in all lanes of the group: the
+                // branches below are group-uniform
+                const T ab = a * b, g2 = g * g;
+                if (g != T(0) && ab > T(0)) {
+                    const bool rel = s_top[p] | s_top[q];
+                    if (rel) c2max = fmax(c2max, g2 / ab);
+                    if (g2 > tol2 * ab) {
+                        T cT, sT;
+                        jacobi_rotation(a, b, g, cT, sT);
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            xp[offs[j]] = cT * u[j] - sT * v[j];
+                            xq[offs[j]] = sT * u[j] + cT * v[j];
+                        }
+                        if (!kPrefetchQ) {
+#pragma unroll
+                            for (int j = 0; j < R; ++j) { qu[j] = qp[offs[j]]; qv[j] = qq[offs[j]]; }
+                        }
+#pragma unroll
+                        for (int j = 0; j < R; ++j) {
+                            qp[offs[j]] = cT * qu[j] - sT * qv[j];
+                            qq[offs[j]] = sT * qu[j] + cT * qv[j];
+                        }
+                        rot |= rel;
+                    }
                 }
-                if (gl == 0 && rel) atomicAdd(&s_rot, 1);
             }
             __syncthreads();
         }
-        const float cmax = s_cmax;
-        const int rot = s_rot;
+        // block-wide max squared cosine and rotation flag, once per sweep
+        for (int o = 16; o > 0; o >>= 1) {
+            c2max = fmax(c2max, __shfl_xor_sync(0xffffffffu, c2max, o));
+            rot |= __shfl_xor_sync(0xffffffffu, rot, o);
+        }
+        if (lane == 0) { s_wmax[warp] = c2max; s_wrot[warp] = rot; }
         __syncthreads();
-        if (rot == 0) break;
-        if (cmax < 1e3f * (float)eps && cmax > 0.25f * prev_cmax) break;   // stagnated at the floor
-        prev_cmax = cmax;
+        T bmax = T(0);
+        int brot = 0;
+        for (int w = 0; w < nw; ++w) { bmax = fmax(bmax, s_wmax[w]); brot |= s_wrot[w]; }
+        if (brot == 0) break;
+        if (bmax < floor2 && bmax > T(0.0625) * prev2) break;   // stagnated at the floor
+        prev2 = bmax;
     }
+    __syncthreads();
     if (sweep_count && tid == 0) atomicAdd(sweep_count, sw + 1);
-    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     for (int c = warp; c < kp; c += nw) {
         T a = T(0);
         for (int row = lane; row < kp; row += 32) { T u = Xc[c * ld + row]; a = fma(u, u, a); }
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) s_norm[c] = (c < k) ? (double)sqrt(a) : -1.0;
+        if (lane == 0) s_norm[c] = (c < k) ? sqrt(a) : T(-1);
     }
     __syncthreads();
-    double smax = 0.0;
-    for (int c = 0; c < k; ++c) smax = fmax(smax, s_norm[c]);
+    T smax = T(0);
+    for (int c = lane; c < k; c += 32) smax = fmax(smax, s_norm[c]);
+    for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    const T cutT = (T)cut, rscale = T(1) / scale;
     for (int c = warp; c < k; c += nw) {
-        double sc = s_norm[c];
+        const T sc = s_norm[c];
         int rank = 0;
-        for (int j = 0; j < k; ++j) rank += (s_norm[j] > sc) || (s_norm[j] == sc && j < c);
-        T inv = (smax > 0.0 && sc > cut * smax) ? (T)(1.0 / sc) : T(0);
+        for (int j = lane; j < k; j += 32) rank += (s_norm[j] > sc) || (s_norm[j] == sc && j < c);
+        for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+        const T inv = (smax > T(0) && sc > cutT * smax) ? T(1) / sc : T(0);
         for (int row = lane; row < k; row += 32) {
             L_out[(long long)row * k + rank] = Xc[c * ld + row] * inv;
             Q_out[(long long)row * k + rank] = Qc[c * ld + row];
         }
-        if (lane == 0) s_out[rank] = (T)sc;
+        if (lane == 0) s_out[rank] = sc * rscale;
     }
 }
 #endif  // KH_JACOBI_KERNEL
@@ -332,36 +428,44 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
 // (in sorted order, dropped ones zero).  Unlike a symmetric (Loewdin)
 // orthogonalisation, a weak column nearly parallel to a strong one never
 // rotates the strong one.
+// sorted = false keeps the given column order (a second pass over columns that
+// are already orthonormal: their norms carry no information).
 template <typename T>
-void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st);
+void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted = true);
 
 #ifdef KH_JACOBI_KERNEL
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads)
-cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X) {
+cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted) {
     extern __shared__ unsigned char smem_raw[];
     const int ld = k | 1;                          // odd row stride: conflict-free column walks
     T* Lm = reinterpret_cast<T*>(smem_raw);       // k x ld, row-major
     T* Li = Lm + k * ld;
-    __shared__ T s_inv[160];
+    __shared__ T s_inv[160], s_rs[160], s_rdiag[160], s_diag[160];
     __shared__ int s_perm[160];
     __shared__ int s_keep[160];
-    __shared__ double s_diag[160];
-    __shared__ double s_max;
+    __shared__ T s_max;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int j = tid; j < k; j += nt) s_diag[j] = G[(long long)j * k + j];
+    const T tauT = (T)tau;
+    for (int j = tid; j < k; j += nt) s_diag[j] = (T)fmax(G[(long long)j * k + j], 0.0);
     __syncthreads();
-    if (tid == 0) {
-        double m = 0.0;
-        for (int j = 0; j < k; ++j) m = fmax(m, s_diag[j]);
-        s_max = sqrt(fmax(m, 0.0));
+    if (warp == 0) {
+        T m = T(0);
+        for (int j = lane; j < k; j += 32) m = fmax(m, s_diag[j]);
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_max = sqrt(m);
     }
     __syncthreads();
+    const T cutT = (T)cut_abs;
     for (int j = tid; j < k; j += nt) {
-        double nj = sqrt(fmax(s_diag[j], 0.0));
-        s_inv[j] = (s_max > 0.0 && nj > cut_abs * s_max) ? (T)(1.0 / nj) : T(0);
-        int rank = 0;
-        for (int i = 0; i < k; ++i) rank += (s_diag[i] > s_diag[j]) || (s_diag[i] == s_diag[j] && i < j);
+        const T dj = s_diag[j];
+        const T nj = sqrt(dj);
+        s_inv[j] = (s_max > T(0) && nj > cutT * s_max) ? T(1) / nj : T(0);
+        int rank = j;
+        if (sorted) {
+            rank = 0;
+            for (int i = 0; i < k; ++i) rank += (s_diag[i] > dj) || (s_diag[i] == dj && i < j);
+        }
         s_perm[rank] = j;
     }
     __syncthreads();
@@ -369,48 +473,60 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
         int a = e / k, b = e % k;
         int pa = s_perm[a], pb = s_perm[b];
         Lm[a * ld + b] = (T)G[(long long)pa * k + pb] * s_inv[pa] * s_inv[pb];
-        Li[a * ld + b] = T(0);
     }
     __syncthreads();
+    // Right-looking Cholesky on the lower triangle with unscaled columns:
+    // step j leaves the Schur-complement entries a_ij (i > j) in column j and
+    // subtracts a_ij a_cj / d_j from the trailing block; L_ij = a_ij / sqrt(d_j)
+    // is applied afterwards.  A pivot d_j <= tau drops direction j (no update).
     for (int j = 0; j < k; ++j) {
         const T d = Lm[j * ld + j];
-        const bool keep = (double)d > tau;        // same value in every thread
-        if (keep) {
-            const T ljj = sqrt(d);
-            for (int i = j + 1 + tid; i < k; i += nt) Lm[i * ld + j] /= ljj;
-            __syncthreads();
-            if (tid == 0) { Lm[j * ld + j] = ljj; s_keep[j] = 1; }
+        if (d > tauT) {                           // same value in every thread
+            const T rd = T(1) / d;
             for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
-                const T lij = Lm[i * ld + j];
+                const T lij = Lm[i * ld + j] * rd;
                 for (int c = j + 1 + lane; c <= i; c += 32) Lm[i * ld + c] -= lij * Lm[c * ld + j];
             }
-        } else {
-            __syncthreads();
-            for (int i = j + tid; i < k; i += nt) Lm[i * ld + j] = T(0);
-            if (tid == 0) s_keep[j] = 0;
         }
         __syncthreads();
     }
-    // Li = L^-1 on the kept index set, one warp per column
-    for (int j = warp; j < k; j += nw) {
-        if (!s_keep[j]) continue;
-        if (lane == 0) Li[j * ld + j] = T(1) / Lm[j * ld + j];
-        __syncwarp();
-        for (int i = j + 1; i < k; ++i) {
-            if (!s_keep[i]) continue;
+    for (int j = tid; j < k; j += nt) {
+        const T d = Lm[j * ld + j];
+        const bool keep = d > tauT;
+        s_keep[j] = keep;
+        const T sq = keep ? sqrt(d) : T(1);
+        s_rs[j] = keep ? T(1) / sq : T(0);
+        s_rdiag[j] = T(1) / sq;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {       // scale: L_ij = a_ij / sqrt(d_j), zero for dropped j
+        int i = e / k, j = e % k;
+        if (i > j) Lm[i * ld + j] *= s_rs[j];
+    }
+    __syncthreads();
+    // Li = L^-1 (dropped diagonal entries read as 1), four lanes per column j:
+    // Li[i][j] = -(sum_{m<i} L_im Li[m][j]) / L_ii for i > j, the sum split
+    // over the lanes by m mod 4 and combined by shuffles; every lane walks the
+    // same loop bounds (Li[m][j] = 0 for m < j).
+    for (int e = tid; e < 4 * ((k + 7) / 8 * 8); e += nt) {
+        const int j = e >> 2, part = e & 3;
+        const bool col = j < k;
+        for (int i = 0; i < k; ++i) {
             T sum = T(0);
-            for (int m = j + lane; m < i; m += 32) sum = fma(Lm[i * ld + m], Li[m * ld + j], sum);
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) Li[i * ld + j] = -sum / Lm[i * ld + i];
+            if (col)
+                for (int m = part; m < i; m += 4) sum = fma(Lm[i * ld + m], Li[m * ld + j], sum);
+            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+            if (col && part == 0) Li[i * ld + j] = (i < j) ? T(0) : ((i == j) ? s_rdiag[i] : -sum * s_rdiag[i]);
             __syncwarp();
         }
     }
     __syncthreads();
-    // X[perm a][b] = inv[perm a] * Li[b][a]   (Q = Y_s L^-T)
+    // X[perm a][b] = inv[perm a] * Li[b][a]   (Q = Y_s L^-T; dropped b give zero columns)
     for (int e = tid; e < k * k; e += nt) {
         int a = e / k, b = e % k;
         int pa = s_perm[a];
-        X[(long long)pa * k + b] = s_inv[pa] * Li[b * ld + a];
+        X[(long long)pa * k + b] = s_keep[b] ? s_inv[pa] * Li[b * ld + a] : T(0);
     }
 }
 #endif  // KH_JACOBI_KERNEL

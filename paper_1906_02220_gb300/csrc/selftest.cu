@@ -76,6 +76,19 @@ void run_svd(int k, const double* X, double* S, double* L, double* Qm, void* scr
     kh::cast<T, double>(q, Qm, (long long)k * k, st);
 }
 
+template <typename T>
+void run_orth(int n, int k, double cut, const double* Y, double* Q, void* scratch, size_t bytes, cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    T* y = cv.take<T>((size_t)n * k);
+    T* tmp = cv.take<T>((size_t)n * k);
+    T* u = cv.take<T>((size_t)n * k);
+    T* xk = cv.take<T>((size_t)k * k);
+    double* dg = cv.take<double>((size_t)k * k);
+    kh::cast<double, T>(Y, y, (long long)n * k, st);
+    kh::cholqr2<T>(y, n, k, cut, tmp, xk, dg, u, st);
+    kh::cast<T, double>(u, Q, (long long)n * k, st);
+}
+
 template <typename F>
 kh_status run(F&& f) {
     try {
@@ -145,6 +158,19 @@ kh_status kh_selftest_svd(int prec, int k, const double* X, double* S, double* L
     return run([&] {
         if (prec == KH_FP64) run_svd<double>(k, X, S, L, Qm, scratch, bytes, st);
         else run_svd<float>(k, X, S, L, Qm, scratch, bytes, st);
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+kh_status kh_selftest_orth(int prec, int n, int k, double cut, const double* Y, double* Qm, void* scratch,
+                           size_t bytes, void* stream) {
+    if (n < 1 || k < 1 || !Y || !Qm || !scratch || !(cut >= 0.0)) return KH_EINVAL;
+    if (k > (prec == KH_FP64 ? 112 : 160)) return KH_EINVAL;
+    if (bytes < kh_selftest_bytes(n, k, k)) return KH_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] {
+        if (prec == KH_FP64) run_orth<double>(n, k, cut, Y, Qm, scratch, bytes, st);
+        else run_orth<float>(n, k, cut, Y, Qm, scratch, bytes, st);
         KH_CUDA(cudaStreamSynchronize(st));
     });
 }

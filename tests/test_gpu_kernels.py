@@ -69,7 +69,8 @@ def test_jacobi_near_diagonal_relative_accuracy(g):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("k,decades", [(1, 0), (6, 3), (24, 9), (80, 12), (113, 6)])
+@pytest.mark.parametrize("k,decades", [(1, 0), (6, 3), (24, 9), (40, 6), (57, 6), (80, 12), (90, 6), (100, 8),
+                                       (113, 6), (150, 6)])
 def test_one_sided_jacobi_svd(g, prec, k, decades):
     """Singular values to absolute accuracy ~eps * s_1 (no squaring), also for
     a matrix with a null block; X Q = L S and Q orthogonal."""
@@ -88,6 +89,36 @@ def test_one_sided_jacobi_svd(g, prec, k, decades):
     assert np.abs(S - ref).max() <= 30 * eps * k * s[0]
     assert np.abs(Q.T @ Q - np.eye(k)).max() <= 30 * eps * k
     assert np.abs(X @ Q - L * S).max() <= 30 * eps * k * s[0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,k,decades", [(1, 1, 0), (37, 5, 2), (200, 33, 8), (1024, 80, 6), (300, 160, 4)])
+def test_cholqr2_orthonormal_basis(g, prec, n, k, decades):
+    """Ordered CholQR2 on graded columns with an exactly dependent and a zero
+    column: the kept columns are orthonormal, the dropped ones exactly zero,
+    their number equals the rank, span(Q) holds every column of Y, and the
+    first column lies along the largest column of Y."""
+    import torch
+    if prec == "fp64" and k > 112:
+        pytest.skip("beyond the FP64 Jacobi limit")
+    rng = np.random.default_rng(n + k)
+    Y = rng.standard_normal((n, k)) * np.logspace(0, -decades, k)[rng.permutation(k)]
+    rank = min(n, k)
+    if k > 4 and n > k:
+        Y[:, k - 1] = Y[:, 0] + 0.5 * Y[:, 1]
+        Y[:, k - 2] = 0.0
+        rank = k - 2
+    Q = g.selftest_orth(torch.as_tensor(Y, device="cuda:0"), prec).cpu().numpy()
+    eps = 2.3e-16 if prec == "fp64" else 1.2e-7
+    norms = np.linalg.norm(Q, axis=0)
+    live = norms > 0.5
+    assert np.all(norms[~live] == 0.0)
+    assert live.sum() == rank
+    Ql = Q[:, live]
+    assert np.abs(Ql.T @ Ql - np.eye(rank)).max() <= 50 * eps * k
+    assert np.abs(Y - Ql @ (Ql.T @ Y)).max() <= 1e3 * eps * np.abs(Y).max()
+    j0 = np.argmax(np.linalg.norm(Y, axis=0))
+    assert abs(Q[:, 0] @ Y[:, j0]) / np.linalg.norm(Y[:, j0]) > 1 - 1e3 * eps
 
 
 @pytest.mark.parametrize("prec", ["tf32", "tf32x3"])

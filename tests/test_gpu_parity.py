@@ -102,6 +102,28 @@ def test_ctm_metric_and_spectra_match_oracle(g, prec, D, chi):
         assert abs(tr - info["trunc"][d]) < max(1e-12, 1e-3 * info["trunc"][d]) + (0 if prec == "fp64" else 1e-5)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("D,p,chi", [(2, 1, 8), (3, 2, 12), (4, 2, 12)])
+def test_ctm_layered_path_matches_oracle(g, prec, D, p, chi):
+    """Tensors with D^2 > 2p take the layer-by-layer site contraction (the
+    double-layer operand would cost more there); converged metric and
+    projector spectra agree with the oracle.  (4, 2, 12) runs the subspace
+    iteration (n = 192)."""
+    T = kh_inputs.random_composite(D, 17 + D, p=p)
+    env, specs, _ = _oracle_ctm(T, chi, 0)
+    env, info = ctmrg.ctmrg(ctmrg.double_tensor(T), env, tol=1e-13, max_sweeps=300)
+    N_ref = ctmrg.metric(env, D)
+    ctx = g.Context(D, chi, prec, p_max=p, n_slots=1, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 300, 3, 1e-12 if prec == "fp64" else 1e-7, allow_noconv=True)
+    N = ctx.ctm_metric(0).cpu().numpy()
+    tol = TOL[prec]
+    assert np.abs(_nrm(N) - _nrm(N_ref)).max() < tol * 10
+    for d in range(4):
+        s, _ = ctx.ctm_projectors(0, d)
+        assert np.abs(_nrm(s.cpu().numpy()) - _nrm(info["spectra"][d])).max() < tol * 10
+
+
 def test_ctm_single_sweep_is_deterministic_and_exact_for_small_n(g):
     """With n = chi D^2 within the Jacobi limit the projector SVD is exact, so
     ONE sweep from the traced boundary matches the oracle's single sweep."""
