@@ -611,7 +611,7 @@ __global__ void add_kernel(const T* a, T* b, long long n) {
 //    M = L S (V_w Q)^T exactly; singular values to ~eps s_1 absolute.  V is
 //    kept orthonormal by one Newton-Schulz step V <- V (3 - V^T V)/2.
 //  subspace mode: Y = M V, U = orth(Y), Z = M^T U, V' = orth(Z), then the
-//    one-sided Jacobi SVD of H = V'^T Z gives M ~ (U Q) S (V' L)^T.  The warm
+//    one-sided Jacobi SVD of G = Z^T V' (G Q = L S) gives M ~ (U L) S (V' Q)^T.  The warm
 //    basis keeps its live columns and replaces dead ones by random vectors
 //    projected off the live span, so new tail directions are picked up.
 template <typename T>
@@ -684,12 +684,17 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
             orth(Z2, n, k, Vo, G2, W2, L2);                                    // V' = orth(Z)
             Vin = Vo;
         }
-        gemm_rm<T>(k, k, n, Vo, true, Z2, false, Hk, st, T(1), T(0), nullptr, skbuf, sk_elems);                      // H = V'^T Z
+        // G = H^T = Z^T V' with H = V'^T Z the Rayleigh-Ritz matrix (M ~ U G V'^T).
+        // V' = orth(Z) by the ordered CholQR makes H a column-permuted
+        // triangular factor with graded rows, so G's columns (H's rows) are
+        // nearly orthogonal already: the one-sided Jacobi of G is the
+        // QR-preconditioned Jacobi SVD and needs fewer sweeps than that of H.
+        gemm_rm<T>(k, k, n, Z2, true, Vo, false, Hk, st, T(1), T(0), nullptr, skbuf, sk_elems);
         prof_begin(7);
-        svd_jacobi<T>(Hk, k, Sk, Lk, Qk, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, chi + 8);   // H Q = L S
+        svd_jacobi<T>(Hk, k, Sk, Lk, Qk, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, chi + 8);   // G Q = L S
         prof_end(7, 0.0);
-        gemm_rm<T>(n, k, k, Vo, false, Lk, false, Z1, st);                     // right vectors of M
-        gemm_rm<T>(n, k, k, U, false, Qk, false, Uf, st);                      // left vectors of M
+        gemm_rm<T>(n, k, k, Vo, false, Qk, false, Z1, st);                     // right vectors of M: V' Q
+        gemm_rm<T>(n, k, k, U, false, Lk, false, Uf, st);                      // left vectors of M: U L
         KH_CUDA(cudaMemcpyAsync(Vw, Z1, sizeof(T) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
         {
             const int thr = 1024 / k * k;

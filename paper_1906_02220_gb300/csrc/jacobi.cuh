@@ -434,16 +434,26 @@ template <typename T>
 void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted = true);
 
 #ifdef KH_JACOBI_KERNEL
+__device__ __forceinline__ float chol_recip(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double chol_recip(double x) { return 1.0 / x; }
+
+// Right-looking Cholesky with one barrier per column (unscaled columns, the
+// scaling applied at the end), then the inverse of the triangular factor by
+// recursive doubling: the 8 x 8 diagonal blocks are inverted in parallel,
+// and at each level pairs of already inverted diagonal blocks A (above) and
+// C (below) are joined by Li_CA = -Li_CC (L_CA Li_AA), two parallel products
+// per level, the intermediate kept in the unused upper triangle of L.
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads)
 cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted) {
+    constexpr int KM = sizeof(T) == 8 ? 112 : 160;   // largest k
     extern __shared__ unsigned char smem_raw[];
     const int ld = k | 1;                          // odd row stride: conflict-free column walks
-    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x ld, row-major
-    T* Li = Lm + k * ld;
-    __shared__ T s_inv[160], s_rs[160], s_rdiag[160], s_diag[160];
-    __shared__ int s_perm[160];
-    __shared__ int s_keep[160];
+    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x ld, row-major (lower triangle: L)
+    T* Li = Lm + k * ld;                           // k x ld: L^-1
+    __shared__ T s_inv[KM], s_diag[KM], s_rs[KM];
+    __shared__ int s_perm[KM];
+    __shared__ int s_keep[KM];
     __shared__ T s_max;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const T tauT = (T)tau;
@@ -473,16 +483,16 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
         int a = e / k, b = e % k;
         int pa = s_perm[a], pb = s_perm[b];
         Lm[a * ld + b] = (T)G[(long long)pa * k + pb] * s_inv[pa] * s_inv[pb];
+        Li[a * ld + b] = T(0);
     }
     __syncthreads();
-    // Right-looking Cholesky on the lower triangle with unscaled columns:
-    // step j leaves the Schur-complement entries a_ij (i > j) in column j and
-    // subtracts a_ij a_cj / d_j from the trailing block; L_ij = a_ij / sqrt(d_j)
-    // is applied afterwards.  A pivot d_j <= tau drops direction j (no update).
+    // Cholesky: step j leaves the Schur-complement entries a_ij (i > j) in
+    // column j and subtracts a_ij a_cj / d_j from the trailing block; a pivot
+    // d_j <= tau drops direction j (no update, zero column).
     for (int j = 0; j < k; ++j) {
         const T d = Lm[j * ld + j];
         if (d > tauT) {                           // same value in every thread
-            const T rd = T(1) / d;
+            const T rd = chol_recip(d);
             for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
                 const T lij = Lm[i * ld + j] * rd;
                 for (int c = j + 1 + lane; c <= i; c += 32) Lm[i * ld + c] -= lij * Lm[c * ld + j];
@@ -494,34 +504,73 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
         const T d = Lm[j * ld + j];
         const bool keep = d > tauT;
         s_keep[j] = keep;
-        const T sq = keep ? sqrt(d) : T(1);
-        s_rs[j] = keep ? T(1) / sq : T(0);
-        s_rdiag[j] = T(1) / sq;
+        s_rs[j] = keep ? T(1) / sqrt(d) : T(0);
     }
     __syncthreads();
-    for (int e = tid; e < k * k; e += nt) {       // scale: L_ij = a_ij / sqrt(d_j), zero for dropped j
+    for (int e = tid; e < k * k; e += nt) {       // L_ij = a_ij / sqrt(d_j); unit diagonal for dropped j
         int i = e / k, j = e % k;
         if (i > j) Lm[i * ld + j] *= s_rs[j];
+        else if (i == j) Lm[i * ld + i] = s_keep[i] ? sqrt(Lm[i * ld + i]) : T(1);
     }
     __syncthreads();
-    // Li = L^-1 (dropped diagonal entries read as 1), four lanes per column j:
-    // Li[i][j] = -(sum_{m<i} L_im Li[m][j]) / L_ii for i > j, the sum split
-    // over the lanes by m mod 4 and combined by shuffles; every lane walks the
-    // same loop bounds (Li[m][j] = 0 for m < j).
-    for (int e = tid; e < 4 * ((k + 7) / 8 * 8); e += nt) {
-        const int j = e >> 2, part = e & 3;
-        const bool col = j < k;
-        for (int i = 0; i < k; ++i) {
-            T sum = T(0);
-            if (col)
-                for (int m = part; m < i; m += 4) sum = fma(Lm[i * ld + m], Li[m * ld + j], sum);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            if (col && part == 0) Li[i * ld + j] = (i < j) ? T(0) : ((i == j) ? s_rdiag[i] : -sum * s_rdiag[i]);
-            __syncwarp();
+    // diagonal 8 x 8 blocks of L^-1: lane c < 8 of warp w inverts column c of block w
+    const int nb = (k + 7) / 8;
+    for (int blk = warp; blk < nb; blk += nw) {
+        const int j0 = blk * 8, bs = min(8, k - j0);
+        if (lane < bs) {
+            const int c = lane;
+            T x[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int rr = r < bs ? r : bs - 1;        // in-bounds address for padded rows
+                T v = (r == c) ? T(1) : T(0);
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (m < r) v -= Lm[(j0 + rr) * ld + j0 + m] * x[m];
+                x[r] = v / Lm[(j0 + rr) * ld + j0 + rr];
+            }
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (r < bs) Li[(j0 + r) * ld + j0 + c] = x[r];
         }
     }
     __syncthreads();
+    // recursive doubling over spans s = 8, 16, 32, ...: A = rows [a0, a0+s),
+    // C = rows [a0+s, min(a0+2s, k)); Tm[c][a] = sum_m L[c][m] Li[m][a] stored
+    // at Lm[a][c] (upper triangle), then Li[c][a] = -sum_m Li[c][m] Tm[m][a]
+    for (int sp = 8; sp < k; sp *= 2) {
+        const int npair = (k + 2 * sp - 1) / (2 * sp);
+        // items: pair p, C row ci (< sp), A column aj (< sp)
+        const int items = npair * sp * sp;
+        for (int e = tid; e < items; e += nt) {
+            const int p = e / (sp * sp), rem = e % (sp * sp);
+            const int a0 = p * 2 * sp, ci = a0 + sp + rem / sp, aj = a0 + rem % sp;
+            if (ci >= k) continue;
+            T s0 = T(0), s1 = T(0);
+            int m = aj;
+            for (; m + 1 < a0 + sp; m += 2) {
+                s0 = fma(Lm[ci * ld + m], Li[m * ld + aj], s0);
+                s1 = fma(Lm[ci * ld + m + 1], Li[(m + 1) * ld + aj], s1);
+            }
+            if (m < a0 + sp) s0 = fma(Lm[ci * ld + m], Li[m * ld + aj], s0);
+            Lm[aj * ld + ci] = s0 + s1;
+        }
+        __syncthreads();
+        for (int e = tid; e < items; e += nt) {
+            const int p = e / (sp * sp), rem = e % (sp * sp);
+            const int a0 = p * 2 * sp, ci = a0 + sp + rem / sp, aj = a0 + rem % sp;
+            if (ci >= k) continue;
+            T s0 = T(0), s1 = T(0);
+            int m = a0 + sp;
+            for (; m + 1 <= ci; m += 2) {
+                s0 = fma(Li[ci * ld + m], Lm[aj * ld + m], s0);
+                s1 = fma(Li[ci * ld + m + 1], Lm[aj * ld + m + 1], s1);
+            }
+            if (m <= ci) s0 = fma(Li[ci * ld + m], Lm[aj * ld + m], s0);
+            Li[ci * ld + aj] = -(s0 + s1);
+        }
+        __syncthreads();
+    }
     // X[perm a][b] = inv[perm a] * Li[b][a]   (Q = Y_s L^-T; dropped b give zero columns)
     for (int e = tid; e < k * k; e += nt) {
         int a = e / k, b = e % k;
