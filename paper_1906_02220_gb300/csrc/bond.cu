@@ -200,7 +200,8 @@ __device__ __forceinline__ int row_index(int side, int o1, int o2, int t1, int t
 
 // X[(o1,o2)][j][(ph,k)] = sum_{t1,t2} N[row(o,t)][j] Oth[ph][t1][t2][k]
 __global__ void als_x_kernel(const double* __restrict__ N, const double* __restrict__ Oth, int D, int side,
-                             double* __restrict__ X) {
+                             double* __restrict__ X, const int* skip) {
+    if (skip && *skip) return;
     const int D4 = D * D * D * D, d2 = D * D;
     long long tot = (long long)d2 * D4 * 4 * D;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
@@ -219,56 +220,73 @@ __global__ void als_x_kernel(const double* __restrict__ N, const double* __restr
 }
 
 // R[(o1,o2,k)][(o1',o2',k')] = sum_{t1',t2',ph} X[(o1,o2)][row(o',t')][(ph,k)] Oth[ph][t1'][t2'][k']
-// S[(o1,o2,k)][q]           = sum_{j,ph} X[(o1,o2)][j][(ph,k)] Tp[pidx(q,ph)][j]
-__global__ void als_rs_kernel(const double* __restrict__ X, const double* __restrict__ Oth,
-                              const double* __restrict__ Tp, int D, int side, double* __restrict__ R,
-                              double* __restrict__ S) {
+// (one thread per entry)
+__global__ void als_r_kernel(const double* __restrict__ X, const double* __restrict__ Oth, int D, int side,
+                             double* __restrict__ R, const int* skip) {
+    if (skip && *skip) return;
     const int D4 = D * D * D * D, m = D * D * D;
-    long long totR = (long long)m * m, tot = totR + 4LL * m;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+    const long long totR = (long long)m * m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < totR;
          i += (long long)gridDim.x * blockDim.x) {
-        if (i < totR) {
-            int a = (int)(i / m), b = (int)(i % m);
-            int o1 = a / (D * D), o2 = (a / D) % D, k = a % D;
-            int q1 = b / (D * D), q2 = (b / D) % D, kp = b % D;
-            const double* x = X + (long long)(o1 * D + o2) * D4 * 4 * D;
-            double s = 0.0;
-            for (int t1 = 0; t1 < D; ++t1)
-                for (int t2 = 0; t2 < D; ++t2) {
-                    int j = row_index(side, q1, q2, t1, t2, D);
-                    for (int ph = 0; ph < 4; ++ph)
-                        s += x[((long long)j * 4 + ph) * D + k] * Oth[((ph * D + t1) * D + t2) * D + kp];
-                }
-            R[i] = s;
-        } else {
-            long long e = i - totR;
-            int a = (int)(e / 4), q = (int)(e % 4);
-            int o1 = a / (D * D), o2 = (a / D) % D, k = a % D;
-            const double* x = X + (long long)(o1 * D + o2) * D4 * 4 * D;
-            double s = 0.0;
-            for (int j = 0; j < D4; ++j)
-                for (int ph = 0; ph < 4; ++ph) {
-                    int pidx = (side == 0) ? (q * 4 + ph) : (ph * 4 + q);
-                    s += x[((long long)j * 4 + ph) * D + k] * Tp[(long long)pidx * D4 + j];
-                }
-            S[a * 4 + q] = s;
-        }
+        int a = (int)(i / m), b = (int)(i % m);
+        int o1 = a / (D * D), o2 = (a / D) % D, k = a % D;
+        int q1 = b / (D * D), q2 = (b / D) % D, kp = b % D;
+        const double* x = X + (long long)(o1 * D + o2) * D4 * 4 * D;
+        double s = 0.0;
+        for (int t1 = 0; t1 < D; ++t1)
+            for (int t2 = 0; t2 < D; ++t2) {
+                int j = row_index(side, q1, q2, t1, t2, D);
+                for (int ph = 0; ph < 4; ++ph)
+                    s += x[((long long)j * 4 + ph) * D + k] * Oth[((ph * D + t1) * D + t2) * D + kp];
+            }
+        R[i] = s;
+    }
+}
+
+// S[(o1,o2,k)][q] = sum_{j,ph} X[(o1,o2)][j][(ph,k)] Tp[pidx(q,ph)][j]
+// (one warp per entry, lanes over j: D^4 4 terms each)
+__global__ void als_s_kernel(const double* __restrict__ X, const double* __restrict__ Tp, int D, int side,
+                             double* __restrict__ S, const int* skip) {
+    if (skip && *skip) return;
+    const int D4 = D * D * D * D, m = D * D * D;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < 4LL * m; e += nwarps) {
+        int a = (int)(e / 4), q = (int)(e % 4);
+        int o1 = a / (D * D), o2 = (a / D) % D, k = a % D;
+        const double* x = X + (long long)(o1 * D + o2) * D4 * 4 * D;
+        double s = 0.0;
+        for (int j = lane; j < D4; j += 32)
+            for (int ph = 0; ph < 4; ++ph) {
+                int pidx = (side == 0) ? (q * 4 + ph) : (ph * 4 + q);
+                s += x[((long long)j * 4 + ph) * D + k] * Tp[(long long)pidx * D4 + j];
+            }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) S[a * 4 + q] = s;
     }
 }
 
 // One-CTA solve of (R + delta I) X = S (m x m, 4 right-hand sides) by a
-// right-looking Cholesky in global memory (work copy W).  X written to the
-// own tensor in layout [ph][o1][o2][k] = Own[ph][a].  flag[0] |= 1 on a
+// right-looking FP64 Cholesky, in shared memory when smem != 0 (dynamic size
+// (m^2 + 4m) doubles), else in the global work copy Wg.  Thread 0 forms each
+// pivot (FP64 division and square root are slow, so they are done once);
+// the columns are scaled after the factorisation.  X is written to the own
+// tensor in layout [ph][o1][o2][k] = Own[ph][a].  flag[0] |= 1 on a
 // non-positive pivot.  skip: if *skip, do nothing.
 __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __restrict__ S, int m, double reg,
-                                  double* __restrict__ W, double* __restrict__ Own, int* flag, const int* skip) {
+                                  double* __restrict__ Wg, double* __restrict__ Own, int* flag, const int* skip,
+                                  int smem) {
     if (skip && *skip) return;
-    __shared__ double s_delta;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) {
+    extern __shared__ double sh_w[];
+    __shared__ double s_delta, s_rd;
+    __shared__ double s_sq[512];
+    double* W = smem ? sh_w : Wg;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (warp == 0) {
         double tr = 0.0;
-        for (int i = 0; i < m; ++i) tr += R[(long long)i * m + i];
-        s_delta = reg * tr / m;
+        for (int i = lane; i < m; i += 32) tr += R[(long long)i * m + i];
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        if (lane == 0) s_delta = reg * tr / m;
     }
     __syncthreads();
     for (long long e = tid; e < (long long)m * m; e += nt) {
@@ -281,20 +299,25 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
     for (int j = 0; j < m; ++j) {
         if (tid == 0) {
             double dj = W[(long long)j * m + j];
-            if (!(dj > 0.0)) { flag[0] |= 1; dj = 1e-300; }
-            W[(long long)j * m + j] = sqrt(dj);
+            if (!(dj > 0.0)) { flag[0] |= 1; dj = 1e-300; W[(long long)j * m + j] = dj; }
+            s_rd = 1.0 / dj;
         }
         __syncthreads();
-        double ljj = W[(long long)j * m + j];
-        for (int i = j + 1 + tid; i < m; i += nt) W[(long long)i * m + j] /= ljj;
-        __syncthreads();
-        int rows = m - j - 1;
-        for (long long e = tid; e < (long long)rows * rows; e += nt) {
-            int i = j + 1 + (int)(e / rows), c = j + 1 + (int)(e % rows);
-            if (c <= i) W[(long long)i * m + c] -= W[(long long)i * m + j] * W[(long long)c * m + j];
+        const double rd = s_rd;
+        for (int i = j + 1 + warp; i < m; i += nw) {             // rows by warps, columns by lanes
+            const double lij = W[(long long)i * m + j] * rd;
+            for (int c = j + 1 + lane; c <= i; c += 32) W[(long long)i * m + c] -= lij * W[(long long)c * m + j];
         }
         __syncthreads();
     }
+    for (int j = tid; j < m; j += nt) s_sq[j] = sqrt(W[(long long)j * m + j]);
+    __syncthreads();
+    for (long long e = tid; e < (long long)m * m; e += nt) {     // L_ij = a_ij / sqrt(d_j)
+        int i = (int)(e / m), j = (int)(e % m);
+        if (i > j) W[e] /= s_sq[j];
+        else if (i == j) W[e] = s_sq[j];
+    }
+    __syncthreads();
     // forward: L y = S
     for (int j = 0; j < m; ++j) {
         double ljj = W[(long long)j * m + j];
@@ -324,20 +347,26 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
 }
 
 // cost d = sum_ph b^T R b - 2 b.S + c, with b = Own (layout [ph][a]); c = cost[0].
-// Writes cost[1 + slot] and compares with the previous value cost[2] -> flag[1].
+// Blocks add partial sums into cost[4]; the last block to finish forms
+// d, writes cost[1], compares with the previous value -> done[0], counts the
+// iteration in cost[3] and resets the accumulator (counter in done[1]).
+// skip: if *skip, do nothing.
 __global__ void als_cost_kernel(const double* __restrict__ R, const double* __restrict__ S,
                                 const double* __restrict__ Own, int m, double* cost, int* done, double tol,
-                                int first) {
+                                int first, const int* skip) {
+    if (skip && *skip) return;
     __shared__ double red[32];
+    __shared__ int s_last;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const long long gid = blockIdx.x * (long long)nt + tid, gst = (long long)gridDim.x * nt;
     double s = 0.0;
-    for (long long e = tid; e < (long long)m * m; e += nt) {
+    for (long long e = gid; e < (long long)m * m; e += gst) {
         int a = (int)(e / m), b = (int)(e % m);
         double r = R[e];
         for (int q = 0; q < 4; ++q) s += Own[q * m + a] * r * Own[q * m + b];
     }
-    for (int e = tid; e < 4 * m; e += nt) {
-        int a = e / 4, q = e % 4;
+    for (long long e = gid; e < 4 * m; e += gst) {
+        int a = (int)(e / 4), q = (int)(e % 4);
         s -= 2.0 * Own[q * m + a] * S[e];
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -346,14 +375,24 @@ __global__ void als_cost_kernel(const double* __restrict__ R, const double* __re
     if (tid == 0) {
         double t = 0.0;
         for (int w = 0; w < nt / 32; ++w) t += red[w];
-        double c = cost[0];
-        double dnew = t + c;
+        atomicAdd(&cost[4], t);
+        __threadfence();
+        s_last = (atomicAdd(&done[1], 1) == (int)gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && tid == 0) {
+        __threadfence();
+        const double t = atomicAdd(&cost[4], 0.0);
+        const double c = cost[0];
+        const double dnew = t + c;
         if (!first) {
-            double dold = cost[1];
-            if (c == 0.0 || fabs(dold - dnew) / c < tol) *done = 1;
+            const double dold = cost[1];
+            if (c == 0.0 || fabs(dold - dnew) / c < tol) done[0] = 1;
         }
         cost[1] = dnew;
-        cost[3] += 1.0;     // iterations counted
+        cost[3] += 1.0;     // evaluations counted
+        cost[4] = 0.0;
+        done[1] = 0;
     }
 }
 
@@ -572,42 +611,62 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     gemm_rm<double>(mT, D, mT, Tm, true, Wd, false, B2, st, 1.0, 0.0, colsc);
     // initial cost with (A'', B'') from the start: B-side normal equations from A''
     const int threads = 256;
-    als_x_kernel<<<grid_for(4LL * dm.d2 * D4 * D), threads, 0, st>>>(N, A2, D, 1, XA);
-    KH_LAUNCHED();
-    als_rs_kernel<<<grid_for((long long)m * m + 4 * m), threads, 0, st>>>(XA, A2, Tp, D, 1, R, S);
-    KH_LAUNCHED();
-    als_cost_kernel<<<1, 256, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 1);
-    KH_LAUNCHED();
-    int iters = 0;
-    for (int it = 1; it <= cfg.als_max_iter; ++it) {
-        // A step (fixed B'')
-        als_x_kernel<<<grid_for(4LL * dm.d2 * D4 * D), threads, 0, st>>>(N, B2, D, 0, XA);
-        KH_LAUNCHED();
-        als_rs_kernel<<<grid_for((long long)m * m + 4 * m), threads, 0, st>>>(XA, B2, Tp, D, 0, R, S);
-        KH_LAUNCHED();
-        chol_solve_kernel<<<1, 512, 0, st>>>(R, S, m, cfg.als_reg, Xmat, A2, flags, nullptr);
-        KH_LAUNCHED();
-        // B step (fixed A'')
-        als_x_kernel<<<grid_for(4LL * dm.d2 * D4 * D), threads, 0, st>>>(N, A2, D, 1, XA);
-        KH_LAUNCHED();
-        als_rs_kernel<<<grid_for((long long)m * m + 4 * m), threads, 0, st>>>(XA, A2, Tp, D, 1, R, S);
-        KH_LAUNCHED();
-        chol_solve_kernel<<<1, 512, 0, st>>>(R, S, m, cfg.als_reg, Xmat, B2, flags, nullptr);
-        KH_LAUNCHED();
-        als_cost_kernel<<<1, 256, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 0);
-        KH_LAUNCHED();
-        iters = it;
-        int hf[2];
-        KH_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
-        KH_CUDA(cudaStreamSynchronize(st));
-        if (hf[0]) fail(KH_ENUMERIC, "ALS: Cholesky breakdown (metric not positive)");
-        if (hf[1]) break;
+    const long long nX = 4LL * dm.d2 * D4 * D, nR = (long long)m * m;
+    const int sgrid = (int)((4LL * m * 32 + threads - 1) / threads);
+    const int cgrid = (int)std::min<long long>(32, (nR + threads - 1) / threads);
+    const size_t chol_sm = sizeof(double) * ((size_t)m * m + 4 * m);
+    const int chol_smem = chol_sm <= 200 * 1024 ? 1 : 0;
+    if (chol_smem && chol_sm > 48 * 1024) {
+        static size_t attr_set = 0;
+        if (chol_sm > attr_set) {
+            KH_CUDA(cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)chol_sm));
+            attr_set = chol_sm;
+        }
     }
-    double hc[2];
+    const int* done = flags + 1;
+    auto normal_eqs = [&](const double* oth, int side) {
+        als_x_kernel<<<grid_for(nX), threads, 0, st>>>(N, oth, D, side, XA, done);
+        KH_LAUNCHED();
+        als_r_kernel<<<grid_for(nR), threads, 0, st>>>(XA, oth, D, side, R, done);
+        KH_LAUNCHED();
+        als_s_kernel<<<sgrid, threads, 0, st>>>(XA, Tp, D, side, S, done);
+        KH_LAUNCHED();
+    };
+    normal_eqs(A2, 1);
+    als_cost_kernel<<<cgrid, threads, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 1, nullptr);
+    KH_LAUNCHED();
+    // Sweeps run on the device until the relative cost change is below the
+    // tolerance (flags[1] set by the cost kernel, after which every kernel of
+    // the loop returns at once); the host looks at the flags every few sweeps.
+    constexpr int kCheckEvery = 4;
+    for (int it = 1; it <= cfg.als_max_iter; ++it) {
+        normal_eqs(B2, 0);                                   // A step (fixed B'')
+        chol_solve_kernel<<<1, 512, chol_smem ? chol_sm : 0, st>>>(R, S, m, cfg.als_reg, Xmat, A2, flags, done,
+                                                                   chol_smem);
+        KH_LAUNCHED();
+        normal_eqs(A2, 1);                                   // B step (fixed A'')
+        chol_solve_kernel<<<1, 512, chol_smem ? chol_sm : 0, st>>>(R, S, m, cfg.als_reg, Xmat, B2, flags, done,
+                                                                   chol_smem);
+        KH_LAUNCHED();
+        als_cost_kernel<<<cgrid, threads, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 0, done);
+        KH_LAUNCHED();
+        if (it % kCheckEvery == 0 || it == cfg.als_max_iter) {
+            int hf[2];
+            KH_CUDA(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+            KH_CUDA(cudaStreamSynchronize(st));
+            if (hf[0]) fail(KH_ENUMERIC, "ALS: Cholesky breakdown (metric not positive)");
+            if (hf[1]) break;
+        }
+    }
+    double hc[4];
+    int hf0 = 0;
     KH_CUDA(cudaMemcpyAsync(hc, cost, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaMemcpyAsync(&hf0, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     KH_CUDA(cudaStreamSynchronize(st));
+    if (hf0) fail(KH_ENUMERIC, "ALS: Cholesky breakdown (metric not positive)");
     *rel_cost = hc[0] != 0.0 ? hc[1] / hc[0] : 0.0;
-    return iters;
+    return (int)hc[3] - 1;                                   // sweeps (the first evaluation is the start)
 }
 
 template <typename T>
