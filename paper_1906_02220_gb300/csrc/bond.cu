@@ -410,19 +410,19 @@ __global__ void tnt_kernel(const double* __restrict__ Tp, const double* __restri
     if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
 }
 
-// truncated-SVD start from the eigenpairs of Tm Tm^T (descending):
-// A''[(sA,aA,u,r)][k] = W[:,k] lam_k^{1/4}; colscale for B'' = Tm^T W lam^{-1/4}
+// truncated-SVD start from the singular triplets of Tm (descending sv):
+// A''[(sA,aA,u,r)][k] = U[:,k] s_k^{1/2}; colscale for B'' = Tm^T U s^{-1/2}
 template <typename TJ>
-__global__ void svd_init_kernel(const TJ* Wt, const TJ* Lt, int mT, int D, double* A2m, double* colsc, double* Wd) {
-    double l0 = (double)Lt[0];
+__global__ void svd_init_kernel(const TJ* Ut, const TJ* sv, int mT, int D, double* A2m, double* colsc, double* Wd) {
+    double s0 = (double)sv[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mT * D; i += gridDim.x * blockDim.x) {
         int r = i / D, k = i % D;
-        double lk = (k < mT) ? (double)Lt[k] : 0.0;
-        bool ok = (l0 > 0.0) && (lk > 1e-28 * l0);
-        double w = (double)Wt[(long long)r * mT + k];
-        A2m[i] = ok ? w * pow(lk, 0.25) : 0.0;
+        double sk = (k < mT) ? (double)sv[k] : 0.0;
+        bool ok = (s0 > 0.0) && (sk > 1e-14 * s0);
+        double w = (double)Ut[(long long)r * mT + k];
+        A2m[i] = ok ? w * sqrt(sk) : 0.0;
         Wd[i] = w;
-        if (r == 0) colsc[k] = ok ? pow(lk, -0.25) : 0.0;
+        if (r == 0) colsc[k] = ok ? 1.0 / sqrt(sk) : 0.0;
     }
 }
 
@@ -597,14 +597,13 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     KH_LAUNCHED();
     // truncated SVD start: Tm[(sA,aA,u,r)][(sB,aB,d,l)] from T'[sA,aA,sB,aB,l,u,r,d]
     permute<double, double>(Tp, Tm, {2, 2, 2, 2, D, D, D, D}, {0, 1, 5, 6, 2, 3, 7, 4}, st);
-    gemm_rm<double>(mT, mT, mT, Tm, false, Tm, true, Gt, st);               // Tm Tm^T
     double* colsc = dwork;
     double* Wd = dwork + 64;
     // The start only seeds the ALS, which then converges to tolerance in
-    // FP64, so its eigenvectors are taken from the FP32 Jacobi (FP64 Jacobi
-    // on one SM is ~60x slower on this part).
-    cast<double, float>(Gt, Gtf, (long long)mT * mT, st);
-    jacobi_eig<float>(Gtf, mT, mT, 0, Wtf, mT, 0, Ltf, 0, 1, 60, 2e-6, nullptr, nullptr, st);
+    // FP64, so the singular vectors come from the FP32 one-sided Jacobi of
+    // Tm^T (Tm^T Q = L S, so Tm = Q S L^T and U = Q).
+    permute<double, float>(Tm, Gtf, {mT, mT}, {1, 0}, st);
+    svd_jacobi<float>(Gtf, mT, Ltf, (float*)Gt, Wtf, 60, 2e-6, 0.0, st);
     svd_init_kernel<float><<<grid_for(mT * D), 256, 0, st>>>(Wtf, Ltf, mT, D, A2, colsc, Wd);
     KH_LAUNCHED();
     // B''[(sB,aB,d,l)][k] = sum_i Tm[i][.] Wd[i][k] colsc[k]

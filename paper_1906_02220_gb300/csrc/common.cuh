@@ -59,11 +59,32 @@ struct Carver {
 // ------------------------------------------------------------------ permutation
 
 constexpr int kMaxRank = 8;
+
+// Division of 32-bit n < 2^31 by a divisor d fixed on the host: with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, q = (umulhi(n, m) + n) >> l
+// (Granlund & Montgomery, "Division by invariant integers using multiplication").
+struct FastDiv {
+    uint32_t d, m, l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    f.l = l;
+    f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+    return f;
+}
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+    return (__umulhi(n, f.m) + n) >> f.l;
+}
+
 struct PermArgs {
     int rank;
     long long total;
     long long out_dims[kMaxRank];   // output shape (row-major)
     long long in_strides[kMaxRank]; // input stride of each output axis
+    FastDiv div[kMaxRank];          // output dims as fast divisors (32-bit path)
 };
 
 // out[i_0..i_{r-1}] = in[sum_j i_j * in_strides[j]]
@@ -78,6 +99,25 @@ __global__ void permute_kernel(const Ti* __restrict__ in, To* __restrict__ out, 
             long long i = rem % d;
             rem /= d;
             src += i * a.in_strides[j];
+        }
+        out[idx] = (To)in[src];
+    }
+}
+
+// Same with 32-bit index arithmetic (total < 2^31): multiply-shift divisions.
+template <typename Ti, typename To>
+__global__ void permute32_kernel(const Ti* __restrict__ in, To* __restrict__ out, PermArgs a) {
+    const uint32_t total = (uint32_t)a.total;
+    const uint32_t step = gridDim.x * blockDim.x;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += step) {
+        uint32_t rem = idx, src = 0;
+#pragma unroll
+        for (int j = kMaxRank - 1; j >= 0; --j) {
+            if (j < a.rank) {
+                const uint32_t q = fast_div(rem, a.div[j]);
+                src += (rem - q * a.div[j].d) * (uint32_t)a.in_strides[j];
+                rem = q;
+            }
         }
         out[idx] = (To)in[src];
     }
@@ -98,6 +138,7 @@ inline PermArgs make_perm(const std::vector<long long>& in_shape, const std::vec
     for (int j = 0; j < r; ++j) {
         a.out_dims[j] = in_shape[order[j]];
         a.in_strides[j] = in_str[order[j]];
+        if (a.out_dims[j] >= 1 && a.out_dims[j] < (1LL << 31)) a.div[j] = make_fastdiv((uint32_t)a.out_dims[j]);
     }
     return a;
 }
@@ -113,7 +154,11 @@ template <typename Ti, typename To>
 inline void permute(const Ti* in, To* out, const std::vector<long long>& in_shape,
                     const std::vector<int>& order, cudaStream_t st) {
     PermArgs a = make_perm(in_shape, order);
-    permute_kernel<Ti, To><<<grid_for(a.total), 256, 0, st>>>(in, out, a);
+    if (a.total <= 0) return;
+    if (a.total < (1LL << 31))
+        permute32_kernel<Ti, To><<<grid_for(a.total), 256, 0, st>>>(in, out, a);
+    else
+        permute_kernel<Ti, To><<<grid_for(a.total), 256, 0, st>>>(in, out, a);
     KH_LAUNCHED();
 }
 
@@ -148,14 +193,33 @@ struct GemmArgs {
 
 constexpr int GT_K = 16;
 
+// Asynchronous 4- or 8-byte global -> shared copy (sm_80+ cp.async), zero
+// fill when !valid (no bytes read; the source address is still in bounds).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Tile BM x BN per CTA, each of the 256 threads computes TM x TN outputs
 // strided by (BM/TM, BN/TN) so that shared-memory reads are conflict-free.
+// K tiles of GT_K stream through a STAGES-deep ring of shared buffers filled
+// by cp.async, so the global latency of a tile is paid once per ring, not
+// once per tile.
 template <typename T, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
     static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+    constexpr int STAGES = sizeof(T) == 4 ? 4 : 2;
     constexpr int RX = BN / TN;                    // threads along N
-    __shared__ T As[GT_K][BM + 1];
-    __shared__ T Bs[GT_K][BN + 1];
+    __shared__ T As[STAGES][GT_K][BM + 1];
+    __shared__ T Bs[STAGES][GT_K][BN + 1];
     const int tid = threadIdx.x;
     const int tx = tid % RX, ty = tid / RX;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -169,19 +233,17 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
     const bool a_kfast = (g.sAk == 1);
     const bool b_nfast = (g.sBn == 1);
-    // register double buffering: the next K tile's global loads are issued
-    // before the current tile's FMAs
     constexpr int NA = BM * GT_K / 256, NB = BN * GT_K / 256;
     static_assert(NA * 256 == BM * GT_K && NB * 256 == BN * GT_K, "tile/thread mismatch");
-    T ra[NA], rb[NB];
-    auto load_tiles = [&](int k0) {
+    auto issue = [&](int buf, int k0) {
 #pragma unroll
         for (int t = 0; t < NA; ++t) {
             const int e = tid + 256 * t;
             int mm, kk;
             if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
             const int gm = m0 + mm, gk = k0 + kk;
-            ra[t] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : T(0);
+            const bool ok = gm < g.M && gk < g.K;
+            cp_async_elem(&As[buf][kk][mm], ok ? A + gm * g.sAm + gk * g.sAk : A, ok);
         }
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
@@ -189,41 +251,37 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
             int nn, kb;
             if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
             const int gn = n0 + nn, gkb = k0 + kb;
-            rb[t] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : T(0);
+            const bool ok = gn < g.N && gkb < g.K;
+            cp_async_elem(&Bs[buf][kb][nn], ok ? B + gkb * g.sBk + gn * g.sBn : B, ok);
         }
     };
-    load_tiles(0);
-    for (int k0 = 0; k0 < g.K; k0 += GT_K) {
+    const int KT = (g.K + GT_K - 1) / GT_K;
 #pragma unroll
-        for (int t = 0; t < NA; ++t) {
-            const int e = tid + 256 * t;
-            int mm, kk;
-            if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
-            As[kk][mm] = ra[t];
-        }
-#pragma unroll
-        for (int t = 0; t < NB; ++t) {
-            const int e = tid + 256 * t;
-            int nn, kb;
-            if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
-            Bs[kb][nn] = rb[t];
-        }
-        __syncthreads();
-        if (k0 + GT_K < g.K) load_tiles(k0 + GT_K);
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < KT) issue(s, s * GT_K);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < KT; ++kt) {
+        cp_async_wait<STAGES - 2>();              // this thread's copies of tile kt have landed
+        __syncthreads();                           // everyone's; and tile kt-1 is no longer read
+        const int nk = kt + STAGES - 1;
+        if (nk < KT) issue(nk % STAGES, nk * GT_K);
+        cp_async_commit();
+        const int buf = kt % STAGES;
 #pragma unroll
         for (int kk = 0; kk < GT_K; ++kk) {
             T a[TM], bb[TN];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + (BM / TM) * i];
+            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + (BM / TM) * i];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + RX * j];
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx + RX * j];
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
-        __syncthreads();
     }
+    cp_async_wait<0>();
     T* C = g.C + b * g.sCb;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -340,7 +398,9 @@ inline void gemm_rm(int M, int N, int K, const T* A, bool tA, const T* B, bool t
 
 // ------------------------------------------------------------------ reductions
 
-// out[0] = sum x^2 (FP64 accumulate), single block-grid reduction via atomics
+// out[0] = sum x^2 (FP64 accumulate), one atomic per block; launch it on a
+// grid of a few blocks per SM (sumsq_grid): one atomic per element block
+// would serialise thousands of FP64 atomics on one address
 template <typename T>
 __global__ void sumsq_kernel(const T* __restrict__ x, long long n, double* out) {
     double s = 0.0;
@@ -359,6 +419,11 @@ __global__ void sumsq_kernel(const T* __restrict__ x, long long n, double* out) 
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) atomicAdd(out, s);
     }
+}
+
+inline int sumsq_grid(long long n) {
+    long long g = (n + 255) / 256;
+    return (int)(g < 304 ? (g < 1 ? 1 : g) : 304);
 }
 
 }  // namespace kh

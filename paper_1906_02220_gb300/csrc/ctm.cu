@@ -624,7 +624,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
     half_system_product(n);
     double* normM2 = dscr + 8000;
     KH_CUDA(cudaMemsetAsync(normM2, 0, sizeof(double), st));
-    sumsq_kernel<T><<<grid_for((long long)n * n), 256, 0, st>>>(Mt, (long long)n * n, normM2);
+    sumsq_kernel<T><<<sumsq_grid((long long)n * n), 256, 0, st>>>(Mt, (long long)n * n, normM2);
     KH_LAUNCHED();
     uint64_t stream = (uint64_t)slot_id * 4 + dir;
     T* Vw = sl.Vw + (long long)dir * n * k;
@@ -769,11 +769,11 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
     gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // [a][rk][rb][a_up]
     double* ns = dscr + 8010;
     KH_CUDA(cudaMemsetAsync(ns, 0, 3 * sizeof(double), st));
-    sumsq_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C1n, chi2, ns);
+    sumsq_kernel<T><<<sumsq_grid(chi2), 256, 0, st>>>(C1n, chi2, ns);
     KH_LAUNCHED();
-    sumsq_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C4n, chi2, ns + 1);
+    sumsq_kernel<T><<<sumsq_grid(chi2), 256, 0, st>>>(C4n, chi2, ns + 1);
     KH_LAUNCHED();
-    sumsq_kernel<T><<<grid_for(E1), 256, 0, st>>>(E4n, E1, ns + 2);
+    sumsq_kernel<T><<<sumsq_grid(E1), 256, 0, st>>>(E4n, E1, ns + 2);
     KH_LAUNCHED();
     store_normalized_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C1n, chi2, ns, sl.C + s * chi2, Cop + s * chi2);
     KH_LAUNCHED();
@@ -867,7 +867,8 @@ void Engine<T>::compute_metric(Slot<T>& sl, double* N_out) {
     gemm_rm<T>(chi * d2, d2 * chi, chi, mt2, false, E4, false, mdn, st);      // [(e,d)][(l,h)]
     permute<T, T>(mup, mupp, {chi, D, D, D, D, chi}, {1, 2, 3, 4, 0, 5}, st);  // [uk][ub][rk][rb][h][e]
     permute<T, T>(mdn, mdnp, {chi, D, D, D, D, chi}, {5, 0, 1, 2, 3, 4}, st);  // [h][e][dk][db][lk][lb]
-    gemm_rm<T>(d2 * d2, d2 * d2, chi * chi, mupp, false, mdnp, false, mN4, st);
+    gemm_rm<T>(d2 * d2, d2 * d2, chi * chi, mupp, false, mdnp, false, mN4, st, T(1), T(0), nullptr, skbuf,
+               sk_elems);                                                      // K = chi^2: split over CTAs
     permute<T, double>(mN4, N_out, {D, D, D, D, D, D, D, D}, {6, 0, 2, 4, 7, 1, 3, 5}, st);
     symmetrize_kernel<<<grid_for((long long)dm.D4 * dm.D4), 256, 0, st>>>(N_out, dm.D4);
     KH_LAUNCHED();
