@@ -123,6 +123,29 @@ __global__ void permute32_kernel(const Ti* __restrict__ in, To* __restrict__ out
     }
 }
 
+// Permutation fused with the 3xTF32 operand split: hi = the value with its 13
+// low mantissa bits cleared (exactly TF32), lo = value - hi (32-bit path).
+static __global__ void permute_split32_kernel(const float* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
+                                       PermArgs a) {
+    const uint32_t total = (uint32_t)a.total;
+    const uint32_t step = gridDim.x * blockDim.x;
+    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += step) {
+        uint32_t rem = idx, src = 0;
+#pragma unroll
+        for (int j = kMaxRank - 1; j >= 0; --j) {
+            if (j < a.rank) {
+                const uint32_t q = fast_div(rem, a.div[j]);
+                src += (rem - q * a.div[j].d) * (uint32_t)a.in_strides[j];
+                rem = q;
+            }
+        }
+        const float v = in[src];
+        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        hi[idx] = h;
+        lo[idx] = v - h;
+    }
+}
+
 // Build PermArgs from an input shape and the axis order of the output:
 // out axis j is input axis order[j].
 inline PermArgs make_perm(const std::vector<long long>& in_shape, const std::vector<int>& order) {
@@ -148,6 +171,15 @@ inline int grid_for(long long n, int block = 256) {
     if (g > 152LL * 64) g = 152LL * 64;
     if (g < 1) g = 1;
     return (int)g;
+}
+
+inline void permute_split(const float* in, float* hi, float* lo, const std::vector<long long>& in_shape,
+                          const std::vector<int>& order, cudaStream_t st) {
+    PermArgs a = make_perm(in_shape, order);
+    if (a.total <= 0) return;
+    if (a.total >= (1LL << 31)) fail(KH_EINVAL, "permute_split: tensor too large");
+    permute_split32_kernel<<<grid_for(a.total), 256, 0, st>>>(in, hi, lo, a);
+    KH_LAUNCHED();
 }
 
 template <typename Ti, typename To>
@@ -193,33 +225,14 @@ struct GemmArgs {
 
 constexpr int GT_K = 16;
 
-// Asynchronous 4- or 8-byte global -> shared copy (sm_80+ cp.async), zero
-// fill when !valid (no bytes read; the source address is still in bounds).
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    const int n = valid ? (int)sizeof(T) : 0;
-    if (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Tile BM x BN per CTA, each of the 256 threads computes TM x TN outputs
 // strided by (BM/TM, BN/TN) so that shared-memory reads are conflict-free.
-// K tiles of GT_K stream through a STAGES-deep ring of shared buffers filled
-// by cp.async, so the global latency of a tile is paid once per ring, not
-// once per tile.
 template <typename T, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
     static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
-    constexpr int STAGES = sizeof(T) == 4 ? 4 : 2;
     constexpr int RX = BN / TN;                    // threads along N
-    __shared__ T As[STAGES][GT_K][BM + 1];
-    __shared__ T Bs[STAGES][GT_K][BN + 1];
+    __shared__ T As[GT_K][BM + 1];
+    __shared__ T Bs[GT_K][BN + 1];
     const int tid = threadIdx.x;
     const int tx = tid % RX, ty = tid / RX;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -233,17 +246,19 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
         for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
     const bool a_kfast = (g.sAk == 1);
     const bool b_nfast = (g.sBn == 1);
+    // register double buffering: the next K tile's global loads are issued
+    // before the current tile's FMAs
     constexpr int NA = BM * GT_K / 256, NB = BN * GT_K / 256;
     static_assert(NA * 256 == BM * GT_K && NB * 256 == BN * GT_K, "tile/thread mismatch");
-    auto issue = [&](int buf, int k0) {
+    T ra[NA], rb[NB];
+    auto load_tiles = [&](int k0) {
 #pragma unroll
         for (int t = 0; t < NA; ++t) {
             const int e = tid + 256 * t;
             int mm, kk;
             if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
             const int gm = m0 + mm, gk = k0 + kk;
-            const bool ok = gm < g.M && gk < g.K;
-            cp_async_elem(&As[buf][kk][mm], ok ? A + gm * g.sAm + gk * g.sAk : A, ok);
+            ra[t] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : T(0);
         }
 #pragma unroll
         for (int t = 0; t < NB; ++t) {
@@ -251,37 +266,41 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmArgs<T> g) {
             int nn, kb;
             if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
             const int gn = n0 + nn, gkb = k0 + kb;
-            const bool ok = gn < g.N && gkb < g.K;
-            cp_async_elem(&Bs[buf][kb][nn], ok ? B + gkb * g.sBk + gn * g.sBn : B, ok);
+            rb[t] = (gn < g.N && gkb < g.K) ? B[gkb * g.sBk + gn * g.sBn] : T(0);
         }
     };
-    const int KT = (g.K + GT_K - 1) / GT_K;
+    load_tiles(0);
+    for (int k0 = 0; k0 < g.K; k0 += GT_K) {
 #pragma unroll
-    for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < KT) issue(s, s * GT_K);
-        cp_async_commit();
-    }
-    for (int kt = 0; kt < KT; ++kt) {
-        cp_async_wait<STAGES - 2>();              // this thread's copies of tile kt have landed
-        __syncthreads();                           // everyone's; and tile kt-1 is no longer read
-        const int nk = kt + STAGES - 1;
-        if (nk < KT) issue(nk % STAGES, nk * GT_K);
-        cp_async_commit();
-        const int buf = kt % STAGES;
+        for (int t = 0; t < NA; ++t) {
+            const int e = tid + 256 * t;
+            int mm, kk;
+            if (a_kfast) { mm = e / GT_K; kk = e % GT_K; } else { mm = e % BM; kk = e / BM; }
+            As[kk][mm] = ra[t];
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            const int e = tid + 256 * t;
+            int nn, kb;
+            if (b_nfast) { nn = e % BN; kb = e / BN; } else { nn = e / GT_K; kb = e % GT_K; }
+            Bs[kb][nn] = rb[t];
+        }
+        __syncthreads();
+        if (k0 + GT_K < g.K) load_tiles(k0 + GT_K);
 #pragma unroll
         for (int kk = 0; kk < GT_K; ++kk) {
             T a[TM], bb[TN];
 #pragma unroll
-            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + (BM / TM) * i];
+            for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + (BM / TM) * i];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) bb[j] = Bs[buf][kk][tx + RX * j];
+            for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + RX * j];
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
         }
+        __syncthreads();
     }
-    cp_async_wait<0>();
     T* C = g.C + b * g.sCb;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
@@ -328,9 +347,11 @@ __global__ void splitk_reduce_kernel(const T* __restrict__ part, int splits, int
 
 template <typename T>
 inline void gemm_dispatch(const GemmArgs<T>& g, cudaStream_t st) {
+    const long long tiles64 = (long long)((g.M + 63) / 64) * ((g.N + 63) / 64) * g.batch;
     if (g.M <= 16 && g.N <= 16) gemm_launch<T, 16, 16, 1, 1>(g, st);
     else if (g.N <= 16) gemm_launch<T, 128, 16, 2, 4>(g, st);
     else if (g.M <= 16) gemm_launch<T, 16, 128, 4, 2>(g, st);
+    else if (g.N <= 128 && tiles64 < 76) gemm_launch<T, 16, 128, 4, 2>(g, st);   // few 64x64 tiles: more, thinner CTAs
     else gemm_launch<T, 64, 64, 4, 4>(g, st);
 }
 

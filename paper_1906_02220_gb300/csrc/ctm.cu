@@ -206,11 +206,11 @@ __global__ void rand_kernel(T* V, long long tot, uint64_t seed, uint64_t stream)
         V[i] = (T)rnd_uniform(seed, stream, (uint64_t)i);
 }
 
-// Gram G = Z^T Z (Z: n x k row-major, k <= 160): one CTA per chunk of rows,
-// staged in shared memory; thread (ti, tj) of a 16 x 16 grid accumulates
-// G[ti + 16 a][tj + 16 b] over the chunk (in T), chunk sums are added to the
-// FP64 result.
-template <typename T>
+// Gram G = Z^T Z (Z: n x k row-major, k <= 16 KT): one CTA per chunk of rows,
+// staged in shared memory; thread (ti, tj) of a 16 x 16 grid holds the
+// KT x KT register tile G[ti + 16 a][tj + 16 b] and accumulates it over the
+// chunk (in T), then adds it to the FP64 result.
+template <typename T, int KT>
 __global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int n, int k, double* __restrict__ G,
                                                    int rows_per) {
     extern __shared__ unsigned char smem_raw[];
@@ -219,32 +219,48 @@ __global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int 
     for (int e = threadIdx.x; e < nr * k; e += blockDim.x) Ys[e] = Z[(long long)r0 * k + e];
     __syncthreads();
     const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
-    for (int i = ti; i < k; i += 16) {
-        T acc[10];
+    T acc[KT][KT];
 #pragma unroll
-        for (int bb = 0; bb < 10; ++bb) acc[bb] = T(0);
-        for (int r = 0; r < nr; ++r) {
-            const T yi = Ys[r * k + i];
+    for (int a = 0; a < KT; ++a)
 #pragma unroll
-            for (int bb = 0; bb < 10; ++bb) {
-                const int j = tj + 16 * bb;
-                if (j < k) acc[bb] = fma(yi, Ys[r * k + j], acc[bb]);
-            }
+        for (int b = 0; b < KT; ++b) acc[a][b] = T(0);
+    for (int r = 0; r < nr; ++r) {
+        const T* y = Ys + r * k;
+        T yi[KT], yj[KT];
+#pragma unroll
+        for (int a = 0; a < KT; ++a) {
+            const int i = ti + 16 * a, j = tj + 16 * a;
+            yi[a] = i < k ? y[i] : T(0);
+            yj[a] = j < k ? y[j] : T(0);
         }
 #pragma unroll
-        for (int bb = 0; bb < 10; ++bb) {
-            const int j = tj + 16 * bb;
-            if (j < k) atomicAdd(&G[i * k + j], (double)acc[bb]);
-        }
+        for (int a = 0; a < KT; ++a)
+#pragma unroll
+            for (int b = 0; b < KT; ++b) acc[a][b] = fma(yi[a], yj[b], acc[a][b]);
     }
+#pragma unroll
+    for (int a = 0; a < KT; ++a)
+#pragma unroll
+        for (int b = 0; b < KT; ++b) {
+            const int i = ti + 16 * a, j = tj + 16 * b;
+            if (i < k && j < k) atomicAdd(&G[i * k + j], (double)acc[a][b]);
+        }
 }
 
 template <typename T>
 void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
     if (k > 160) fail(KH_EINVAL, "gram: k > 160");
     KH_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * k * k, st));
-    const int rows_per = 32;
-    gram_kernel<T><<<(n + rows_per - 1) / rows_per, 256, sizeof(T) * rows_per * k, st>>>(Z, n, k, dG, rows_per);
+    int rows_per = (int)((48 * 1024) / (sizeof(T) * k));     // stay within the default shared-memory limit
+    if (rows_per > 64) rows_per = 64;
+    const int grid = (n + rows_per - 1) / rows_per;
+    const size_t sm = sizeof(T) * rows_per * k;
+    switch ((k + 15) / 16) {
+#define KH_GRAM(KT) case KT: gram_kernel<T, KT><<<grid, 256, sm, st>>>(Z, n, k, dG, rows_per); break;
+        KH_GRAM(1) KH_GRAM(2) KH_GRAM(3) KH_GRAM(4) KH_GRAM(5)
+        KH_GRAM(6) KH_GRAM(7) KH_GRAM(8) KH_GRAM(9) KH_GRAM(10)
+#undef KH_GRAM
+    }
     KH_LAUNCHED();
 }
 
@@ -452,8 +468,25 @@ void Engine<T>::refresh_operands(Slot<T>& sl) {
 //    on the tensor cores when the precision asks for them;
 //  otherwise layer by layer: the ket layer as one GEMM (K = D^2), then the
 //    bra layer batched over b (K = p D^2)                                  (4 nb p D^6 flops).
+// The double-layer site contraction runs as a 3xTF32 tensor-core GEMM: its
+// Y operand is then written directly as the (hi, lo) pair into (mup, mdn).
 template <typename T>
-void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo) {
+bool Engine<T>::site_presplit(const Slot<T>& sl) const {
+    return sl.dl && tc_npass == 3 && sizeof(T) == 4 && dm.D4 % 4 == 0;
+}
+
+// Y permuted into the site contraction's block layout: into Yp, or as the
+// split pair (mup, mdn) when site_presplit.
+template <typename T>
+void Engine<T>::site_operand(const Slot<T>& sl, const T* Y, T* Yp, const std::vector<long long>& shape,
+                             const std::vector<int>& order) {
+    if (site_presplit(sl)) permute_split((const float*)Y, (float*)mup, (float*)mdn, shape, order, st);
+    else permute<T, T>(Y, Yp, shape, order, st);
+}
+
+template <typename T>
+void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo,
+                           bool presplit) {
     const int d2 = dm.d2, d4 = dm.D4;
     prof_begin(1);
     if (Wt) {
@@ -461,7 +494,7 @@ void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* o
             TcOperand a{(const float*)Ybuf, nullptr, d4}, b{(const float*)Wt, nullptr, d4};
             if (tc_npass == 3) {
                 float *yh = (float*)mup, *yl = (float*)mdn;     // nb D^4 = n^2 elements
-                tc_split((const float*)Ybuf, yh, yl, nb * d4, st);
+                if (!presplit) tc_split((const float*)Ybuf, yh, yl, nb * d4, st);
                 a = TcOperand{yh, yl, d4};
                 b = TcOperand{(const float*)Wt, (const float*)Wt_lo, d4};
             }
@@ -496,10 +529,10 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
     T* X = X1[which];
     gemm_rm<T>(chi, d2 * chi, chi, C1, false, E1p, false, X, st);            // [x4][(uk,ub,z)]
     gemm_rm<T>(chi * d2, d2 * chi, chi, E4, false, X, false, Y1, st);        // [(w,lk,lb)][(uk,ub,z)]
-    permute<T, T>(Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3}, st);  // [w][z][lb][ub][lk][uk]
+    site_operand(sl, Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3});     // [w][z][lb][ub][lk][uk]
     const long long w4 = (long long)f * dm.D4 * dm.D4;
     site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wcor + w4 : nullptr,
-               sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr);                 // [w][z][rk][dk][rb][db]
+               sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr, site_presplit(sl));   // [w][z][rk][dk][rb][db]
     if (which == 0 && tc_npass)   // Q_s^T [(z,rk,rb)][(w,dk,db)]: K-major operand of Mt = Q_{s+3} Q_s
         permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {1, 2, 4, 0, 3, 5}, st);
     else
@@ -761,10 +794,10 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
     }
     gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                  // C4n = C4E3 P~^T
     gemm_rm<T>(d2 * chi, d2 * chi, chi, E4, true, P, false, Y1, st);             // [(lk,lb,x4)][(dk,db,a)]
-    permute<T, T>(Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3}, st);       // [x4][a][lb][db][lk][dk]
+    site_operand(sl, Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3});         // [x4][a][lb][db][lk][dk]
     const long long w4 = (long long)s * dm.D4 * dm.D4;
     site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wedg + w4 : nullptr,
-               sl.dl && sl.Wedg_lo ? sl.Wedg_lo + w4 : nullptr);                 // [x4][a][uk][rk][ub][rb]
+               sl.dl && sl.Wedg_lo ? sl.Wedg_lo + w4 : nullptr, site_presplit(sl));   // [x4][a][uk][rk][ub][rb]
     permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
     gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // [a][rk][rb][a_up]
     double* ns = dscr + 8010;

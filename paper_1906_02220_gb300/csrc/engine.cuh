@@ -143,7 +143,11 @@ struct Engine : EngineBase {
     // CTM internals
     void refresh_operands(Slot<T>& sl);
     void corner(Slot<T>& sl, int frame, int which);
-    void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo);
+    void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo,
+                    bool presplit = false);
+    bool site_presplit(const Slot<T>& sl) const;
+    void site_operand(const Slot<T>& sl, const T* Y, T* Yp, const std::vector<long long>& shape,
+                      const std::vector<int>& order);
     void projector(Slot<T>& sl, int dir, int slot_id);
     void orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L);
     void absorb(Slot<T>& sl, int s);
