@@ -124,9 +124,10 @@ __global__ void permute32_kernel(const Ti* __restrict__ in, To* __restrict__ out
 }
 
 // Permutation fused with the 3xTF32 operand split: hi = the value with its 13
-// low mantissa bits cleared (exactly TF32), lo = value - hi (32-bit path).
-static __global__ void permute_split32_kernel(const float* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
-                                       PermArgs a) {
+// low mantissa bits cleared (exactly TF32), lo = value - hi (32-bit path);
+// the permuted value itself also goes to out when out is not null.
+static __global__ void permute_split32_kernel(const float* __restrict__ in, float* __restrict__ hi,
+                                              float* __restrict__ lo, float* __restrict__ out, PermArgs a) {
     const uint32_t total = (uint32_t)a.total;
     const uint32_t step = gridDim.x * blockDim.x;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += step) {
@@ -143,6 +144,7 @@ static __global__ void permute_split32_kernel(const float* __restrict__ in, floa
         const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
         hi[idx] = h;
         lo[idx] = v - h;
+        if (out) out[idx] = v;
     }
 }
 
@@ -174,11 +176,11 @@ inline int grid_for(long long n, int block = 256) {
 }
 
 inline void permute_split(const float* in, float* hi, float* lo, const std::vector<long long>& in_shape,
-                          const std::vector<int>& order, cudaStream_t st) {
+                          const std::vector<int>& order, cudaStream_t st, float* out = nullptr) {
     PermArgs a = make_perm(in_shape, order);
     if (a.total <= 0) return;
     if (a.total >= (1LL << 31)) fail(KH_EINVAL, "permute_split: tensor too large");
-    permute_split32_kernel<<<grid_for(a.total), 256, 0, st>>>(in, hi, lo, a);
+    permute_split32_kernel<<<grid_for(a.total), 256, 0, st>>>(in, hi, lo, out, a);
     KH_LAUNCHED();
 }
 

@@ -533,10 +533,16 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
     const long long w4 = (long long)f * dm.D4 * dm.D4;
     site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wcor + w4 : nullptr,
                sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr, site_presplit(sl));   // [w][z][rk][dk][rb][db]
-    if (which == 0 && tc_npass)   // Q_s^T [(z,rk,rb)][(w,dk,db)]: K-major operand of Mt = Q_{s+3} Q_s
-        permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {1, 2, 4, 0, 3, 5}, st);
+    // Q_0 stored transposed, [(z,rk,rb)][(w,dk,db)], as the K-major operand of
+    // Mt = Q_{s+3} Q_s on tensor cores; with 3xTF32 the (hi, lo) pairs of both
+    // operands are written by the same pass (Q_1: mup, mdn; Q_0: mupp, mdnp)
+    const std::vector<int> order = (which == 0 && tc_npass) ? std::vector<int>{1, 2, 4, 0, 3, 5}
+                                                            : std::vector<int>{0, 3, 5, 1, 2, 4};
+    if (mt_presplit())
+        permute_split((const float*)Qt, (float*)(which == 1 ? mup : mupp), (float*)(which == 1 ? mdn : mdnp),
+                      {chi, chi, D, D, D, D}, order, st, (float*)Q[which]);
     else
-        permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}, st);  // [w][dk][db][z][rk][rb]
+        permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, order, st);
 }
 
 // Orthonormal basis of the columns of Y (n x k) by two passes of the ordered
@@ -567,22 +573,25 @@ void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
 // Half-system product Mt = Q_{s+3} Q_s (= M^T), the largest single GEMM of a
 // move: on tensor cores (TF32 or 3xTF32) when the precision asks for it.
 template <typename T>
+bool Engine<T>::mt_presplit() const {
+    return tc_npass == 3 && sizeof(T) == 4 && dm.n % 4 == 0;
+}
+
+template <typename T>
 void Engine<T>::half_system_product(int n) {
     prof_begin(0);
     if (tc_npass && sizeof(T) == 4 && n % 4 == 0) {     // TMA rows must be 16-byte multiples
         const float* Qb = (const float*)Q[1];
         const float* QaT = (const float*)Q[0];
         TcOperand a{Qb, nullptr, n}, b{QaT, nullptr, n};
-        if (tc_npass == 3) {
+        if (tc_npass == 3) {       // operands split when Q_0, Q_1 were written (mt_presplit)
             float *ah = (float*)mup, *al = (float*)mdn, *bh = (float*)mupp, *bl = (float*)mdnp;
-            tc_split(Qb, ah, al, (long long)n * n, st);
-            tc_split(QaT, bh, bl, (long long)n * n, st);
             a = TcOperand{ah, al, n};
             b = TcOperand{bh, bl, n};
         }
         tc_gemm(a, b, (float*)Mt, n, n, n, n, 1.f, 0.f, nullptr, tc_npass, tc_err, st);
-    } else {
-        gemm_rm<T>(n, n, n, Q[1], false, Q[0], false, Mt, st);
+    } else {      // Q_0 is stored transposed whenever the tensor cores are enabled
+        gemm_rm<T>(n, n, n, Q[1], false, Q[0], tc_npass != 0, Mt, st);
     }
     prof_end(0, 2.0 * n * (double)n * n);
 }
@@ -605,23 +614,42 @@ __global__ void warm_split_kernel(const T* Vw, const int* live, int n, int k, T*
 // A warm-basis column is kept unless it is (near) zero, i.e. its direction
 // was dropped by the orthonormalisation: kept tail directions keep
 // converging by power iteration instead of restarting from random vectors.
-// One block: thread (part, c) sums rows part, part + parts, ... of column c
-// (consecutive threads read consecutive columns of a row: coalesced).
+// Column squared norms: block b sums rows b*parts + part (+ gridDim parts, ...),
+// thread (part, c) reading consecutive columns of a row (coalesced); the
+// per-block sums go to acc by atomics and the last block to finish forms
+// live[] and clears acc and the block counter for the next call.
 template <typename T>
-__global__ void live_mask_kernel(const T* __restrict__ V, int n, int k, int* live) {
+__global__ void live_mask_kernel(const T* __restrict__ V, int n, int k, int* live, float* acc, int* counter) {
     extern __shared__ float s_part[];                 // parts x k
+    __shared__ int s_last;
     const int parts = blockDim.x / k;
     const int c = threadIdx.x % k, part = threadIdx.x / k;
     if (part < parts) {
         float a = 0.f;
-        for (int r = part; r < n; r += parts) { float v = (float)V[(long long)r * k + c]; a = fmaf(v, v, a); }
+        for (int r = blockIdx.x * parts + part; r < n; r += gridDim.x * parts) {
+            float v = (float)V[(long long)r * k + c];
+            a = fmaf(v, v, a);
+        }
         s_part[part * k + c] = a;
     }
     __syncthreads();
     for (int cc = threadIdx.x; cc < k; cc += blockDim.x) {
         float a = 0.f;
         for (int q = 0; q < parts; ++q) a += s_part[q * k + cc];
-        live[cc] = (a > 0.25f) ? 1 : 0;
+        atomicAdd(&acc[cc], a);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int cc = threadIdx.x; cc < k; cc += blockDim.x) {
+            const float a = atomicAdd(&acc[cc], 0.f);
+            live[cc] = (a > 0.25f) ? 1 : 0;
+            acc[cc] = 0.f;
+        }
+        if (threadIdx.x == 0) *counter = 0;
     }
 }
 
@@ -730,8 +758,9 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         gemm_rm<T>(n, k, k, U, false, Lk, false, Uf, st);                      // left vectors of M: U L
         KH_CUDA(cudaMemcpyAsync(Vw, Z1, sizeof(T) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
         {
-            const int thr = 1024 / k * k;
-            live_mask_kernel<T><<<1, thr, sizeof(float) * thr, st>>>(Z1, n, k, live);
+            const int thr = 256 / k > 0 ? 256 / k * k : k;
+            live_mask_kernel<T><<<16, thr, sizeof(float) * thr, st>>>(Z1, n, k, live, (float*)(dscr + 7000),
+                                                                       flags + 56);
         }
         KH_LAUNCHED();
         sl.warm[dir] = true;

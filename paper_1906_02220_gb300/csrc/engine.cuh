@@ -134,6 +134,7 @@ struct Engine : EngineBase {
     int tc_npass = 0;          // 0: CUDA-core GEMMs; 1: TF32; 3: 3xTF32
     unsigned long long rng_counter = 0;
     void half_system_product(int n);
+    bool mt_presplit() const;
 
     Engine() {}
     Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s);

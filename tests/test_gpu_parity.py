@@ -103,12 +103,14 @@ def test_ctm_metric_and_spectra_match_oracle(g, prec, D, chi):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
-@pytest.mark.parametrize("D,p,chi", [(2, 1, 8), (3, 2, 12), (4, 2, 12)])
+@pytest.mark.parametrize("D,p,chi", [(2, 1, 8), (3, 2, 12), (3, 2, 13), (4, 2, 12)])
 def test_ctm_layered_path_matches_oracle(g, prec, D, p, chi):
     """Tensors with D^2 > 2p take the layer-by-layer site contraction (the
     double-layer operand would cost more there); converged metric and
     projector spectra agree with the oracle.  (4, 2, 12) runs the subspace
-    iteration (n = 192)."""
+    iteration (n = 192); (3, 2, 13) has n = 117, not a multiple of 4, so the
+    tensor-core precisions fall back to CUDA cores for the half-system product
+    (TMA rows must be 16-byte multiples)."""
     T = kh_inputs.random_composite(D, 17 + D, p=p)
     env, specs, _ = _oracle_ctm(T, chi, 0)
     env, info = ctmrg.ctmrg(ctmrg.double_tensor(T), env, tol=1e-13, max_sweeps=300)
