@@ -749,19 +749,50 @@ __global__ void obs_kernel(const double* __restrict__ Xs, Mat4x3 H, double hA, d
 template <typename T>
 void Engine<T>::observables(const double* Hh, double hA, double hB, int mx, int mn, double tol, double* out) {
     if (dm.nslots < 6) fail(KH_EINVAL, "observables need n_slots >= 6");
-    int sweeps = 0;
+    // The three mappings are independent CTMRG problems: slot 3 + g runs on
+    // lane g (its own scratch and stream), forked from and joined back to the
+    // context's stream.
+    struct Rebind {
+        Engine* e;
+        ~Rebind() { e->bind(0); }
+    } rebind{this};
+    const int nl = nlanes >= 3 ? 3 : 1;
+    auto lane_of = [&](int g) { return nl == 3 ? g : 0; };
+    bind(0);
+    if (nl == 3) {
+        KH_CUDA(cudaEventRecord(lane_ev[0], lanes[0].st));
+        for (int i = 1; i < 3; ++i) KH_CUDA(cudaStreamWaitEvent(lanes[i].st, lane_ev[0], 0));
+    }
     for (int g = 0; g < 3; ++g) {
-        int s = 3 + g;
+        bind(lane_of(g));
+        const int s = 3 + g;
         if (!slots[s].env_valid || slots[s].p == 0) {
             if (slots[g].p != 0) copy_env(s, g);
             else init_env(s, nullptr);
         }
         build_composite(s, g, nullptr);
-        sweeps += sweep(s, mx, mn, tol, nullptr);
+    }
+    int sweeps = 0;
+    if (nl == 3) {
+        const int ids[3] = {3, 4, 5};
+        sweeps = sweep_lanes(ids, 3, mx, mn, tol);
+    } else {
+        for (int g = 0; g < 3; ++g) sweeps += sweep(3 + g, mx, mn, tol, nullptr);
+    }
+    for (int g = 0; g < 3; ++g) {
+        bind(lane_of(g));
+        const int s = 3 + g;
         compute_metric(slots[s], N);
         gemm_rm<double>(16, dm.D4, dm.D4, slots[s].Ts, false, N, false, dwork, st);
         gemm_rm<double>(16, 16, dm.D4, dwork, false, slots[s].Ts, true, Xs + g * 256, st);
     }
+    if (nl == 3) {
+        for (int i = 1; i < 3; ++i) {
+            KH_CUDA(cudaEventRecord(lane_ev[i], lanes[i].st));
+            KH_CUDA(cudaStreamWaitEvent(lanes[0].st, lane_ev[i], 0));
+        }
+    }
+    bind(0);
     Mat4x3 H;
     for (int i = 0; i < 48; ++i) H.v[i] = Hh[i];
     double* dout = dscr + 4200;

@@ -86,6 +86,42 @@ void Engine<T>::layout(Carver& cv) {
         s.delta = cv.take<double>(1);
         s.live = cv.take<int>(4LL * d.kk);
     }
+    carve_lane(cv);
+    save_lane(0);
+    const long long mT = 4LL * d.d2;                 // rows of T' as [(sA,aA,u,r)]
+    const long long m = D3;                          // size of R
+    A2 = cv.take<double>(4 * D3);
+    B2 = cv.take<double>(4 * D3);
+    XA = cv.take<double>(4LL * d.D4 * d.d2 * d.D);  // [(o1,o2)][D^4][(ph,k)]
+    R = cv.take<double>(m * m);
+    S = cv.take<double>(m * 4);
+    Xs = cv.take<double>(3LL * 16 * 16 + 64);
+    Tm = cv.take<double>(mT * mT);
+    Gt = cv.take<double>(mT * mT);
+    Wt = cv.take<double>(mT * mT);
+    Lt = cv.take<double>(mT);
+    Gtf = cv.take<float>(mT * mT);
+    Wtf = cv.take<float>(mT * mT);
+    Ltf = cv.take<float>(mT);
+    Xmat = cv.take<double>(m * m + 4 * m);
+    cost = cv.take<double>(64);
+    flags = cv.take<int>(64);
+    tc_err = cv.take<int>(64);
+    nlanes = d.nslots >= 6 ? 3 : 1;
+    for (int i = 1; i < nlanes; ++i) {
+        carve_lane(cv);
+        save_lane(i);
+    }
+    bind(0);
+}
+
+// Scratch of one lane (the buffers a CTM move, the metric and the
+// observables' contractions write).
+template <typename T>
+void Engine<T>::carve_lane(Carver& cv) {
+    const Dims& d = dm;
+    const long long chi2 = (long long)d.chi * d.chi, E1 = (long long)d.chi * d.d2 * d.chi;
+    const long long n = d.n, n2 = n * n, kk = d.kk;
     Cop = cv.take<T>(4 * chi2);
     Eop = cv.take<T>(4 * E1);
     X1[0] = cv.take<T>(E1);
@@ -130,28 +166,42 @@ void Engine<T>::layout(Carver& cv) {
     mdnp = cv.take<T>(n2);
     mN4 = cv.take<T>((long long)d.D4 * d.D4);
     N = cv.take<double>((long long)d.D4 * d.D4);
-    const long long mT = 4LL * d.d2;                 // rows of T' as [(sA,aA,u,r)]
-    const long long m = D3;                          // size of R
-    A2 = cv.take<double>(4 * D3);
-    B2 = cv.take<double>(4 * D3);
-    XA = cv.take<double>(4LL * d.D4 * d.d2 * d.D);  // [(o1,o2)][D^4][(ph,k)]
-    R = cv.take<double>(m * m);
-    S = cv.take<double>(m * 4);
-    Xs = cv.take<double>(3LL * 16 * 16 + 64);
-    Tm = cv.take<double>(mT * mT);
-    Gt = cv.take<double>(mT * mT);
-    Wt = cv.take<double>(mT * mT);
-    Lt = cv.take<double>(mT);
-    Gtf = cv.take<float>(mT * mT);
-    Wtf = cv.take<float>(mT * mT);
-    Ltf = cv.take<float>(mT);
-    Xmat = cv.take<double>(m * m + 4 * m);
-    cost = cv.take<double>(64);
     dwork = cv.take<double>(4 * E1 + 16LL * d.D4 + 64);
-    flags = cv.take<int>(64);
-    tc_err = cv.take<int>(64);
     sk_elems = 16LL * n * (kk > d.chi ? kk : d.chi);
     skbuf = cv.take<T>(sk_elems);
+}
+
+template <typename T>
+void Engine<T>::save_lane(int i) {
+    Lane<T>& L = lanes[i];
+#define KH_SAVE(f) L.f = f;
+    KH_LANE_PTRS(KH_SAVE)
+    KH_LANE_DPTRS(KH_SAVE)
+#undef KH_SAVE
+    L.X1[0] = X1[0]; L.X1[1] = X1[1];
+    L.Q[0] = Q[0]; L.Q[1] = Q[1];
+}
+
+template <typename T>
+void Engine<T>::bind(int i) {
+    const Lane<T>& L = lanes[i];
+#define KH_BIND(f) f = L.f;
+    KH_LANE_PTRS(KH_BIND)
+    KH_LANE_DPTRS(KH_BIND)
+#undef KH_BIND
+    X1[0] = L.X1[0]; X1[1] = L.X1[1];
+    Q[0] = L.Q[0]; Q[1] = L.Q[1];
+    st = L.st;
+}
+
+template <typename T>
+Engine<T>::~Engine() {
+    if (own_streams) {
+        for (int i = 1; i < 3; ++i)
+            if (lanes[i].st) cudaStreamDestroy(lanes[i].st);
+    }
+    for (auto& e : lane_ev)
+        if (e) cudaEventDestroy(e);
 }
 
 template <typename T>
@@ -177,10 +227,17 @@ template <typename T>
 Engine<T>::Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s) {
     cfg = c;
     st = s;
+    lanes[0].st = s;
     dm = make_dims(c, sizeof(T) == 8);
     tc_npass = (c.prec == KH_TF32) ? 1 : (c.prec == KH_TF32X3 ? 3 : 0);
     Carver cv(ws, bytes);
     layout(cv);
+    for (int i = 1; i < nlanes; ++i) {
+        KH_CUDA(cudaStreamCreateWithFlags(&lanes[i].st, cudaStreamNonBlocking));
+        own_streams = true;
+    }
+    for (int i = 0; i < nlanes; ++i) KH_CUDA(cudaEventCreateWithFlags(&lane_ev[i], cudaEventDisableTiming));
+    bind(0);
     KH_CUDA(cudaMemsetAsync(ws, 0, cv.off, st));
     init_state_kernel<<<1, 32, 0, st>>>(A, B, dm.D);
     KH_LAUNCHED();
@@ -760,7 +817,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         {
             const int thr = 256 / k > 0 ? 256 / k * k : k;
             live_mask_kernel<T><<<16, thr, sizeof(float) * thr, st>>>(Z1, n, k, live, (float*)(dscr + 7000),
-                                                                       flags + 56);
+                                                                       (int*)(dscr + 7100));
         }
         KH_LAUNCHED();
         sl.warm[dir] = true;
@@ -888,6 +945,77 @@ int Engine<T>::sweep(int slot, int max_sweeps, int min_sweeps, double tol, doubl
     sl.sweeps_done += done;
     if (delta_out) *delta_out = delta;
     return done;
+}
+
+// Sweeps of up to three slots at once, slot_ids[i] on lane i: the moves are
+// issued round-robin over the lanes (each lane's stream orders its own
+// work, the lanes run concurrently on the GPU); with tol >= 0 the host reads
+// every active slot's spectrum change after each sweep.  Returns the total
+// number of sweeps.
+template <typename T>
+int Engine<T>::sweep_lanes(const int* slot_ids, int count, int mx, int mn, double tol) {
+    struct Rebind {
+        Engine* e;
+        ~Rebind() { e->bind(0); }
+    } rebind{this};
+    if (count < 1 || count > nlanes) fail(KH_EINVAL, "sweep_lanes: bad lane count");
+    bool active[3] = {false, false, false};
+    int done[3] = {0, 0, 0};
+    double delta[3] = {INFINITY, INFINITY, INFINITY};
+    for (int i = 0; i < count; ++i) {
+        bind(i);
+        Slot<T>& sl = slots[slot_ids[i]];
+        if (sl.p <= 0) fail(KH_EINVAL, "slot has no site tensor");
+        if (!sl.env_valid) init_env(slot_ids[i], nullptr);
+        refresh_operands(sl);
+        active[i] = true;
+    }
+    for (int it = 1; it <= mx; ++it) {
+        for (int s = 0; s < 4; ++s)
+            for (int i = 0; i < count; ++i)
+                if (active[i]) {
+                    bind(i);
+                    move(slots[slot_ids[i]], s, slot_ids[i]);
+                }
+        for (int i = 0; i < count; ++i)
+            if (active[i]) {
+                bind(i);
+                Slot<T>& sl = slots[slot_ids[i]];
+                delta_kernel<<<1, 256, 0, st>>>(sl.spec, sl.prev, dm.chi, sl.prev_valid ? 1 : 0, sl.delta);
+                KH_LAUNCHED();
+                sl.prev_valid = true;
+                done[i] = it;
+                if (tol >= 0.0) KH_CUDA(cudaMemcpyAsync(&delta[i], sl.delta, sizeof(double), cudaMemcpyDeviceToHost, st));
+            }
+        if (tol >= 0.0) {
+            int terr = 0;
+            for (int i = 0; i < count; ++i)
+                if (active[i]) {
+                    bind(i);
+                    KH_CUDA(cudaStreamSynchronize(st));
+                }
+            if (tc_npass) {
+                bind(0);
+                KH_CUDA(cudaMemcpyAsync(&terr, tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+                KH_CUDA(cudaStreamSynchronize(st));
+                if (terr) fail(KH_ETIMEOUT, "tensor-core kernel wait timed out (flag " + std::to_string(terr) + ")");
+            }
+            bool any = false;
+            for (int i = 0; i < count; ++i)
+                if (active[i]) {
+                    if (!(delta[i] == delta[i])) fail(KH_ENUMERIC, "NaN in CTM spectra");
+                    if (it >= mn && delta[i] < tol) active[i] = false;
+                    any = any || active[i];
+                }
+            if (!any) break;
+        }
+    }
+    int total = 0;
+    for (int i = 0; i < count; ++i) {
+        slots[slot_ids[i]].sweeps_done += done[i];
+        total += done[i];
+    }
+    return total;
 }
 
 template <typename T>

@@ -104,6 +104,27 @@ struct EngineBase {
                              double* out) = 0;
 };
 
+// Per-lane scratch of the CTM moves and the metric.  Lane 0 serves every
+// call on the context's stream; lanes 1 and 2 (own streams) let the
+// observables run the CTMs of the three bond mappings concurrently (each
+// move is latency-bound and leaves most SMs idle).
+#define KH_LANE_PTRS(X) X(Cop) X(Eop) X(Y1) X(Yp) X(Zk) X(Qt) X(Mt) X(V0) X(Z1) X(U) X(Z2) X(Vo) X(Uf) \
+    X(G1) X(W1) X(L1) X(G2) X(W2) X(L2) X(Xk) X(Hk) X(Lk) X(Qk) X(Sk) X(isq) X(P) X(PtT) X(C4E3) X(C1n) \
+    X(C4n) X(E4n) X(mt1) X(mt2) X(mup) X(mdn) X(mupp) X(mdnp) X(mN4) X(skbuf)
+#define KH_LANE_DPTRS(X) X(dscr) X(N) X(dwork)
+template <typename T>
+struct Lane {
+#define KH_DECL(f) T* f = nullptr;
+    KH_LANE_PTRS(KH_DECL)
+#undef KH_DECL
+#define KH_DECL(f) double* f = nullptr;
+    KH_LANE_DPTRS(KH_DECL)
+#undef KH_DECL
+    T* X1[2] = {nullptr, nullptr};
+    T* Q[2] = {nullptr, nullptr};
+    cudaStream_t st = 0;
+};
+
 template <typename T>
 struct Engine : EngineBase {
     // persistent
@@ -133,6 +154,15 @@ struct Engine : EngineBase {
     long long sk_elems = 0;
     int tc_npass = 0;          // 0: CUDA-core GEMMs; 1: TF32; 3: 3xTF32
     unsigned long long rng_counter = 0;
+    Lane<T> lanes[3];
+    int nlanes = 1;            // 3 when the context has the six slots of the observables
+    bool own_streams = false;
+    cudaEvent_t lane_ev[3] = {nullptr, nullptr, nullptr};
+    void bind(int i);          // lane i's scratch and stream become the members used by the moves
+    void save_lane(int i);
+    void carve_lane(Carver& cv);
+    int sweep_lanes(const int* slot_ids, int count, int mx, int mn, double tol);
+    ~Engine() override;
     void half_system_product(int n);
     bool mt_presplit() const;
 
