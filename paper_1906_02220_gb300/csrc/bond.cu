@@ -281,6 +281,8 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
     __shared__ double s_delta, s_rd;
     __shared__ double s_sq[512];
     double* W = smem ? sh_w : Wg;
+    // shared memory: odd row stride, so that walking a column hits distinct banks
+    const long long ld = smem ? m + 1 : m;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     if (warp == 0) {
         double tr = 0.0;
@@ -291,52 +293,52 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
     __syncthreads();
     for (long long e = tid; e < (long long)m * m; e += nt) {
         int i = (int)(e / m), j = (int)(e % m);
-        W[e] = R[e] + ((i == j) ? s_delta : 0.0);
+        W[i * ld + j] = R[e] + ((i == j) ? s_delta : 0.0);
     }
-    double* y = W + (long long)m * m;   // m x 4
+    double* y = W + (long long)m * ld;  // m x 4
     for (int e = tid; e < 4 * m; e += nt) y[e] = S[e];
     __syncthreads();
     for (int j = 0; j < m; ++j) {
         if (tid == 0) {
-            double dj = W[(long long)j * m + j];
-            if (!(dj > 0.0)) { flag[0] |= 1; dj = 1e-300; W[(long long)j * m + j] = dj; }
+            double dj = W[(long long)j * ld + j];
+            if (!(dj > 0.0)) { flag[0] |= 1; dj = 1e-300; W[(long long)j * ld + j] = dj; }
             s_rd = 1.0 / dj;
         }
         __syncthreads();
         const double rd = s_rd;
         for (int i = j + 1 + warp; i < m; i += nw) {             // rows by warps, columns by lanes
-            const double lij = W[(long long)i * m + j] * rd;
-            for (int c = j + 1 + lane; c <= i; c += 32) W[(long long)i * m + c] -= lij * W[(long long)c * m + j];
+            const double lij = W[(long long)i * ld + j] * rd;
+            for (int c = j + 1 + lane; c <= i; c += 32) W[(long long)i * ld + c] -= lij * W[(long long)c * ld + j];
         }
         __syncthreads();
     }
-    for (int j = tid; j < m; j += nt) s_sq[j] = sqrt(W[(long long)j * m + j]);
+    for (int j = tid; j < m; j += nt) s_sq[j] = sqrt(W[(long long)j * ld + j]);
     __syncthreads();
     for (long long e = tid; e < (long long)m * m; e += nt) {     // L_ij = a_ij / sqrt(d_j)
         int i = (int)(e / m), j = (int)(e % m);
-        if (i > j) W[e] /= s_sq[j];
-        else if (i == j) W[e] = s_sq[j];
+        if (i > j) W[i * ld + j] /= s_sq[j];
+        else if (i == j) W[i * ld + j] = s_sq[j];
     }
     __syncthreads();
     // forward: L y = S
     for (int j = 0; j < m; ++j) {
-        double ljj = W[(long long)j * m + j];
+        double ljj = W[(long long)j * ld + j];
         if (tid < 4) y[j * 4 + tid] /= ljj;
         __syncthreads();
         for (int e = tid; e < (m - j - 1) * 4; e += nt) {
             int i = j + 1 + e / 4, q = e % 4;
-            y[i * 4 + q] -= W[(long long)i * m + j] * y[j * 4 + q];
+            y[i * 4 + q] -= W[(long long)i * ld + j] * y[j * 4 + q];
         }
         __syncthreads();
     }
     // backward: L^T x = y
     for (int j = m - 1; j >= 0; --j) {
-        double ljj = W[(long long)j * m + j];
+        double ljj = W[(long long)j * ld + j];
         if (tid < 4) y[j * 4 + tid] /= ljj;
         __syncthreads();
         for (int e = tid; e < j * 4; e += nt) {
             int i = e / 4, q = e % 4;
-            y[i * 4 + q] -= W[(long long)j * m + i] * y[j * 4 + q];
+            y[i * 4 + q] -= W[(long long)j * ld + i] * y[j * 4 + q];
         }
         __syncthreads();
     }
@@ -613,7 +615,7 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     const long long nX = 4LL * dm.d2 * D4 * D, nR = (long long)m * m;
     const int sgrid = (int)((4LL * m * 32 + threads - 1) / threads);
     const int cgrid = (int)std::min<long long>(32, (nR + threads - 1) / threads);
-    const size_t chol_sm = sizeof(double) * ((size_t)m * m + 4 * m);
+    const size_t chol_sm = sizeof(double) * ((size_t)m * (m + 1) + 4 * m);
     const int chol_smem = chol_sm <= 200 * 1024 ? 1 : 0;
     if (chol_smem && chol_sm > 48 * 1024) {
         static size_t attr_set = 0;

@@ -592,11 +592,11 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
                sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr, site_presplit(sl));   // [w][z][rk][dk][rb][db]
     // Q_0 stored transposed, [(z,rk,rb)][(w,dk,db)], as the K-major operand of
     // Mt = Q_{s+3} Q_s on tensor cores; with 3xTF32 the (hi, lo) pairs of both
-    // operands are written by the same pass (Q_1: mup, mdn; Q_0: mupp, mdnp)
+    // operands are written by the same pass (Q_1: q1_hi, q1_lo; Q_0: mupp, mdnp)
     const std::vector<int> order = (which == 0 && tc_npass) ? std::vector<int>{1, 2, 4, 0, 3, 5}
                                                             : std::vector<int>{0, 3, 5, 1, 2, 4};
     if (mt_presplit())
-        permute_split((const float*)Qt, (float*)(which == 1 ? mup : mupp), (float*)(which == 1 ? mdn : mdnp),
+        permute_split((const float*)Qt, (float*)(which == 1 ? q1_hi : mupp), (float*)(which == 1 ? q1_lo : mdnp),
                       {chi, chi, D, D, D, D}, order, st, (float*)Q[which]);
     else
         permute<T, T>(Qt, Q[which], {chi, chi, D, D, D, D}, order, st);
@@ -642,7 +642,7 @@ void Engine<T>::half_system_product(int n) {
         const float* QaT = (const float*)Q[0];
         TcOperand a{Qb, nullptr, n}, b{QaT, nullptr, n};
         if (tc_npass == 3) {       // operands split when Q_0, Q_1 were written (mt_presplit)
-            float *ah = (float*)mup, *al = (float*)mdn, *bh = (float*)mupp, *bl = (float*)mdnp;
+            float *ah = (float*)q1_hi, *al = (float*)q1_lo, *bh = (float*)mupp, *bl = (float*)mdnp;
             a = TcOperand{ah, al, n};
             b = TcOperand{bh, bl, n};
         }
@@ -907,8 +907,35 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
 template <typename T>
 void Engine<T>::move(Slot<T>& sl, int s, int slot_id) {
     prof_begin(2);
-    corner(sl, s, 0);
-    corner(sl, (s + 3) & 3, 1);
+    if (nlanes >= 2 && !in_lanes) {
+        // The two enlarged corners are independent: corner s+3 runs on lane 1
+        // (its own stream and scratch) reading lane 0's environment operands
+        // and writing Q_{s+3} (and its split, into lane 1's mupp/mdnp) where
+        // the half-system product reads them; lane 0 waits before the projector.
+        KH_CUDA(cudaEventRecord(lane_ev[0], st));
+        KH_CUDA(cudaStreamWaitEvent(lanes[1].st, lane_ev[0], 0));
+        corner(sl, s, 0);
+        struct Rebind {
+            Engine* e;
+            ~Rebind() { e->bind(0); }
+        } rebind{this};
+        bind(1);
+        Cop = lanes[0].Cop;
+        Eop = lanes[0].Eop;
+        X1[1] = lanes[0].X1[1];
+        Q[1] = lanes[0].Q[1];
+        q1_hi = lanes[1].mupp;
+        q1_lo = lanes[1].mdnp;
+        corner(sl, (s + 3) & 3, 1);
+        KH_CUDA(cudaEventRecord(lane_ev[1], st));
+        bind(0);
+        KH_CUDA(cudaStreamWaitEvent(st, lane_ev[1], 0));
+    } else {
+        q1_hi = mup;
+        q1_lo = mdn;
+        corner(sl, s, 0);
+        corner(sl, (s + 3) & 3, 1);
+    }
     prof_end(2, 0.0);
     prof_begin(3);
     projector(sl, s, slot_id);
@@ -956,9 +983,13 @@ template <typename T>
 int Engine<T>::sweep_lanes(const int* slot_ids, int count, int mx, int mn, double tol) {
     struct Rebind {
         Engine* e;
-        ~Rebind() { e->bind(0); }
+        ~Rebind() {
+            e->bind(0);
+            e->in_lanes = false;
+        }
     } rebind{this};
     if (count < 1 || count > nlanes) fail(KH_EINVAL, "sweep_lanes: bad lane count");
+    in_lanes = count > 1;
     bool active[3] = {false, false, false};
     int done[3] = {0, 0, 0};
     double delta[3] = {INFINITY, INFINITY, INFINITY};

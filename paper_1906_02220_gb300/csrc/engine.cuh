@@ -158,6 +158,8 @@ struct Engine : EngineBase {
     int nlanes = 1;            // 3 when the context has the six slots of the observables
     bool own_streams = false;
     cudaEvent_t lane_ev[3] = {nullptr, nullptr, nullptr};
+    bool in_lanes = false;     // lanes 1, 2 busy with other slots (sweep_lanes)
+    T *q1_hi = nullptr, *q1_lo = nullptr;   // where the 3xTF32 split of Q_{s+3} was written
     void bind(int i);          // lane i's scratch and stream become the members used by the moves
     void save_lane(int i);
     void carve_lane(Carver& cv);
