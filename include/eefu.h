@@ -250,6 +250,13 @@ kh_status kh_selftest_svd(int prec, int k, const double* dev_X, double* dev_S, d
 kh_status kh_selftest_orth(int prec, int n, int k, double cut, const double* dev_Y, double* dev_Q,
                            void* dev_scratch, size_t scratch_bytes, void* stream);
 
+/* FP64 reciprocal, reciprocal square root and square root as the library's
+ * latency-bound FP64 kernels form them (Newton-Raphson iteration from the FP32
+ * hardware estimates, IEEE operations outside the FP32 normal range): for the
+ * n device values x, dev_out[3i] = 1/x_i, dev_out[3i+1] = 1/sqrt(x_i) (0 for
+ * x_i <= 0), dev_out[3i+2] = sqrt(x_i) (0 for x_i < 0).  Synchronises stream. */
+kh_status kh_selftest_fp64_newton(int n, const double* dev_x, double* dev_out, void* stream);
+
 /* --- allocation-free variant (the paper has no counterpart) ---------------- */
 
 /* Same result as kh_selftest_gemm (dev_C = dev_A dev_B, row-major FP64 device

@@ -27,7 +27,7 @@ ABI_FUNCTIONS = [
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
     "eefu_trotter_step", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
-    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_orth", "kh_gemm_noalloc", "kh_gemm_noalloc_max_bytes",
+    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_orth", "kh_selftest_fp64_newton", "kh_gemm_noalloc", "kh_gemm_noalloc_max_bytes",
 ]
 
 
@@ -86,6 +86,7 @@ def load_library(path=LIB_PATH):
         "kh_selftest_symeig": (I, [I, I, P, P, P, P, S, P]),
         "kh_selftest_svd": (I, [I, I, P, P, P, P, P, S, P]),
         "kh_selftest_orth": (I, [I, I, I, D, P, P, P, S, P]),
+        "kh_selftest_fp64_newton": (I, [I, P, P, P]),
         "kh_gemm_noalloc": (I, [I, I, I, I, P, P, P, P]),
         "kh_gemm_noalloc_max_bytes": (S, []),
     }
@@ -169,6 +170,20 @@ def selftest_orth(Y, prec="fp64", cut=1e-12):
     if st != KH_OK:
         raise KhError(st, "kh_selftest_orth")
     return Q
+
+
+def selftest_fp64_newton(x):
+    """(1/x, 1/sqrt(x), sqrt(x)) of an FP64 CUDA tensor as the library's FP64
+    kernels form them (Newton-Raphson from FP32 estimates)."""
+    import torch
+    n = x.numel()
+    out = torch.empty(3 * n, dtype=torch.float64, device=x.device)
+    st = lib().kh_selftest_fp64_newton(n, _tptr(x.contiguous()), _tptr(out),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_fp64_newton")
+    o = out.view(n, 3)
+    return o[:, 0], o[:, 1], o[:, 2]
 
 
 def gemm_noalloc(A, B, prec="fp64"):

@@ -279,7 +279,7 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
     if (skip && *skip) return;
     extern __shared__ double sh_w[];
     __shared__ double s_delta, s_rd;
-    __shared__ double s_sq[512];
+    __shared__ double s_sq[512], s_rsq[512];
     double* W = smem ? sh_w : Wg;
     // shared memory: odd row stride, so that walking a column hits distinct banks
     const long long ld = smem ? m + 1 : m;
@@ -302,7 +302,7 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
         if (tid == 0) {
             double dj = W[(long long)j * ld + j];
             if (!(dj > 0.0)) { flag[0] |= 1; dj = 1e-300; W[(long long)j * ld + j] = dj; }
-            s_rd = 1.0 / dj;
+            s_rd = rcp_nr(dj);
         }
         __syncthreads();
         const double rd = s_rd;
@@ -312,18 +312,21 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
         }
         __syncthreads();
     }
-    for (int j = tid; j < m; j += nt) s_sq[j] = sqrt(W[(long long)j * ld + j]);
+    for (int j = tid; j < m; j += nt) {
+        const double d = W[(long long)j * ld + j];
+        s_rsq[j] = rsqrt_nr(d);
+        s_sq[j] = d * s_rsq[j];
+    }
     __syncthreads();
     for (long long e = tid; e < (long long)m * m; e += nt) {     // L_ij = a_ij / sqrt(d_j)
         int i = (int)(e / m), j = (int)(e % m);
-        if (i > j) W[i * ld + j] /= s_sq[j];
+        if (i > j) W[i * ld + j] *= s_rsq[j];
         else if (i == j) W[i * ld + j] = s_sq[j];
     }
     __syncthreads();
     // forward: L y = S
     for (int j = 0; j < m; ++j) {
-        double ljj = W[(long long)j * ld + j];
-        if (tid < 4) y[j * 4 + tid] /= ljj;
+        if (tid < 4) y[j * 4 + tid] *= s_rsq[j];
         __syncthreads();
         for (int e = tid; e < (m - j - 1) * 4; e += nt) {
             int i = j + 1 + e / 4, q = e % 4;
@@ -333,8 +336,7 @@ __global__ void chol_solve_kernel(const double* __restrict__ R, const double* __
     }
     // backward: L^T x = y
     for (int j = m - 1; j >= 0; --j) {
-        double ljj = W[(long long)j * ld + j];
-        if (tid < 4) y[j * 4 + tid] /= ljj;
+        if (tid < 4) y[j * 4 + tid] *= s_rsq[j];
         __syncthreads();
         for (int e = tid; e < j * 4; e += nt) {
             int i = e / 4, q = e % 4;
@@ -422,9 +424,9 @@ __global__ void svd_init_kernel(const TJ* Ut, const TJ* sv, int mT, int D, doubl
         double sk = (k < mT) ? (double)sv[k] : 0.0;
         bool ok = (s0 > 0.0) && (sk > 1e-14 * s0);
         double w = (double)Ut[(long long)r * mT + k];
-        A2m[i] = ok ? w * sqrt(sk) : 0.0;
+        A2m[i] = ok ? w * sqrt_nr(sk) : 0.0;
         Wd[i] = w;
-        if (r == 0) colsc[k] = ok ? 1.0 / sqrt(sk) : 0.0;
+        if (r == 0) colsc[k] = ok ? rsqrt_nr(sk) : 0.0;
     }
 }
 
@@ -444,9 +446,10 @@ __device__ void jacobi_serial(double* A, double* V, int n) {
             for (int q = p + 1; q < n; ++q) {
                 double apq = A[p * n + q];
                 if (apq == 0.0) continue;
-                double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                double tau = (A[q * n + q] - A[p * n + p]) * rcp_nr(2.0 * apq);
+                double t = rcp_nr(fabs(tau) + sqrt_nr(1.0 + tau * tau));
+                if (tau < 0.0) t = -t;
+                double c = rsqrt_nr(1.0 + t * t), s = t * c;
                 for (int k = 0; k < n; ++k) {
                     double akp = A[k * n + p], akq = A[k * n + q];
                     A[k * n + p] = c * akp - s * akq;
@@ -501,8 +504,8 @@ __global__ void gauge_kernel(const double* __restrict__ A2, const double* __rest
                 double a = 0.0, b = 0.0;
                 for (int k = 0; k < D; ++k) {
                     bool ok = lam[k] > 1e-28 * lmax && lam[k] > 0.0;
-                    double sq = ok ? sqrt(lam[k]) : 0.0;
-                    double isq = ok ? 1.0 / sqrt(lam[k]) : 0.0;
+                    double isq = ok ? rsqrt_nr(lam[k]) : 0.0;
+                    double sq = ok ? lam[k] * isq : 0.0;
                     a += WA[i * D + k] * sq * WA[j * D + k];
                     b += WA[i * D + k] * isq * WA[j * D + k];
                 }
@@ -529,7 +532,8 @@ __global__ void gauge_kernel(const double* __restrict__ A2, const double* __rest
             int src = perm[c];
             mu[c] = tmp[src * D + src];
             bool ok = m0 > 0.0 && mu[c] > 1e-28 * m0;
-            double q4 = ok ? pow(mu[c], 0.25) : 0.0, iq4 = ok ? pow(mu[c], -0.25) : 0.0;
+            const double r2 = ok ? sqrt_nr(mu[c]) : 0.0;                 // mu^(1/2)
+            double q4 = ok ? sqrt_nr(r2) : 0.0, iq4 = ok ? rsqrt_nr(r2) : 0.0;
             for (int i = 0; i < D; ++i) {
                 double x = 0.0, y = 0.0;
                 for (int a = 0; a < D; ++a) {
@@ -567,8 +571,8 @@ __global__ void gauge_kernel(const double* __restrict__ A2, const double* __rest
     if (tid == 0) {
         double sa = 0.0, sb = 0.0;
         for (int e = 0; e < mR * D; ++e) { sa += An[e] * An[e]; sb += Bn[e] * Bn[e]; }
-        nrm[0] = sa > 0.0 ? 1.0 / sqrt(sa) : 1.0;
-        nrm[1] = sb > 0.0 ? 1.0 / sqrt(sb) : 1.0;
+        nrm[0] = sa > 0.0 ? rsqrt_nr(sa) : 1.0;
+        nrm[1] = sb > 0.0 ? rsqrt_nr(sb) : 1.0;
     }
     __syncthreads();
     // write back: A''[ph][u][r][k] -> Asite[ph][x][y][z] with u = alpha', r = alpha, k = gamma

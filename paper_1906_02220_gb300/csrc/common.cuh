@@ -444,6 +444,38 @@ __global__ void sumsq_kernel(const T* __restrict__ x, long long n, double* out) 
     }
 }
 
+// FP64 reciprocal, reciprocal square root and square root by Newton-Raphson
+// iteration from the FP32 hardware estimates: each step squares the relative
+// error (reciprocal: y <- y + y (1 - x y); reciprocal square root:
+// y <- y (3/2 - (x/2) y^2)), so two steps take the ~2^-23 estimate below FP64
+// rounding (a few ulp).  FP64 division and square root issue as long
+// dependent sequences on GB300's narrow FP64 pipe; these take four or five
+// FP64 FMAs.  Arguments outside the FP32 normal range use the IEEE operation.
+__device__ __forceinline__ double rcp_nr(double x) {
+    const float ax = fabsf((float)x);
+    if (!(ax > 1e-30f && ax < 1e30f)) return 1.0 / x;
+    double y = (double)__frcp_rn((float)x);
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {      // x > 0
+    const float xf = (float)x;
+    if (!(xf > 1e-30f && xf < 1e30f)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf(xf);
+    const double h = 0.5 * x;
+    y = y * fma(-h * y, y, 1.5);
+    return y * fma(-h * y, y, 1.5);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {       // x >= 0
+    const float xf = (float)x;
+    if (!(xf > 1e-30f && xf < 1e30f)) return sqrt(x);
+    const double r = rsqrt_nr(x);
+    const double s = x * r;
+    return fma(fma(-s, s, x), 0.5 * r, s);                   // s + (x - s^2) / (2 sqrt x)
+}
+
 inline int sumsq_grid(long long n) {
     long long g = (n + 255) / 256;
     return (int)(g < 304 ? (g < 1 ? 1 : g) : 304);

@@ -89,6 +89,14 @@ void run_orth(int n, int k, double cut, const double* Y, double* Q, void* scratc
     kh::cast<T, double>(u, Q, (long long)n * k, st);
 }
 
+__global__ void newton_kernel(const double* __restrict__ x, int n, double* __restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[3 * i] = kh::rcp_nr(x[i]);
+        out[3 * i + 1] = x[i] > 0.0 ? kh::rsqrt_nr(x[i]) : 0.0;
+        out[3 * i + 2] = x[i] >= 0.0 ? kh::sqrt_nr(x[i]) : 0.0;
+    }
+}
+
 template <typename F>
 kh_status run(F&& f) {
     try {
@@ -158,6 +166,16 @@ kh_status kh_selftest_svd(int prec, int k, const double* X, double* S, double* L
     return run([&] {
         if (prec == KH_FP64) run_svd<double>(k, X, S, L, Qm, scratch, bytes, st);
         else run_svd<float>(k, X, S, L, Qm, scratch, bytes, st);
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+kh_status kh_selftest_fp64_newton(int n, const double* x, double* out, void* stream) {
+    if (n < 1 || !x || !out) return KH_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] {
+        newton_kernel<<<kh::grid_for(n), 256, 0, st>>>(x, n, out);
+        KH_LAUNCHED();
         KH_CUDA(cudaStreamSynchronize(st));
     });
 }

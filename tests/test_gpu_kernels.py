@@ -91,6 +91,29 @@ def test_one_sided_jacobi_svd(g, prec, k, decades):
     assert np.abs(X @ Q - L * S).max() <= 30 * eps * k * s[0]
 
 
+def test_fp64_newton_reciprocals_match_ieee(g):
+    """The FP64 reciprocal / reciprocal square root / square root used by the
+    latency-bound FP64 kernels (Newton-Raphson from FP32 estimates) agree with
+    the correctly rounded IEEE results to 2 ulp, also at the edges of the FP32
+    range where they fall back to the IEEE operations."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = np.concatenate([10.0 ** rng.uniform(-29, 29, 4000), rng.uniform(0.5, 2.0, 1000),
+                        [1.0, 2.0, 3.0, 1e-31, 1e31, 1e-300, 1e300, 5e-324, 2.0 ** -1022]])
+    xs = np.concatenate([x, -x[:100]])
+    r, rs, sq = (t.cpu().numpy() for t in g.selftest_fp64_newton(torch.as_tensor(xs, device="cuda:0")))
+    ulp = 2.3e-16
+    with np.errstate(over="ignore", divide="ignore"):
+        ref = 1.0 / xs
+    fin = np.isfinite(ref)
+    assert np.all(np.abs(r[fin] / ref[fin] - 1.0) <= 2 * ulp)
+    assert np.all(r[~fin] == ref[~fin])
+    pos = xs > 0
+    assert np.all(np.abs(rs[pos] / (1.0 / np.sqrt(xs[pos])) - 1.0) <= 2 * ulp)
+    assert np.all(np.abs(sq[pos] / np.sqrt(xs[pos]) - 1.0) <= 2 * ulp)
+    assert np.all(rs[~pos] == 0.0) and np.all(sq[~pos] == 0.0)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("n,k,decades", [(1, 1, 0), (37, 5, 2), (200, 33, 8), (1024, 80, 6), (300, 160, 4)])
 def test_cholqr2_orthonormal_basis(g, prec, n, k, decades):
