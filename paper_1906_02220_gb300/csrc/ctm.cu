@@ -830,6 +830,9 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         KH_CUDA(cudaMemsetAsync(P, 0, sizeof(T) * (size_t)n * chi, st));
         KH_CUDA(cudaMemsetAsync(PtT, 0, sizeof(T) * (size_t)n * chi, st));
     }
+    // P and P~^T are independent: P on the side lane (its own split-K scratch)
+    const bool side = side_lane();
+    if (side) fork_side();
     {   // P = Qb^T V S^-1/2
         GemmArgs<T> g;
         g.M = n; g.N = nkeep; g.K = n; g.batch = 1;
@@ -837,8 +840,8 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         g.B = Z1; g.sBk = k; g.sBn = 1; g.sBb = 0;
         g.C = P; g.sCm = chi; g.sCn = 1; g.sCb = 0;
         g.alpha = T(1); g.beta = T(0); g.colscale = isq;
-        g.sk = skbuf; g.sk_elems = sk_elems;
-        gemm<T>(g, st);
+        g.sk = side ? lanes[1].skbuf : skbuf; g.sk_elems = sk_elems;
+        gemm<T>(g, side ? lanes[1].st : st);
     }
     {   // P~^T = Qa U S^-1/2  (Qa stored transposed when tensor cores are used)
         GemmArgs<T> g;
@@ -850,58 +853,72 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         g.sk = skbuf; g.sk_elems = sk_elems;
         gemm<T>(g, st);
     }
+    if (side) join_side();
 }
 
+// Absorption: the corner updates C1n = P^T X1a, C4n = (C4 E3) P~^T (on the
+// side lane when free, with that lane's split-K and norm scratch) and the
+// edge update E4n = [E4^T P, site, permute] P~^T (on the move's lane), each
+// normalised and stored to the FP64 masters and the operand copies.
 template <typename T>
 void Engine<T>::absorb(Slot<T>& sl, int s) {
     const int chi = dm.chi, d2 = dm.d2, D = dm.D, n = dm.n;
     const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
-    {   // C1n = P^T X1a
-        GemmArgs<T> g;
-        g.M = chi; g.N = chi; g.K = n; g.batch = 1;
-        g.A = P; g.sAm = 1; g.sAk = chi; g.sAb = 0;
-        g.B = X1[0]; g.sBk = chi; g.sBn = 1; g.sBb = 0;
-        g.C = C1n; g.sCm = chi; g.sCn = 1; g.sCb = 0;
-        g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
-        g.sk = skbuf; g.sk_elems = sk_elems;
-        gemm<T>(g, st);
+    const bool side = side_lane();
+    if (side) fork_side();
+    {
+        cudaStream_t cs = side ? lanes[1].st : st;
+        T* csk = side ? lanes[1].skbuf : skbuf;
+        double* cns = (side ? lanes[1].dscr : dscr) + 8010;
+        {   // C1n = P^T X1a
+            GemmArgs<T> g;
+            g.M = chi; g.N = chi; g.K = n; g.batch = 1;
+            g.A = P; g.sAm = 1; g.sAk = chi; g.sAb = 0;
+            g.B = X1[0]; g.sBk = chi; g.sBn = 1; g.sBb = 0;
+            g.C = C1n; g.sCm = chi; g.sCn = 1; g.sCb = 0;
+            g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
+            g.sk = csk; g.sk_elems = sk_elems;
+            gemm<T>(g, cs);
+        }
+        const T* C4 = Cop + ((s + 3) & 3) * chi2;
+        const T* E3 = Eop + ((s + 2) & 3) * E1;
+        {   // C4E3[v][y4][(dk,db)] = sum_x3 C4[x3][y4] E3[v][(dk,db)][x3]
+            GemmArgs<T> g;
+            g.M = chi; g.N = d2; g.K = chi; g.batch = chi;
+            g.A = C4; g.sAm = 1; g.sAk = chi; g.sAb = 0;
+            g.B = E3; g.sBk = 1; g.sBn = chi; g.sBb = (long long)d2 * chi;
+            g.C = C4E3; g.sCm = d2; g.sCn = 1; g.sCb = n;
+            g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
+            gemm<T>(g, cs);
+        }
+        gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, cs, T(1), T(0), nullptr, csk, sk_elems);   // C4n = C4E3 P~^T
+        KH_CUDA(cudaMemsetAsync(cns, 0, 2 * sizeof(double), cs));
+        sumsq_kernel<T><<<sumsq_grid(chi2), 256, 0, cs>>>(C1n, chi2, cns);
+        KH_LAUNCHED();
+        sumsq_kernel<T><<<sumsq_grid(chi2), 256, 0, cs>>>(C4n, chi2, cns + 1);
+        KH_LAUNCHED();
+        store_normalized_kernel<T><<<grid_for(chi2), 256, 0, cs>>>(C1n, chi2, cns, sl.C + s * chi2, Cop + s * chi2);
+        KH_LAUNCHED();
+        store_normalized_kernel<T><<<grid_for(chi2), 256, 0, cs>>>(C4n, chi2, cns + 1, sl.C + ((s + 3) & 3) * chi2,
+                                                                   Cop + ((s + 3) & 3) * chi2);
+        KH_LAUNCHED();
     }
-    const T* C4 = Cop + ((s + 3) & 3) * chi2;
-    const T* E3 = Eop + ((s + 2) & 3) * E1;
     const T* E4 = Eop + ((s + 3) & 3) * E1;
-    {   // C4E3[v][y4][(dk,db)] = sum_x3 C4[x3][y4] E3[v][(dk,db)][x3]
-        GemmArgs<T> g;
-        g.M = chi; g.N = d2; g.K = chi; g.batch = chi;
-        g.A = C4; g.sAm = 1; g.sAk = chi; g.sAb = 0;
-        g.B = E3; g.sBk = 1; g.sBn = chi; g.sBb = (long long)d2 * chi;
-        g.C = C4E3; g.sCm = d2; g.sCn = 1; g.sCb = n;
-        g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
-        gemm<T>(g, st);
-    }
-    gemm_rm<T>(chi, chi, n, C4E3, false, PtT, false, C4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                  // C4n = C4E3 P~^T
     gemm_rm<T>(d2 * chi, d2 * chi, chi, E4, true, P, false, Y1, st);             // [(lk,lb,x4)][(dk,db,a)]
     site_operand(sl, Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3});         // [x4][a][lb][db][lk][dk]
     const long long w4 = (long long)s * dm.D4 * dm.D4;
     site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wedg + w4 : nullptr,
                sl.dl && sl.Wedg_lo ? sl.Wedg_lo + w4 : nullptr, site_presplit(sl));   // [x4][a][uk][rk][ub][rb]
     permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
-    gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // [a][rk][rb][a_up]
+    gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);   // [a][rk][rb][a_up]
     double* ns = dscr + 8010;
-    KH_CUDA(cudaMemsetAsync(ns, 0, 3 * sizeof(double), st));
-    sumsq_kernel<T><<<sumsq_grid(chi2), 256, 0, st>>>(C1n, chi2, ns);
-    KH_LAUNCHED();
-    sumsq_kernel<T><<<sumsq_grid(chi2), 256, 0, st>>>(C4n, chi2, ns + 1);
-    KH_LAUNCHED();
+    KH_CUDA(cudaMemsetAsync(ns + 2, 0, sizeof(double), st));
     sumsq_kernel<T><<<sumsq_grid(E1), 256, 0, st>>>(E4n, E1, ns + 2);
-    KH_LAUNCHED();
-    store_normalized_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C1n, chi2, ns, sl.C + s * chi2, Cop + s * chi2);
-    KH_LAUNCHED();
-    store_normalized_kernel<T><<<grid_for(chi2), 256, 0, st>>>(C4n, chi2, ns + 1, sl.C + ((s + 3) & 3) * chi2,
-                                                              Cop + ((s + 3) & 3) * chi2);
     KH_LAUNCHED();
     store_normalized_kernel<T><<<grid_for(E1), 256, 0, st>>>(E4n, E1, ns + 2, sl.E + ((s + 3) & 3) * E1,
                                                             Eop + ((s + 3) & 3) * E1);
     KH_LAUNCHED();
+    if (side) join_side();
 }
 
 template <typename T>

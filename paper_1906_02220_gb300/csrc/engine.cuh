@@ -160,6 +160,17 @@ struct Engine : EngineBase {
     cudaEvent_t lane_ev[3] = {nullptr, nullptr, nullptr};
     bool in_lanes = false;     // lanes 1, 2 busy with other slots (sweep_lanes)
     T *q1_hi = nullptr, *q1_lo = nullptr;   // where the 3xTF32 split of Q_{s+3} was written
+    // Side lane for independent pieces of a move (lane 1), when not busy:
+    // fork makes lane 1 wait for lane 0's work so far, join the reverse.
+    bool side_lane() const { return nlanes >= 2 && !in_lanes; }
+    void fork_side() {
+        KH_CUDA(cudaEventRecord(lane_ev[0], lanes[0].st));
+        KH_CUDA(cudaStreamWaitEvent(lanes[1].st, lane_ev[0], 0));
+    }
+    void join_side() {
+        KH_CUDA(cudaEventRecord(lane_ev[1], lanes[1].st));
+        KH_CUDA(cudaStreamWaitEvent(lanes[0].st, lane_ev[1], 0));
+    }
     void bind(int i);          // lane i's scratch and stream become the members used by the moves
     void save_lane(int i);
     void carve_lane(Carver& cv);
