@@ -605,7 +605,8 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
 // Orthonormal basis of the columns of Y (n x k) by two passes of the ordered
 // Cholesky-QR (cholqr_factor): Uo = Y X_1 X_2, dropped directions become zero
 // columns.  The second pass, in the first pass's column order, restores the
-// orthogonality that the first loses to the conditioning of Y.  Scratch: tmp (n x k), Xk (k x k), dG (k x k FP64).
+// orthogonality that the first loses to the conditioning of Y (by a single
+// Newton-Schulz step when that loss is already small).  Scratch: tmp (n x k), Xk (k x k), dG (k x k FP64).
 template <typename T>
 void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T* Uo, cudaStream_t st) {
     const double tau = sizeof(T) == 8 ? 1e-12 : 1e-5;
@@ -613,7 +614,9 @@ void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T*
     cholqr_factor<T>(dG, k, cut, tau, Xk, st);
     gemm_rm<T>(n, k, k, Y, false, Xk, false, tmp, st);
     gram<T>(tmp, n, k, dG, st);
-    cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st, false);
+    // the second pass sees nearly orthonormal columns: a Newton-Schulz step
+    // (3I - G)/2 suffices when G is within 1e-4 (FP32) / 1e-8 (FP64) of I
+    cholqr_factor<T>(dG, k, 1e-3, tau, Xk, st, false, sizeof(T) == 8 ? 1e-8 : 1e-4);
     gemm_rm<T>(n, k, k, tmp, false, Xk, false, Uo, st);
 }
 template void cholqr2<float>(const float*, int, int, double, float*, float*, double*, float*, cudaStream_t);
@@ -1237,7 +1240,8 @@ void svd_jacobi(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double to
 #undef KH_SVDJ
 }
 template <typename T>
-void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted) {
+void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted,
+                   double ns_tol) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
     size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
     static size_t attr_set = 0;
@@ -1245,11 +1249,11 @@ void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cu
         KH_CUDA(cudaFuncSetAttribute(cholqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set = sm;
     }
-    cholqr_kernel<T><<<1, kJacobiThreads, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0);
+    cholqr_kernel<T><<<1, 1024, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0, ns_tol);
     KH_LAUNCHED();
 }
-template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t, bool);
-template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t, bool);
+template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t, bool, double);
+template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t, bool, double);
 
 template void svd_jacobi<float>(const float*, int, float*, float*, float*, int, double, double, cudaStream_t, int*,
                                 int);

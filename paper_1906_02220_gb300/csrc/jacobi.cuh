@@ -429,9 +429,13 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
 // orthogonalisation, a weak column nearly parallel to a strong one never
 // rotates the strong one.
 // sorted = false keeps the given column order (a second pass over columns that
-// are already orthonormal: their norms carry no information).
+// are already orthonormal: their norms carry no information).  ns_tol > 0:
+// when the Gram matrix of the nonzero columns deviates from the identity by
+// less than ns_tol (max entry), X is one Newton-Schulz step (3I - G)/2
+// instead (orthogonality error ~ (3/4) ns_tol^2), zero for zero columns.
 template <typename T>
-void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted = true);
+void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted = true,
+                   double ns_tol = 0.0);
 
 #ifdef KH_JACOBI_KERNEL
 __device__ __forceinline__ float chol_recip(float x) { return __fdividef(1.f, x); }
@@ -444,8 +448,9 @@ __device__ __forceinline__ double chol_recip(double x) { return 1.0 / x; }
 // C (below) are joined by Li_CA = -Li_CC (L_CA Li_AA), two parallel products
 // per level, the intermediate kept in the unused upper triangle of L.
 template <typename T>
-__global__ void __launch_bounds__(kJacobiThreads)
-cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted) {
+__global__ void __launch_bounds__(1024)
+cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted,
+              double ns_tol) {
     constexpr int KM = sizeof(T) == 8 ? 112 : 160;   // largest k
     extern __shared__ unsigned char smem_raw[];
     const int ld = k | 1;                          // odd row stride: conflict-free column walks
@@ -459,6 +464,32 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
     const T tauT = (T)tau;
     for (int j = tid; j < k; j += nt) s_diag[j] = (T)fmax(G[(long long)j * k + j], 0.0);
     __syncthreads();
+    if (ns_tol > 0.0) {
+        // Gram of the nonzero columns close to the identity: one Newton-Schulz step
+        T dev = T(0);
+        for (int e = tid; e < k * k; e += nt) {
+            const int i = e / k, j = e % k;
+            if (s_diag[i] > T(0) && s_diag[j] > T(0)) dev = fmax(dev, fabs((T)G[e] - (i == j ? T(1) : T(0))));
+        }
+        for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+        if (lane == 0) s_inv[warp] = dev;          // s_inv reused as the reduction buffer (nw <= 32)
+        __syncthreads();
+        if (tid == 0) {
+            T m = T(0);
+            for (int w = 0; w < nw; ++w) m = fmax(m, s_inv[w]);
+            s_max = m;
+        }
+        __syncthreads();
+        if (s_max < (T)ns_tol) {
+            for (int e = tid; e < k * k; e += nt) {
+                const int i = e / k, j = e % k;
+                const bool live = s_diag[i] > T(0) && s_diag[j] > T(0);
+                X[e] = live ? ((i == j ? T(1.5) : T(0)) - T(0.5) * (T)G[e]) : T(0);
+            }
+            return;
+        }
+        __syncthreads();
+    }
     if (warp == 0) {
         T m = T(0);
         for (int j = lane; j < k; j += 32) m = fmax(m, s_diag[j]);
