@@ -172,6 +172,13 @@ def _peak(bound, prec, pk, pk_src):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "FP32 CUDA-core FMA peak 152 SM x 128 x 2 x %.0f MHz" % sm_mhz
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the bench
+# workload (profiles/eefu_kitaev_D4_chi64_top_kernels_full.md); the kernels
+# they describe must not have changed since, otherwise the entry is null.
+NCU_TRAFFIC = {("kitaev_D4_chi64", "tf32x3", "half_system_product"): 16.798976e6,
+               ("kitaev_D4_chi64", "tf32x3", "site_layer"): 8.934912e6}
+
+
 def roofline_entry(cat, c, bound, prec, pk, pk_src):
     if c["launches"] == 0 or c["ms"] <= 0:
         return None
@@ -180,7 +187,8 @@ def roofline_entry(cat, c, bound, prec, pk, pk_src):
     achieved = per_launch_flops / per_launch_s / 1e12
     peak, src = _peak(bound, prec, pk, pk_src)
     out = {"bound": bound, "kernel": cat, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-           "frac": achieved / peak, "traffic": None, "peak_source": src, "flops_per_launch": per_launch_flops,
+           "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((WORKLOAD, prec, cat)), "peak_source": src,
+           "flops_per_launch": per_launch_flops,
            "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6}
     if bound == "tensor" and prec == "tf32x3":
         out["mma_passes"] = 3      # achieved counts the 2MNK algorithmic flops once
