@@ -607,9 +607,11 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     double* Wd = dwork + 64;
     // The start only seeds the ALS, which then converges to tolerance in
     // FP64, so the singular vectors come from the FP32 one-sided Jacobi of
-    // Tm^T (Tm^T Q = L S, so Tm = Q S L^T and U = Q).
+    // Tm^T (Tm^T Q = L S, so Tm = Q S L^T and U = Q); only the D leading
+    // triplets are used, so only the D + 4 largest columns must converge
+    // (the near-null tail of Tm would otherwise keep the sweeps going).
     permute<double, float>(Tm, Gtf, {mT, mT}, {1, 0}, st);
-    svd_jacobi<float>(Gtf, mT, Ltf, (float*)Gt, Wtf, 60, 2e-6, 0.0, st);
+    svd_jacobi<float>(Gtf, mT, Ltf, (float*)Gt, Wtf, 60, 2e-6, 0.0, st, nullptr, D + 4);
     svd_init_kernel<float><<<grid_for(mT * D), 256, 0, st>>>(Wtf, Ltf, mT, D, A2, colsc, Wd);
     KH_LAUNCHED();
     // B''[(sB,aB,d,l)][k] = sum_i Tm[i][.] Wd[i][k] colsc[k]
