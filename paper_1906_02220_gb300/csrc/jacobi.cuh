@@ -9,6 +9,8 @@
 // formula: Golub & Van Loan, "Matrix Computations", the symmetric 2x2 Schur
 // decomposition used by the classical Jacobi method.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace kh {
@@ -230,15 +232,17 @@ __device__ __forceinline__ void jacobi_rotation(double a, double b, double g, do
 }
 
 // LP-lane groups (LP = 8), one column pair per group and every pair of a
-// round in flight (kp/2 groups); lane l of a group owns rows l, l + LP, ...,
-// l + (R-1) LP, so all row loops are unrolled at compile time.  The matrix is
+// round in flight (kp/2 groups); lane l of a group owns R rows (R/2 pairs of
+// adjacent rows, each loaded and stored as one vector), so all row loops are
+// unrolled at compile time.  The matrix is
 // scaled by a power of two so that its largest entry is O(1) (exact), which
 // lets the convergence test use squared cosines g^2 <= tol^2 a b without
 // square roots.  Columns are stored contiguously with a stride that is a
 // multiple of 32 words, zero below row k; the four groups of a warp walk the
-// row blocks of their columns in orders shifted by their slot, so that a load
-// of block j touches banks 8 ((j + slot) mod R mod 4) + lane: conflict-free
-// except where the shifted order wraps.  A sweep ends the iteration when no pair
+// 16-row blocks of their columns in orders shifted by their slot, so that the
+// two 64-byte halves a warp's vector access touches fall in alternate bank
+// halves (two wavefronts, the minimum for 256 bytes) except where the
+// shifted order wraps.  A sweep ends the iteration when no pair
 // needed a rotation, or when the largest pair cosine stops falling
 // quadratically while already below 1e3 eps (the rounding floor of the
 // column dot products).
@@ -292,13 +296,18 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
     int sw = 0;
     if (nrel <= 0 || nrel > kp) nrel = kp;
     const bool active = grp < kp / 2;
-    int offs[R];                               // row-block offsets in this group's order
+    // lane gl owns the row pairs (2 gl, 2 gl + 1) + 2 LP jb, jb < R/2, accessed
+    // as one 2-element vector; the row-pair blocks are visited in an order
+    // shifted by the group's slot in its warp
+    static_assert(R % 2 == 0, "R even");
+    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    int offs[R / 2];
     {
-        int jb = (grp % (32 / LP)) % R;
+        int jb = (grp % (32 / LP)) % (R / 2);
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-            offs[j] = LP * jb;
-            if (++jb == R) jb = 0;
+        for (int j = 0; j < R / 2; ++j) {
+            offs[j] = 2 * LP * jb;
+            if (++jb == R / 2) jb = 0;
         }
     }
     for (; sw < max_sweeps; ++sw) {
@@ -329,16 +338,33 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
             if (active) {
                 int p, q;
                 round_robin_pair<T>(r, grp, kp, p, q);
-                T* xp = Xc + p * ld + gl;
-                T* xq = Xc + q * ld + gl;
-                T* qp = Qc + p * ld + gl;
-                T* qq = Qc + q * ld + gl;
+                T* xp = Xc + p * ld + 2 * gl;
+                T* xq = Xc + q * ld + 2 * gl;
+                T* qp = Qc + p * ld + 2 * gl;
+                T* qq = Qc + q * ld + 2 * gl;
                 T u[R], v[R], qu[R], qv[R];
+                auto ld2 = [&](const T* base, T* dst) {
 #pragma unroll
-                for (int j = 0; j < R; ++j) { u[j] = xp[offs[j]]; v[j] = xq[offs[j]]; }
+                    for (int j = 0; j < R / 2; ++j) {
+                        const V2 w = *reinterpret_cast<const V2*>(base + offs[j]);
+                        dst[2 * j] = w.x;
+                        dst[2 * j + 1] = w.y;
+                    }
+                };
+                auto st2 = [&](T* base, const T* src) {
+#pragma unroll
+                    for (int j = 0; j < R / 2; ++j) {
+                        V2 w;
+                        w.x = src[2 * j];
+                        w.y = src[2 * j + 1];
+                        *reinterpret_cast<V2*>(base + offs[j]) = w;
+                    }
+                };
+                ld2(xp, u);
+                ld2(xq, v);
                 if (kPrefetchQ) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) { qu[j] = qp[offs[j]]; qv[j] = qq[offs[j]]; }
+                    ld2(qp, qu);
+                    ld2(qq, qv);
                 }
                 T a = T(0), b = T(0), g = T(0);
 #pragma unroll
@@ -358,20 +384,25 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
                     if (g2 > tol2 * ab) {
                         T cT, sT;
                         jacobi_rotation(a, b, g, cT, sT);
+                        T nu[R], nv[R];
 #pragma unroll
                         for (int j = 0; j < R; ++j) {
-                            xp[offs[j]] = cT * u[j] - sT * v[j];
-                            xq[offs[j]] = sT * u[j] + cT * v[j];
+                            nu[j] = cT * u[j] - sT * v[j];
+                            nv[j] = sT * u[j] + cT * v[j];
                         }
+                        st2(xp, nu);
+                        st2(xq, nv);
                         if (!kPrefetchQ) {
-#pragma unroll
-                            for (int j = 0; j < R; ++j) { qu[j] = qp[offs[j]]; qv[j] = qq[offs[j]]; }
+                            ld2(qp, qu);
+                            ld2(qq, qv);
                         }
 #pragma unroll
                         for (int j = 0; j < R; ++j) {
-                            qp[offs[j]] = cT * qu[j] - sT * qv[j];
-                            qq[offs[j]] = sT * qu[j] + cT * qv[j];
+                            nu[j] = cT * qu[j] - sT * qv[j];
+                            nv[j] = sT * qu[j] + cT * qv[j];
                         }
+                        st2(qp, nu);
+                        st2(qq, nv);
                         rot |= rel;
                     }
                 }
