@@ -365,7 +365,7 @@ inline void gemm(const GemmArgs<T>& g, cudaStream_t st) {
     // then reduce in a fixed order (deterministic)
     const long long tiles = (long long)((g.M + 63) / 64) * ((g.N + 63) / 64);
     if (g.batch == 1 && g.sk && tiles < 76 && g.K >= 256) {
-        int splits = (int)((152 + tiles - 1) / tiles);
+        int splits = (int)((304 + tiles - 1) / tiles);   // about two CTAs per SM
         int maxs = g.K / 128;
         if (splits > maxs) splits = maxs;
         if (splits > 32) splits = 32;

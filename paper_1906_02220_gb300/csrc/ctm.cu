@@ -309,7 +309,7 @@ void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
     if (k > 160) fail(KH_EINVAL, "gram: k > 160");
     KH_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * k * k, st));
     int rows_per = (int)((48 * 1024) / (sizeof(T) * k));     // stay within the default shared-memory limit
-    if (rows_per > 32) rows_per = 32;
+    if (rows_per > 16) rows_per = 16;
     const int grid = (n + rows_per - 1) / rows_per;
     const size_t sm = sizeof(T) * rows_per * k;
     switch ((k + 15) / 16) {
