@@ -236,3 +236,35 @@ def test_trotter_steps_match_oracle(g, prec, D, chi, steps):
         # gauge-covariant (fixed by the balanced-SVD convention), hence looser
         # than the invariants above
         assert np.abs(_nrm(Tg) - _nrm(To)).max() < (1e-7 if prec == "fp64" else 1e-4)
+
+
+def test_bench_configuration_full_size_against_fp64_path(g):
+    """The bench workload at full size (Kitaev K=1, J=0, D=4, chi=64, dbeta=0.01,
+    4 CTM sweeps per layer, 2 per observables mapping) in the launch
+    configuration bench.py times (3xTF32, three lanes): one Trotter step plus
+    observables agrees with the library's FP64 path on the same start to the
+    FP32-level tolerance, and the properties that hold at any size hold: E/site
+    is half the sum of the bond energies (no field), real tensors give <S^y> = 0,
+    truncation errors lie in [0, 1)."""
+    import torch
+    D, chi = 4, 64
+    A0, B0 = kh_inputs.perturbed_product_state(D, seed=0, eps=0.05)
+    Hs = [g.bond_hamiltonian(gm, 0.0, 1.0) for gm in "xyz"]
+    res = {}
+    for prec in ("tf32x3", "fp64"):
+        ctx = g.Context(D, chi, prec, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+        ctx.set_state(_t(A0), _t(B0))
+        ctx.eefu_trotter_step(0.0, [1.0, 1.0, 1.0], 0.01, ctm_max_sweeps=4, ctm_min_sweeps=4, ctm_tol=-1.0,
+                              info=False)
+        res[prec] = ctx.observables(Hs, ctm_max_sweeps=2, ctm_min_sweeps=2, ctm_tol=-1.0)
+        torch.cuda.synchronize()
+    a, b = res["tf32x3"], res["fp64"]
+    for r in (a, b):
+        assert all(np.isfinite(v) for v in r.values())
+        assert abs(r["E_site"] - 0.5 * (r["Hx"] + r["Hy"] + r["Hz"])) < 1e-12
+        assert r["Ay"] == 0.0 and r["By"] == 0.0
+        assert 0.0 <= r["trunc"] < 1.0
+    scale = max(abs(b["E_site"]), 1e-3)
+    assert abs(a["E_site"] - b["E_site"]) < 2e-5 * scale
+    for k in ("Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+        assert abs(a[k] - b[k]) < 2e-5 * max(abs(b[k]), 1e-3), k
