@@ -623,13 +623,9 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     const int cgrid = (int)std::min<long long>(32, (nR + threads - 1) / threads);
     const size_t chol_sm = sizeof(double) * ((size_t)m * (m + 1) + 4 * m);
     const int chol_smem = chol_sm <= 200 * 1024 ? 1 : 0;
-    if (chol_smem && chol_sm > 48 * 1024) {
-        static size_t attr_set = 0;
-        if (chol_sm > attr_set) {
-            KH_CUDA(cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)chol_sm));
-            attr_set = chol_sm;
-        }
+    if (chol_smem) {
+        static size_t granted[kMaxDevices] = {};
+        smem_opt_in(chol_solve_kernel, chol_sm, granted);
     }
     const int* done = flags + 1;
     auto normal_eqs = [&](const double* oth, int side) {
