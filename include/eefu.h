@@ -95,7 +95,12 @@ size_t kh_workspace_bytes(const kh_config* cfg);
  * 256-byte aligned, at least kh_workspace_bytes(cfg) bytes, not touched by
  * the caller while the context lives.  stream: a cudaStream_t (0 = legacy
  * default stream).  All environments start at the traced boundary; the
- * state starts at the beta = 0 purification (Sec. III). */
+ * state starts at the beta = 0 purification (Sec. III).  A context with
+ * n_slots >= 6 also creates two non-blocking streams of its own (freed by
+ * kh_destroy), with their own scratch in the workspace, on which independent
+ * parts of a CTM move and the three mappings of the observables run
+ * concurrently; every call forks them from `stream` and joins them back
+ * before it returns or synchronises, so callers only order work on `stream`. */
 kh_status kh_create(kh_ctx** ctx, const kh_config* cfg, void* dev_workspace,
                     size_t workspace_bytes, void* stream);
 void kh_destroy(kh_ctx* ctx);
