@@ -268,3 +268,26 @@ def test_bench_configuration_full_size_against_fp64_path(g):
     assert abs(a["E_site"] - b["E_site"]) < 2e-5 * scale
     for k in ("Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
         assert abs(a[k] - b[k]) < 2e-5 * max(abs(b[k]), 1e-3), k
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("tf32x3", 2e-5)])
+def test_lanes_match_single_stream(g, prec, tol):
+    """A context with six slots runs the independent pieces of a CTM move
+    (corner s+3, P, the corner updates) on a second stream with its own
+    scratch; one with three slots runs every move on its one stream.  Both
+    give the same converged metric and projector spectra."""
+    D, chi = 3, 14
+    A, B = kh_inputs.perturbed_product_state(D, seed=9, eps=0.2)
+    T = peps.composite(A, B, "y")
+    out = []
+    for n_slots in (3, 6):
+        ctx = g.Context(D, chi, prec, n_slots=n_slots, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+        ctx.ctm_set_tensor(0, _t(T))
+        ctx.ctm_sweep(0, 200, 3, 1e-12 if prec == "fp64" else 1e-7, allow_noconv=True)
+        N = _nrm(ctx.ctm_metric(0).cpu().numpy())
+        specs = [_nrm(ctx.ctm_projectors(0, d)[0].cpu().numpy()) for d in range(4)]
+        out.append((N, specs))
+    (N3, s3), (N6, s6) = out
+    assert np.abs(N3 - N6).max() < tol
+    for d in range(4):
+        assert np.abs(s3[d] - s6[d]).max() < tol
