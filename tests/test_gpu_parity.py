@@ -291,3 +291,33 @@ def test_lanes_match_single_stream(g, prec, tol):
     assert np.abs(N3 - N6).max() < tol
     for d in range(4):
         assert np.abs(s3[d] - s6[d]).max() < tol
+
+
+@pytest.mark.parametrize("D,chi", [(5, 100), (6, 144)])
+def test_large_configurations_run_and_agree_across_precisions(g, D, chi):
+    """The larger bench configurations, (D, chi) = (5, 100) (double-layer site
+    contraction on CUDA cores: D^4 = 625 rows are not 16-byte multiples) and
+    (6, 144) (layer-by-layer site contraction, k = chi + 16 = 160 at the
+    Jacobi limit, the 216 x 216 ALS solve in global memory): one z gate with
+    its environment-weighted bond update and the observables, in 3xTF32 and in
+    FP32 on CUDA cores, satisfy the size-independent properties and agree to
+    single-precision accuracy."""
+    import torch
+    A, B = kh_inputs.perturbed_product_state(D, seed=4, eps=0.05)
+    gate = g.gate(g.bond_hamiltonian("z", 0.0, 1.0), 0.01)
+    Hs = [g.bond_hamiltonian(gm, 0.0, 1.0) for gm in "xyz"]
+    res = {}
+    for prec in ("tf32x3", "fp32"):
+        ctx = g.Context(D, chi, prec, svd_cut=1e-6)
+        ctx.set_state(_t(A), _t(B))
+        info = ctx.eefu_apply_gate("z", gate, ctm_max_sweeps=2, ctm_min_sweeps=2, ctm_tol=-1.0)
+        assert np.isfinite(info["rel_cost"]) and 0.0 <= info["trunc"] < 1.0
+        res[prec] = ctx.observables(Hs, ctm_max_sweeps=1, ctm_min_sweeps=1, ctm_tol=-1.0)
+        del ctx
+        torch.cuda.synchronize()
+    a, b = res["tf32x3"], res["fp32"]
+    for r in (a, b):
+        assert all(np.isfinite(v) for v in r.values())
+        assert abs(r["E_site"] - 0.5 * (r["Hx"] + r["Hy"] + r["Hz"])) < 1e-12
+        assert r["Ay"] == 0.0 and r["By"] == 0.0
+    assert abs(a["E_site"] - b["E_site"]) < 1e-4 * max(abs(b["E_site"]), 1e-3)
