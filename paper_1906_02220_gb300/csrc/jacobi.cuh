@@ -243,9 +243,10 @@ __device__ __forceinline__ void jacobi_rotation(double a, double b, double g, do
 // two 64-byte halves a warp's vector access touches fall in alternate bank
 // halves (two wavefronts, the minimum for 256 bytes) except where the
 // shifted order wraps.  A sweep ends the iteration when no pair
-// needed a rotation, or when the largest pair cosine stops falling
-// quadratically while already below 1e3 eps (the rounding floor of the
-// column dot products).
+// needed a rotation, when its largest pair cosine c had c^2 < tol / 10 (the
+// cosines left are ~c^2, so the next sweep would rotate nothing), or when the
+// largest pair cosine stops falling quadratically while already below
+// 1e3 eps (the rounding floor of the column dot products).
 template <typename T, int LP, int R>
 __global__ void __launch_bounds__(LP * R / 2 * LP)
 svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __restrict__ L_out,
@@ -420,6 +421,9 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
         int brot = 0;
         for (int w = 0; w < nw; ++w) { bmax = fmax(bmax, s_wmax[w]); brot |= s_wrot[w]; }
         if (brot == 0) break;
+        // quadratic convergence: the cosines left after a sweep whose largest
+        // was c are ~c^2, so c^2 < tol / 10 needs no confirming sweep
+        if (bmax < T(0.1) * tol_eff) break;
         if (bmax < floor2 && bmax > T(0.0625) * prev2) break;   // stagnated at the floor
         prev2 = bmax;
     }
