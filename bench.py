@@ -17,6 +17,7 @@ import argparse
 import json
 import os
 import statistics
+import tempfile
 import subprocess
 import sys
 import time
@@ -102,8 +103,8 @@ class ClockSampler:
 
     def __init__(self, gpu_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks_%d.csv" % gpu_index) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % gpu_index
+        self.path = os.path.join(os.environ.get("KH_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "bench_clocks_%d.csv" % gpu_index)
         self.idx = gpu_index
 
     def start(self):

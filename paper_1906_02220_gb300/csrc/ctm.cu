@@ -139,12 +139,6 @@ void Engine<T>::carve_lane(Carver& cv) {
     Z2 = cv.take<T>(n * kk);
     Vo = cv.take<T>(n * kk);
     Uf = cv.take<T>(n * kk);
-    G1 = cv.take<T>(kk * kk);
-    W1 = cv.take<T>(kk * kk);
-    G2 = cv.take<T>(kk * kk);
-    W2 = cv.take<T>(kk * kk);
-    L1 = cv.take<T>(kk);
-    L2 = cv.take<T>(kk);
     Xk = cv.take<T>(kk * kk);
     Hk = cv.take<T>(kk * kk);
     Lk = cv.take<T>(kk * kk);
@@ -623,8 +617,7 @@ template void cholqr2<float>(const float*, int, int, double, float*, float*, dou
 template void cholqr2<double>(const double*, int, int, double, double*, double*, double*, double*, cudaStream_t);
 
 template <typename T>
-void Engine<T>::orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L) {
-    (void)G; (void)W; (void)L;
+void Engine<T>::orth(const T* Y, int n, int k, T* Uo) {
     prof_begin(8);
     cholqr2<T>(Y, n, k, cfg.svd_cut, Qt, Xk, dscr + 8192, Uo, st);
     prof_end(8, 0.0);
@@ -775,7 +768,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
             rand_kernel<T><<<grid_for((long long)n * k), 256, 0, st>>>(V0, (long long)n * k, cfg.seed,
                                                                       stream * 1000003ULL + (rng_counter++));
             KH_LAUNCHED();
-            orth(V0, n, k, U, G1, W1, L1);
+            orth(V0, n, k, U);
             Vin = U;
             q = cfg.svd_iters_cold;
         } else {
@@ -798,11 +791,11 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
             prof_begin(9);
             gemm_rm<T>(n, k, n, Mt, true, Vin, false, Z1, st, T(1), T(0), nullptr, skbuf, sk_elems);                 // Y = M V
             prof_end(9, 2.0 * n * (double)n * k);
-            orth(Z1, n, k, U, G1, W1, L1);                                     // U = orth(Y)
+            orth(Z1, n, k, U);                                                 // U = orth(Y)
             prof_begin(9);
             gemm_rm<T>(n, k, n, Mt, false, U, false, Z2, st, T(1), T(0), nullptr, skbuf, sk_elems);                  // Z = M^T U
             prof_end(9, 2.0 * n * (double)n * k);
-            orth(Z2, n, k, Vo, G2, W2, L2);                                    // V' = orth(Z)
+            orth(Z2, n, k, Vo);                                                // V' = orth(Z)
             Vin = Vo;
         }
         // G = H^T = Z^T V' with H = V'^T Z the Rayleigh-Ritz matrix (M ~ U G V'^T).

@@ -109,7 +109,7 @@ struct EngineBase {
 // observables run the CTMs of the three bond mappings concurrently (each
 // move is latency-bound and leaves most SMs idle).
 #define KH_LANE_PTRS(X) X(Cop) X(Eop) X(Y1) X(Yp) X(Zk) X(Qt) X(Mt) X(V0) X(Z1) X(U) X(Z2) X(Vo) X(Uf) \
-    X(G1) X(W1) X(L1) X(G2) X(W2) X(L2) X(Xk) X(Hk) X(Lk) X(Qk) X(Sk) X(isq) X(P) X(PtT) X(C4E3) X(C1n) \
+    X(Xk) X(Hk) X(Lk) X(Qk) X(Sk) X(isq) X(P) X(PtT) X(C4E3) X(C1n) \
     X(C4n) X(E4n) X(mt1) X(mt2) X(mup) X(mdn) X(mupp) X(mdnp) X(mN4) X(skbuf)
 #define KH_LANE_DPTRS(X) X(dscr) X(N) X(dwork)
 template <typename T>
@@ -137,7 +137,6 @@ struct Engine : EngineBase {
     T *X1[2] = {nullptr, nullptr}, *Y1 = nullptr, *Yp = nullptr, *Zk = nullptr, *Qt = nullptr;
     T *Q[2] = {nullptr, nullptr}, *Mt = nullptr;
     T *V0 = nullptr, *Z1 = nullptr, *U = nullptr, *Z2 = nullptr, *Vo = nullptr, *Uf = nullptr;
-    T *G1 = nullptr, *W1 = nullptr, *L1 = nullptr, *G2 = nullptr, *W2 = nullptr, *L2 = nullptr;
     T *Xk = nullptr, *Hk = nullptr, *Lk = nullptr, *Qk = nullptr, *Sk = nullptr;
     T *isq = nullptr, *P = nullptr, *PtT = nullptr, *C4E3 = nullptr;
     T *C1n = nullptr, *C4n = nullptr, *E4n = nullptr;
@@ -193,7 +192,7 @@ struct Engine : EngineBase {
     void site_operand(const Slot<T>& sl, const T* Y, T* Yp, const std::vector<long long>& shape,
                       const std::vector<int>& order);
     void projector(Slot<T>& sl, int dir, int slot_id);
-    void orth(const T* Y, int n, int k, T* Uo, T* G, T* W, T* L);
+    void orth(const T* Y, int n, int k, T* Uo);
     void absorb(Slot<T>& sl, int s);
     void move(Slot<T>& sl, int s, int slot_id);
     void compute_metric(Slot<T>& sl, double* N_out);
