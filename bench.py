@@ -297,7 +297,7 @@ def run_ours(a, rank, world, local, pg):
         err = None
         if not a.no_fp64_check and a.prec != "fp64":
             err = fp64_check(a, g, dev, A0, B0, w, Hs, last, a.warmup + a.steps)
-        cpu = None if a.no_cpu_baseline else cpu_baseline(a, w, A0, B0)
+        cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, A0, B0)   # N = 1 only
         out = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
