@@ -168,19 +168,23 @@ inline PermArgs make_perm(const std::vector<long long>& in_shape, const std::vec
     return a;
 }
 
-// Opt a kernel in to more than 48 KB of dynamic shared memory on the current
-// device, once per (kernel, device) and size; cache is the call site's table
-// of the sizes already granted, indexed by device ordinal (the attribute is
-// per device, so a context on a second GPU needs its own opt-in).
+// Let a kernel launch with `bytes` of dynamic shared memory on the current
+// device: the 48 KB default covers static plus dynamic shared memory, so the
+// opt-in is made when the kernel's static size plus `bytes` exceeds it; once
+// per (kernel, device) and size, cache being the call site's table of the
+// sizes already settled, indexed by device ordinal (the attribute is per
+// device, so a context on a second GPU needs its own opt-in).
 constexpr int kMaxDevices = 64;
 template <typename K>
 inline void smem_opt_in(K kernel, size_t bytes, size_t (&cache)[kMaxDevices]) {
-    if (bytes <= 48 * 1024) return;
     int dev = 0;
     KH_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) fail(KH_EINVAL, "device ordinal beyond 63");
     if (cache[dev] >= bytes) return;
-    KH_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cudaFuncAttributes fa;
+    KH_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    if (fa.sharedSizeBytes + bytes > 48 * 1024)
+        KH_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     cache[dev] = bytes;
 }
 

@@ -69,11 +69,13 @@ def test_jacobi_near_diagonal_relative_accuracy(g):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("k,decades", [(1, 0), (6, 3), (24, 9), (40, 6), (57, 6), (80, 12), (90, 6), (100, 8),
-                                       (113, 6), (150, 6)])
+@pytest.mark.parametrize("k,decades", [(1, 0), (6, 3), (24, 9), (40, 6), (45, 6), (57, 6), (80, 12), (90, 6),
+                                       (100, 8), (113, 6), (150, 6)])
 def test_one_sided_jacobi_svd(g, prec, k, decades):
     """Singular values to absolute accuracy ~eps * s_1 (no squaring), also for
-    a matrix with a null block; X Q = L S and Q orthogonal."""
+    a matrix with a null block; X Q = L S and Q orthogonal.  k = 45 in FP64
+    needs 47 KB of dynamic on top of the kernel's static shared memory (the
+    48 KB default covers both)."""
     import torch
     if prec == "fp64" and k > 112:
         pytest.skip("beyond the FP64 Jacobi limit")
@@ -115,7 +117,8 @@ def test_fp64_newton_reciprocals_match_ieee(g):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("n,k,decades", [(1, 1, 0), (37, 5, 2), (200, 33, 8), (1024, 80, 6), (300, 160, 4)])
+@pytest.mark.parametrize("n,k,decades", [(1, 1, 0), (37, 5, 2), (200, 33, 8), (300, 76, 5),
+                                         (1024, 80, 6), (300, 160, 4)])
 def test_cholqr2_orthonormal_basis(g, prec, n, k, decades):
     """Ordered CholQR2 on graded columns with an exactly dependent and a zero
     column: the kept columns are orthonormal, the dropped ones exactly zero,

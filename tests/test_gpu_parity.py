@@ -321,3 +321,29 @@ def test_large_configurations_run_and_agree_across_precisions(g, D, chi):
         assert abs(r["E_site"] - 0.5 * (r["Hx"] + r["Hy"] + r["Hz"])) < 1e-12
         assert r["Ay"] == 0.0 and r["By"] == 0.0
     assert abs(a["E_site"] - b["E_site"]) < 1e-4 * max(abs(b["E_site"]), 1e-3)
+
+
+@pytest.mark.parametrize("D,chi", [(2, 2), (3, 5), (2, 13)])
+def test_small_and_odd_shapes_with_lanes(g, D, chi):
+    """Tiny and odd shapes through a whole Trotter step and the observables on a
+    six-slot context (three lanes): chi = 2 (full-mode SVD, n = 8), n = 45 and
+    n = 52 (the half-system product on CUDA cores when n is not a multiple of 4
+    in the tensor-core precisions); 3xTF32 agrees with FP64 and the
+    size-independent properties hold."""
+    import torch
+    A, B = kh_inputs.perturbed_product_state(D, seed=2, eps=0.1)
+    Hs = [g.bond_hamiltonian(gm, 0.3, 1.0) for gm in "xyz"]
+    res = {}
+    for prec in ("tf32x3", "fp64"):
+        ctx = g.Context(D, chi, prec, svd_cut=1e-12 if prec == "fp64" else 1e-6)
+        ctx.set_state(_t(A), _t(B))
+        ctx.eefu_trotter_step(0.3, [1.0, 1.0, 1.0], 0.02, ctm_max_sweeps=3, ctm_min_sweeps=3, ctm_tol=-1.0,
+                              info=False)
+        res[prec] = ctx.observables(Hs, ctm_max_sweeps=2, ctm_min_sweeps=2, ctm_tol=-1.0)
+        torch.cuda.synchronize()
+    for r in res.values():
+        assert all(np.isfinite(v) for v in r.values())
+        assert abs(r["E_site"] - 0.5 * (r["Hx"] + r["Hy"] + r["Hz"])) < 1e-12
+        assert 0.0 <= r["trunc"] < 1.0
+    a, b = res["tf32x3"], res["fp64"]
+    assert abs(a["E_site"] - b["E_site"]) < 1e-4 * max(abs(b["E_site"]), 1e-3)
