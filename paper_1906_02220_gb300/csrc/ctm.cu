@@ -604,8 +604,15 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
 template <typename T>
 void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T* Uo, cudaStream_t st) {
     const double tau = sizeof(T) == 8 ? 1e-12 : 1e-5;
+    // FP64: pivots below k 2^-53 / tau, whose acceptance could lift the
+    // rounding noise of a later, exactly dependent column above tau, are
+    // deferred.  FP32 defers none: there an accepted noise direction is only a
+    // surplus basis vector that the Rayleigh-Ritz step discards, and the same
+    // bound (k 2^-24 / 1e-5, about 0.5) would reorder most columns of an early,
+    // poorly converged iteration.
+    const double defer = sizeof(T) == 8 ? k * 0x1p-53 / tau : 0.0;
     gram<T>(Y, n, k, dG, st);
-    cholqr_factor<T>(dG, k, cut, tau, Xk, st);
+    cholqr_factor<T>(dG, k, cut, tau, Xk, st, true, 0.0, defer);
     gemm_rm<T>(n, k, k, Y, false, Xk, false, tmp, st);
     gram<T>(tmp, n, k, dG, st);
     // the second pass sees nearly orthonormal columns: a Newton-Schulz step
@@ -1227,16 +1234,16 @@ void svd_jacobi(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double to
 }
 template <typename T>
 void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted,
-                   double ns_tol) {
+                   double ns_tol, double defer) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
     size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
     static size_t granted[kMaxDevices] = {};
     smem_opt_in(cholqr_kernel<T>, sm, granted);
-    cholqr_kernel<T><<<1, 1024, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0, ns_tol);
+    cholqr_kernel<T><<<1, 1024, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0, ns_tol, defer);
     KH_LAUNCHED();
 }
-template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t, bool, double);
-template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t, bool, double);
+template void cholqr_factor<float>(const double*, int, double, double, float*, cudaStream_t, bool, double, double);
+template void cholqr_factor<double>(const double*, int, double, double, double*, cudaStream_t, bool, double, double);
 
 template void svd_jacobi<float>(const float*, int, float*, float*, float*, int, double, double, cudaStream_t, int*,
                                 int);

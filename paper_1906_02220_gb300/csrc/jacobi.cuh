@@ -468,9 +468,15 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
 // when the Gram matrix of the nonzero columns deviates from the identity by
 // less than ns_tol (max entry), X is one Newton-Schulz step (3I - G)/2
 // instead (orthogonality error ~ (3/4) ns_tol^2), zero for zero columns.
+// defer > tau: a column whose pivot lies in (tau, defer) is moved, once, to the
+// end of the order.  Accepting a pivot d multiplies the rounding error of every
+// later pivot by about 1/d, and Q = Y X inherits an error ~ eps ||Y|| / sqrt(d)
+// outside span(Y); a column nearly parallel to the ones before it is therefore
+// taken after the well-conditioned ones, by which time its residual has
+// usually become exactly zero (a rank-revealing order, as in column pivoting).
 template <typename T>
 void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted = true,
-                   double ns_tol = 0.0);
+                   double ns_tol = 0.0, double defer = 0.0);
 
 #ifdef KH_JACOBI_KERNEL
 __device__ __forceinline__ float chol_recip(float x) { return __fdividef(1.f, x); }
@@ -485,7 +491,7 @@ __device__ __forceinline__ double chol_recip(double x) { return 1.0 / x; }
 template <typename T>
 __global__ void __launch_bounds__(1024)
 cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted,
-              double ns_tol) {
+              double ns_tol, double defer) {
     constexpr int KM = sizeof(T) == 8 ? 112 : 160;   // largest k
     extern __shared__ unsigned char smem_raw[];
     const int ld = k | 1;                          // odd row stride: conflict-free column walks
@@ -554,10 +560,40 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
     __syncthreads();
     // Cholesky: step j leaves the Schur-complement entries a_ij (i > j) in
     // column j and subtracts a_ij a_cj / d_j from the trailing block; a pivot
-    // d_j <= tau drops direction j (no update, zero column).
-    for (int j = 0; j < k; ++j) {
-        const T d = Lm[j * ld + j];
-        if (d > tauT) {                           // same value in every thread
+    // d_j <= tau drops direction j (no update, zero column).  A pivot in
+    // (tau, defer) is first rotated to the end of the order (positions
+    // j+1, ..., k-1 move up by one), each column at most once: the nd deferred
+    // columns occupy the last nd positions.
+    const T deferT = (T)defer;
+    int nd = 0;
+    for (int j = 0; j < k;) {
+        const T d = Lm[j * ld + j];              // same value in every thread
+        if (d > tauT && d < deferT && j < k - nd) {
+            // new position a holds old position src(a): a (a < j), a + 1 (j <= a < k-1), j (a = k-1).
+            // Rows j.. of the lower triangle are gathered into Li, then copied back.
+            const int rows = k - j;
+            int pnew = 0;
+            if (tid < rows) pnew = s_perm[tid + 1 < rows ? j + tid + 1 : j];
+            for (int e = tid; e < rows * k; e += nt) {
+                const int a = j + e / k, b = e % k;
+                if (b > a) continue;
+                const int pa = a < k - 1 ? a + 1 : j;
+                const int pb = b < j ? b : (b < k - 1 ? b + 1 : j);
+                Li[a * ld + b] = pa >= pb ? Lm[pa * ld + pb] : Lm[pb * ld + pa];
+            }
+            __syncthreads();
+            for (int e = tid; e < rows * k; e += nt) {
+                const int a = j + e / k, b = e % k;
+                if (b > a) continue;
+                Lm[a * ld + b] = Li[a * ld + b];
+                Li[a * ld + b] = T(0);
+            }
+            if (tid < rows) s_perm[j + tid] = pnew;
+            __syncthreads();
+            ++nd;
+            continue;
+        }
+        if (d > tauT) {
             const T rd = chol_recip(d);
             for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
                 const T lij = Lm[i * ld + j] * rd;
@@ -565,6 +601,7 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
             }
         }
         __syncthreads();
+        ++j;
     }
     for (int j = tid; j < k; j += nt) {
         const T d = Lm[j * ld + j];
