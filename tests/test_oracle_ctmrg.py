@@ -75,3 +75,50 @@ def test_projector_is_oblique_identity_when_untruncated():
     assert np.allclose(Qul.reshape(n, n).T @ P @ Pt @ Qdl.reshape(n, n), M, atol=1e-10)
     assert trunc < 1e-28
     assert np.allclose(np.sort(spec)[::-1], np.linalg.svd(M, compute_uv=False), atol=1e-12)
+
+
+def _bond_correlator(Kh, Kv, leg, broken=False, chi=24):
+    """<s_i s_j> on the bond leaving a site through leg r (horizontal) or d
+    (vertical), as a one-site impurity: a ket-only bond matrix
+    M = V^-1 (W o s s^T) V^-T absorbed into that leg turns the bond weight
+    W(s_i, s_j) of psi into s_i s_j W(s_i, s_j), so <T'|N|T> / <T|N|T> is the
+    correlator (metric and mixed ket/bra expectation of the oracle)."""
+    T = exact.ising_peps(Kh, Kv)
+    Kb = Kh if leg == "r" else Kv
+    Vi = np.linalg.inv(exact.ising_bond_root(Kb))
+    W = np.array([[np.exp(Kb / 2), np.exp(-Kb / 2)], [np.exp(-Kb / 2), np.exp(Kb / 2)]])
+    M = Vi @ (W * np.array([[1.0, -1.0], [-1.0, 1.0]])) @ Vi.T
+    Ti = np.einsum("slurd,rR->sluRd", T, M) if leg == "r" else np.einsum("slurd,dD->slurD", T, M)
+    edge = None
+    if broken:
+        V = exact.ising_bond_root(Kh)
+        edge = np.outer(V[0], V[0]).reshape(4)
+    a, env, info = _run(T, chi, edge_vec=edge)
+    N = ctmrg.metric(env, 2)
+    return np.trace(ctmrg.expval_matrix(Ti, N, T)) / np.trace(ctmrg.expval_matrix(T, N))
+
+
+@pytest.mark.parametrize("K,broken", [(0.2, False), (0.3, False), (0.6, True)])
+def test_nearest_neighbour_correlation_closed_form(K, broken):
+    """Isotropic square-lattice Ising internal energy (Onsager): per site
+    u/J = -coth 2K [1 + (2/pi)(2 tanh^2 2K - 1) K1(k)], k = 2 sinh 2K / cosh^2 2K,
+    K1 the complete elliptic integral of the first kind; two bonds per site, so
+    <s s> = -u / 2J.  Independent of the free-energy integral used above."""
+    from scipy.special import ellipk
+    k = 2 * np.sinh(2 * K) / np.cosh(2 * K) ** 2
+    ref = 0.5 / np.tanh(2 * K) * (1 + (2 / np.pi) * (2 * np.tanh(2 * K) ** 2 - 1) * ellipk(k * k))
+    for leg in ("r", "d"):
+        assert abs(_bond_correlator(K, K, leg, broken) - ref) < 1e-10
+
+
+@pytest.mark.parametrize("Kh,Kv", [(0.3, 0.2), (0.15, 0.36)])
+def test_anisotropic_correlations_are_free_energy_derivatives(Kh, Kv):
+    """d(-beta f)/dK_h = <s s>_horizontal and d(-beta f)/dK_v = <s s>_vertical
+    (central differences of the Onsager integral, step 1e-5): a swap of the
+    horizontal and vertical legs of the metric fails."""
+    h = 1e-5
+    dh = (exact.onsager_lnZ(Kh + h, Kv) - exact.onsager_lnZ(Kh - h, Kv)) / (2 * h)
+    dv = (exact.onsager_lnZ(Kh, Kv + h) - exact.onsager_lnZ(Kh, Kv - h)) / (2 * h)
+    assert abs(dh - dv) > 0.05
+    assert abs(_bond_correlator(Kh, Kv, "r") - dh) < 1e-9
+    assert abs(_bond_correlator(Kh, Kv, "d") - dv) < 1e-9
