@@ -1202,7 +1202,7 @@ template <typename T, int LP, int R>
 static void svd_jacobi_launch(const T* X, int k, T* sv, T* L, T* Qm, int max_sweeps, double tol, double cut,
                               cudaStream_t st, int* sweep_count, int nrel) {
     const int kp = (k + 1) & ~1;
-    size_t sm = (size_t)2 * kp * ((LP * R + 31) & ~31) * sizeof(T);
+    size_t sm = (size_t)2 * kp * svdj_ld<T>(LP * R) * sizeof(T);
     static size_t granted[kMaxDevices] = {};   // per instantiation
     smem_opt_in(svd_jacobi_kernel<T, LP, R>, sm, granted);
     const int threads = ((kp / 2) * LP + 31) / 32 * 32;

@@ -204,6 +204,16 @@ template <typename T>
 void svd_jacobi(const T* X, int k, T* s, T* L, T* Q, int max_sweeps, double tol, double cut, cudaStream_t st,
                 int* sweep_count = nullptr, int nrel = 0);
 
+// Column stride of the one-sided Jacobi's shared-memory matrices: the RL =
+// LP R rows a group touches, rounded up to whole 128-byte bank rows (32 FP32
+// or 16 FP64 elements).  FP64 at kp = 112 then needs 2 kp ld 8 = 200,704 bytes
+// for X and Q instead of the 229,376 that a 32-element rounding would take
+// (over the 227 KB per-CTA limit together with the static arrays).
+template <typename T>
+__host__ __device__ constexpr int svdj_ld(int rl) {
+    return (rl + (int)(128 / sizeof(T)) - 1) / (int)(128 / sizeof(T)) * (int)(128 / sizeof(T));
+}
+
 #ifdef KH_JACOBI_KERNEL
 // Rotation (c, s) that orthogonalises two columns with squared norms a, b and
 // inner product g (the symmetric 2x2 Schur rotation of [[a, g], [g, b]]).
@@ -237,8 +247,8 @@ __device__ __forceinline__ void jacobi_rotation(double a, double b, double g, do
 // unrolled at compile time.  The matrix is
 // scaled by a power of two so that its largest entry is O(1) (exact), which
 // lets the convergence test use squared cosines g^2 <= tol^2 a b without
-// square roots.  Columns are stored contiguously with a stride that is a
-// multiple of 32 words, zero below row k; the four groups of a warp walk the
+// square roots.  Columns are stored contiguously with a stride of whole
+// 128-byte bank rows (svdj_ld), zero below row k; the four groups of a warp walk the
 // 16-row blocks of their columns in orders shifted by their slot, so that the
 // two 64-byte halves a warp's vector access touches fall in alternate bank
 // halves (two wavefronts, the minimum for 256 bytes) except where the
@@ -255,7 +265,7 @@ svd_jacobi_kernel(const T* __restrict__ Xin, int k, T* __restrict__ s_out, T* __
     constexpr int RL = LP * R;
     constexpr bool kPrefetchQ = sizeof(T) * R <= 48;   // keep the Q column pair in registers too
     const int kp = (k + 1) & ~1;
-    const int ld = (RL + 31) & ~31;            // column stride: whole bank rows
+    const int ld = svdj_ld<T>(RL);             // column stride: whole bank rows
     T* Xc = reinterpret_cast<T*>(smem_raw);   // Xc[c * ld + r]
     T* Qc = Xc + kp * ld;
     __shared__ T s_wmax[32];

@@ -61,6 +61,19 @@ def test_ising_free_energy(g, prec, Kh, Kv, seed, chi):
     assert abs(lnk - ref) < (1e-9 if prec == "fp64" else TOL[prec])
 
 
+@pytest.mark.parametrize("chi", [28, 96])
+def test_fp64_projectors_at_the_jacobi_size_limit(g, chi):
+    """FP64 projector SVD at k = 112, the largest FP64 size the library
+    accepts: the dense path at chi = 28 (n = chi D^2 = 112) and the subspace
+    path at chi = 96 (chi + 16 oversampling = 112), against Onsager."""
+    Kh, Kv = 0.3, 0.2
+    T = exact.ising_peps(Kh, Kv, gauge_seed=7)
+    ctx = g.Context(2, chi, "fp64", p_max=2, n_slots=1, svd_cut=CUT["fp64"])
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 300, 3, 1e-11)
+    assert abs(np.log(ctx.ctm_kappa(0)) - exact.onsager_lnZ(Kh, Kv)) < 1e-9
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_yang_magnetisation(g, prec):
     K = 0.5
