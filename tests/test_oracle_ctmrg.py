@@ -122,3 +122,27 @@ def test_anisotropic_correlations_are_free_energy_derivatives(Kh, Kv):
     assert abs(dh - dv) > 0.05
     assert abs(_bond_correlator(Kh, Kv, "r") - dh) < 1e-9
     assert abs(_bond_correlator(Kh, Kv, "d") - dv) < 1e-9
+
+
+def _directed_ising(Kh, Kv, hh, hv):
+    """Ising PEPS with directed bond weights: the ket bond between a site's
+    leg r (d) and its neighbour's leg l (u) is W(s_i, s_j) with
+    W^2 = exp(K s s' + h (s - s')).  W is not symmetric, so neither are the
+    corners and edges; on the infinite lattice the h terms telescope (each
+    site is the left end of one horizontal bond and the right end of another),
+    so the free energy per site is Onsager's for every h."""
+    s = np.array([1.0, -1.0])
+
+    def W(K, h):
+        return np.exp(0.5 * (K * np.outer(s, s) + h * (s[:, None] - s[None, :])))
+    I = np.eye(2)
+    return np.einsum("sl,su,sr,sd->slurd", W(Kh, hh).T, W(Kv, hv).T, I, I)
+
+
+@pytest.mark.parametrize("hh,hv", [(0.4, 0.0), (0.4, -0.7)])
+def test_onsager_with_reflection_asymmetric_bond_weights(hh, hv):
+    Kh, Kv = 0.3, 0.2
+    T = _directed_ising(Kh, Kv, hh, hv)
+    a, env, info = _run(T, 16)
+    assert info["delta"] < 1e-12
+    assert abs(np.log(ctmrg.kappa(env, a)) - exact.onsager_lnZ(Kh, Kv)) < 1e-10

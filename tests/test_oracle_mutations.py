@@ -3,7 +3,15 @@ oracle (a dropped term, a wrong sign, a transposed leg or operand, a wrong
 time step) with monkeypatch, on the CPU, and checks that the pin meant to
 guard that part now fails.  Each pin is restated here as a function that
 returns its worst deviation in units of its tolerance (< 1 = the pin
-passes); `test_pins_pass_unmutated` checks the restatements themselves."""
+passes); `test_pins_pass_unmutated` checks the restatements themselves.
+
+Transformations that leave every result unchanged are not planted:
+transposing the expectation matrix (X = T N T^T is symmetric for real
+tensors), exchanging ket and bra legs inside the metric (the layers are
+identical), or reversing the two chi legs of the new edge of a move (the
+same projector pair serves both cuts, so this only relabels the fixed
+point; it reproduces Onsager's free energy even with reflection-asymmetric
+bond weights)."""
 import numpy as np
 import pytest
 from scipy.linalg import expm
