@@ -799,7 +799,7 @@ void Engine<T>::observables(const double* Hh, double hA, double hB, int mx, int 
     bind(0);
     Mat4x3 H;
     for (int i = 0; i < 48; ++i) H.v[i] = Hh[i];
-    double* dout = dscr + 4200;
+    double* dout = dscr + DscrOff::kObsOut;
     obs_kernel<<<1, 32, 0, st>>>(Xs, H, hA, hB, dout);
     KH_LAUNCHED();
     double tr[12];

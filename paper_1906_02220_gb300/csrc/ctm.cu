@@ -151,7 +151,7 @@ void Engine<T>::carve_lane(Carver& cv) {
     C1n = cv.take<T>(chi2);
     C4n = cv.take<T>(chi2);
     E4n = cv.take<T>(E1);
-    dscr = cv.take<double>(8192 + kk * kk);
+    dscr = cv.take<double>(DscrOff::kFixed + kk * kk);
     mt1 = cv.take<T>(E1);
     mt2 = cv.take<T>(E1);
     mup = cv.take<T>(n2);
@@ -479,9 +479,10 @@ template <typename T>
 void Engine<T>::init_env(int slot, const double* edge) {
     Slot<T>& sl = slots[slot];
     const int d2 = dm.d2;
-    if (edge) KH_CUDA(cudaMemcpyAsync(dscr, edge, sizeof(double) * d2, cudaMemcpyHostToDevice, st));
+    double* dedge = dscr + DscrOff::kStage;
+    if (edge) KH_CUDA(cudaMemcpyAsync(dedge, edge, sizeof(double) * d2, cudaMemcpyHostToDevice, st));
     long long tot = 4LL * dm.chi * dm.chi + 4LL * dm.chi * d2 * dm.chi;
-    init_env_kernel<<<grid_for(tot), 256, 0, st>>>(sl.C, sl.E, dm.chi, d2, dscr, edge != nullptr, dm.D);
+    init_env_kernel<<<grid_for(tot), 256, 0, st>>>(sl.C, sl.E, dm.chi, d2, dedge, edge != nullptr, dm.D);
     KH_LAUNCHED();
     sl.env_valid = true;
     sl.prev_valid = false;
@@ -626,7 +627,7 @@ template void cholqr2<double>(const double*, int, int, double, double*, double*,
 template <typename T>
 void Engine<T>::orth(const T* Y, int n, int k, T* Uo) {
     prof_begin(8);
-    cholqr2<T>(Y, n, k, cfg.svd_cut, Qt, Xk, dscr + 8192, Uo, st);
+    cholqr2<T>(Y, n, k, cfg.svd_cut, Qt, Xk, dscr + DscrOff::kGram, Uo, st);
     prof_end(8, 0.0);
 }
 
@@ -743,7 +744,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
     const T* Qa = Q[0];
     const T* Qb = Q[1];
     half_system_product(n);
-    double* normM2 = dscr + 8000;
+    double* normM2 = dscr + DscrOff::kNormM2;
     KH_CUDA(cudaMemsetAsync(normM2, 0, sizeof(double), st));
     sumsq_kernel<T><<<sumsq_grid((long long)n * n), 256, 0, st>>>(Mt, (long long)n * n, normM2);
     KH_LAUNCHED();
@@ -819,8 +820,8 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         KH_CUDA(cudaMemcpyAsync(Vw, Z1, sizeof(T) * (size_t)n * k, cudaMemcpyDeviceToDevice, st));
         {
             const int thr = 256 / k > 0 ? 256 / k * k : k;
-            live_mask_kernel<T><<<16, thr, sizeof(float) * thr, st>>>(Z1, n, k, live, (float*)(dscr + 7000),
-                                                                       (int*)(dscr + 7100));
+            live_mask_kernel<T><<<16, thr, sizeof(float) * thr, st>>>(
+                Z1, n, k, live, (float*)(dscr + DscrOff::kLiveAcc), (int*)(dscr + DscrOff::kLiveCount));
         }
         KH_LAUNCHED();
         sl.warm[dir] = true;
@@ -872,7 +873,7 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
     {
         cudaStream_t cs = side ? lanes[1].st : st;
         T* csk = side ? lanes[1].skbuf : skbuf;
-        double* cns = (side ? lanes[1].dscr : dscr) + 8010;
+        double* cns = (side ? lanes[1].dscr : dscr) + DscrOff::kNorms;
         {   // C1n = P^T X1a
             GemmArgs<T> g;
             g.M = chi; g.N = chi; g.K = n; g.batch = 1;
@@ -914,7 +915,7 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
                sl.dl && sl.Wedg_lo ? sl.Wedg_lo + w4 : nullptr, site_presplit(sl));   // [x4][a][uk][rk][ub][rb]
     permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
     gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);   // [a][rk][rb][a_up]
-    double* ns = dscr + 8010;
+    double* ns = dscr + DscrOff::kNorms;
     KH_CUDA(cudaMemsetAsync(ns + 2, 0, sizeof(double), st));
     sumsq_kernel<T><<<sumsq_grid(E1), 256, 0, st>>>(E4n, E1, ns + 2);
     KH_LAUNCHED();
@@ -1129,7 +1130,7 @@ double Engine<T>::kappa(int slot) {
     const int chi = dm.chi, d2 = dm.d2, p = sl.p, D4 = dm.D4;
     const long long chi2 = (long long)chi * chi, E1 = (long long)chi * d2 * chi;
     compute_metric(sl, N);
-    double* z = dscr + 8020;    // Z11, Z00, Z10, Z01
+    double* z = dscr + DscrOff::kKappa;    // Z11, Z00, Z10, Z01
     KH_CUDA(cudaMemsetAsync(z, 0, 4 * sizeof(double), st));
     double* w1 = dwork;
     double* w2 = dwork + E1;
@@ -1178,8 +1179,8 @@ void Engine<T>::expval(int slot, const double* ops, int n_ops, double* vals) {
     double* TN = dwork;
     gemm_rm<double>(p, D4, D4, sl.Ts, false, N, false, TN, st);
     gemm_rm<double>(p, p, D4, TN, false, sl.Ts, true, X, st);
-    double* dops = dscr;
-    double* dvals = dscr + 4096;
+    double* dops = dscr + DscrOff::kStage;
+    double* dvals = dscr + DscrOff::kExpvalOut;
     KH_CUDA(cudaMemcpyAsync(dops, ops, sizeof(double) * n_ops * p * p, cudaMemcpyHostToDevice, st));
     expval_kernel<<<1, 32, 0, st>>>(dops, n_ops, p, X, dvals);
     KH_LAUNCHED();

@@ -111,6 +111,26 @@ struct EngineBase {
 #define KH_LANE_PTRS(X) X(Cop) X(Eop) X(Y1) X(Yp) X(Zk) X(Qt) X(Mt) X(V0) X(Z1) X(U) X(Z2) X(Vo) X(Uf) \
     X(Xk) X(Hk) X(Lk) X(Qk) X(Sk) X(isq) X(P) X(PtT) X(C4E3) X(C1n) \
     X(C4n) X(E4n) X(mt1) X(mt2) X(mup) X(mdn) X(mupp) X(mdnp) X(mN4) X(skbuf)
+// Fixed regions of the small FP64 scratch dscr that every lane owns (offsets
+// in doubles); the Gram matrix of the orthonormalisation (kk^2) comes last.
+struct DscrOff {
+    static constexpr int kStage = 0;         // host->device staging: edge vector (D^2) or <= 16 operators (p^2 each)
+    static constexpr int kExpvalOut = 4096;  // <= 16 expectation values
+    static constexpr int kObsOut = 4200;     // 10 observables
+    static constexpr int kLiveAcc = 7000;    // column norms of the live mask, k <= 160 floats
+    static constexpr int kLiveCount = 7100;  // its last-block counter (int)
+    static constexpr int kNormM2 = 8000;     // ||Mt||^2 of the half-system product
+    static constexpr int kNorms = 8010;      // sums of squares of C1n, C4n, E4n
+    static constexpr int kKappa = 8020;      // Z11, Z00, Z10, Z01 of the free energy
+    static constexpr int kGram = 8192;       // FP64 Gram matrix, kk^2
+    static constexpr int kFixed = kGram;     // doubles before the Gram matrix
+};
+static_assert(DscrOff::kStage + 16 * 16 * 16 <= DscrOff::kExpvalOut && DscrOff::kExpvalOut + 16 <= DscrOff::kObsOut &&
+                  DscrOff::kObsOut + 10 <= DscrOff::kLiveAcc && DscrOff::kLiveAcc + 160 / 2 <= DscrOff::kLiveCount &&
+                  DscrOff::kLiveCount + 1 <= DscrOff::kNormM2 && DscrOff::kNormM2 + 1 <= DscrOff::kNorms &&
+                  DscrOff::kNorms + 3 <= DscrOff::kKappa && DscrOff::kKappa + 4 <= DscrOff::kGram,
+              "dscr regions overlap");
+
 #define KH_LANE_DPTRS(X) X(dscr) X(N) X(dwork)
 template <typename T>
 struct Lane {
@@ -140,7 +160,7 @@ struct Engine : EngineBase {
     T *Xk = nullptr, *Hk = nullptr, *Lk = nullptr, *Qk = nullptr, *Sk = nullptr;
     T *isq = nullptr, *P = nullptr, *PtT = nullptr, *C4E3 = nullptr;
     T *C1n = nullptr, *C4n = nullptr, *E4n = nullptr;
-    double* dscr = nullptr;    // small FP64 scratch (norms etc.)
+    double* dscr = nullptr;    // small FP64 scratch (norms etc.), regions in DscrOff
     // metric / bond scratch (FP64 unless noted)
     T *mt1 = nullptr, *mt2 = nullptr, *mup = nullptr, *mdn = nullptr, *mupp = nullptr, *mdnp = nullptr, *mN4 = nullptr;
     double *N = nullptr, *Tp = nullptr, *A2 = nullptr, *B2 = nullptr, *XA = nullptr, *R = nullptr,
