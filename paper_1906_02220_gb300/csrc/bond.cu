@@ -624,7 +624,7 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     const size_t chol_sm = sizeof(double) * ((size_t)m * (m + 1) + 4 * m);
     const int chol_smem = chol_sm <= 200 * 1024 ? 1 : 0;
     if (chol_smem) {
-        static size_t granted[kMaxDevices] = {};
+        static std::atomic<size_t> granted[kMaxDevices] = {};
         smem_opt_in(chol_solve_kernel, chol_sm, granted);
     }
     const int* done = flags + 1;

@@ -4,6 +4,9 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
+#include <mutex>
 #include <stdio.h>
 #include <string.h>
 #include <string>
@@ -173,19 +176,29 @@ inline PermArgs make_perm(const std::vector<long long>& in_shape, const std::vec
 // opt-in is made when the kernel's static size plus `bytes` exceeds it; once
 // per (kernel, device) and size, cache being the call site's table of the
 // sizes already settled, indexed by device ordinal (the attribute is per
-// device, so a context on a second GPU needs its own opt-in).
+// device, so a context on a second GPU needs its own opt-in).  Contexts may
+// live on several host threads: the settled size is read lock-free, and a
+// raise is made under one lock, so the attribute only ever grows (a smaller
+// request arriving second never lowers a larger grant another thread is
+// about to launch with).
 constexpr int kMaxDevices = 64;
+inline std::mutex& smem_opt_in_mutex() {
+    static std::mutex m;
+    return m;
+}
 template <typename K>
-inline void smem_opt_in(K kernel, size_t bytes, size_t (&cache)[kMaxDevices]) {
+inline void smem_opt_in(K kernel, size_t bytes, std::atomic<size_t> (&cache)[kMaxDevices]) {
     int dev = 0;
     KH_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) fail(KH_EINVAL, "device ordinal beyond 63");
-    if (cache[dev] >= bytes) return;
+    if (cache[dev].load(std::memory_order_acquire) >= bytes) return;
+    std::lock_guard<std::mutex> lock(smem_opt_in_mutex());
+    if (cache[dev].load(std::memory_order_relaxed) >= bytes) return;
     cudaFuncAttributes fa;
     KH_CUDA(cudaFuncGetAttributes(&fa, kernel));
     if (fa.sharedSizeBytes + bytes > 48 * 1024)
         KH_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    cache[dev] = bytes;
+    cache[dev].store(bytes, std::memory_order_release);
 }
 
 inline int grid_for(long long n, int block = 256) {

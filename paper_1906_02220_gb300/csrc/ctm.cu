@@ -1193,7 +1193,7 @@ void jacobi_eig(const T* G, int k, int ldg, long long sG, T* W, int ldw, long lo
                 int batch, int max_sweeps, double tol, int* sweeps, const int* skip, cudaStream_t st) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "jacobi: k beyond limit");
     size_t sm = jacobi_smem<T>(k);
-    static size_t granted[kMaxDevices] = {};   // per T
+    static std::atomic<size_t> granted[kMaxDevices] = {};   // per T
     smem_opt_in(jacobi_eig_kernel<T>, sm, granted);
     jacobi_eig_kernel<T><<<batch, kJacobiThreads, sm, st>>>(G, k, ldg, sG, W, ldw, sW, evals, sE, max_sweeps, tol,
                                                            sweeps, skip);
@@ -1204,7 +1204,7 @@ static void svd_jacobi_launch(const T* X, int k, T* sv, T* L, T* Qm, int max_swe
                               cudaStream_t st, int* sweep_count, int nrel) {
     const int kp = (k + 1) & ~1;
     size_t sm = (size_t)2 * kp * svdj_ld<T>(LP * R) * sizeof(T);
-    static size_t granted[kMaxDevices] = {};   // per instantiation
+    static std::atomic<size_t> granted[kMaxDevices] = {};   // per instantiation
     smem_opt_in(svd_jacobi_kernel<T, LP, R>, sm, granted);
     const int threads = ((kp / 2) * LP + 31) / 32 * 32;
     svd_jacobi_kernel<T, LP, R><<<1, threads, sm, st>>>(X, k, sv, L, Qm, max_sweeps, tol, cut, sweep_count, nrel);
@@ -1238,7 +1238,7 @@ void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cu
                    double ns_tol, double defer) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
     size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
-    static size_t granted[kMaxDevices] = {};
+    static std::atomic<size_t> granted[kMaxDevices] = {};
     smem_opt_in(cholqr_kernel<T>, sm, granted);
     cholqr_kernel<T><<<1, 1024, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0, ns_tol, defer);
     KH_LAUNCHED();

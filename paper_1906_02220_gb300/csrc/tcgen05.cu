@@ -289,7 +289,7 @@ template <int BN, int NPASS>
 static void launch_tc(const TcOperand& A, const TcOperand& B, float* C, int M, int N, int K, long long ldc,
                       float alpha, float beta, const float* colscale, int* err, cudaStream_t st) {
     using G = tc::Cfg<BN, NPASS>;
-    static size_t granted[kMaxDevices] = {};
+    static std::atomic<size_t> granted[kMaxDevices] = {};
     smem_opt_in(tc::gemm_kernel<BN, NPASS>, (size_t)G::SMEM, granted);
     CUtensorMap ma = make_map(A.hi, M, K, A.ld, tc::BM);
     CUtensorMap mb = make_map(B.hi, N, K, B.ld, BN);
