@@ -33,6 +33,10 @@
  *     E1 attaches to u, E2 to r, E3 to d, E4 to l.
  *   - Errors: every call returns a kh_status; nothing aborts or traps.
  *     On failure kh_last_error() gives a one-line reason.
+ *   - Threads: one host thread at a time per context; different contexts
+ *     may be driven from different host threads concurrently (the state
+ *     they share -- per-kernel shared-memory grants, the tensor-map encoder,
+ *     the launch counter -- is synchronised).
  */
 #ifndef EEFU_H
 #define EEFU_H

@@ -6,7 +6,7 @@
 #include "engine.cuh"
 
 namespace kh {
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 }
 
 struct kh_ctx {
@@ -309,7 +309,7 @@ kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA
     });
 }
 
-unsigned long long kh_launch_count(void) { return kh::g_launches; }
+unsigned long long kh_launch_count(void) { return kh::g_launches.load(std::memory_order_relaxed); }
 
 kh_status kh_profile(kh_ctx* ctx, int enable, double* out) {
     return guard(ctx, [&] {

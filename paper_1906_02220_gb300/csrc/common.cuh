@@ -37,9 +37,10 @@ struct Error {
 
 inline void fail(kh_status st, const std::string& m) { throw Error{st, m}; }
 
-// number of kernels this library has launched (read by kh_launch_count)
-extern unsigned long long g_launches;
-inline void count_launch() { ++g_launches; }
+// number of kernels this library has launched (read by kh_launch_count);
+// atomic because contexts may be driven from several host threads
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ workspace
 

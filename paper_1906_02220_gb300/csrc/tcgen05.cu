@@ -256,21 +256,24 @@ __global__ void split_kernel(const float* __restrict__ x, float* __restrict__ hi
 
 // ------------------------------------------------------------------ host side
 
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-static void get_encode() {
-    if (g_encode) return;
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    KH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (!fn || q != cudaDriverEntryPointSuccess) fail(KH_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+// The driver's tensor-map encoder, looked up once (a function-local static:
+// initialised once even when contexts run on several host threads; a failed
+// lookup throws and is retried by the next call).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        KH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+        if (!f || q != cudaDriverEntryPointSuccess) fail(KH_ECUDA, "cuTensorMapEncodeTiled unavailable");
+        return (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }();
+    return fn;
 }
 
 // Row-major FP32 matrix rows x K (leading dimension ld) as a 2-D tensor map
 // with box {32, box_rows} and 128-byte swizzle.
 static CUtensorMap make_map(const float* p, long long rows, long long K, long long ld, int box_rows) {
-    get_encode();
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = encode_fn();
     if (((uintptr_t)p & 15) != 0) fail(KH_EINVAL, "tensor-core operand not 16-byte aligned");
     if ((ld * 4) % 16 != 0) fail(KH_EINVAL, "tensor-core operand leading dimension not a multiple of 4");
     CUtensorMap m;
@@ -278,9 +281,9 @@ static CUtensorMap make_map(const float* p, long long rows, long long K, long lo
     cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
     cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) fail(KH_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return m;
 }

@@ -74,6 +74,42 @@ def test_fp64_projectors_at_the_jacobi_size_limit(g, chi):
     assert abs(np.log(ctx.ctm_kappa(0)) - exact.onsager_lnZ(Kh, Kv)) < 1e-9
 
 
+def test_contexts_on_two_host_threads(g):
+    """Two contexts driven concurrently from two host threads (FP64 at
+    chi = 16 and FP32 at chi = 24: the same kernels with different
+    shared-memory grants) give the free energies each gives alone."""
+    import threading
+    import torch
+    Kh, Kv = 0.3, 0.2
+    T = exact.ising_peps(Kh, Kv, gauge_seed=7)
+    cases = [("fp64", 16), ("fp32", 24)]
+
+    def run(prec, chi, out, i):
+        try:
+            with torch.cuda.stream(torch.cuda.Stream()):
+                ctx = g.Context(2, chi, prec, p_max=2, n_slots=1, svd_cut=CUT[prec])
+                ctx.ctm_set_tensor(0, _t(T))
+                ctx.ctm_sweep(0, 300, 3, 1e-11 if prec == "fp64" else 10 * TOL[prec])
+                out[i] = np.log(ctx.ctm_kappa(0))
+                torch.cuda.current_stream().synchronize()
+        except Exception as e:          # surfaced below
+            out[i] = e
+
+    alone = [None, None]
+    for i, (prec, chi) in enumerate(cases):
+        run(prec, chi, alone, i)
+    both = [None, None]
+    ths = [threading.Thread(target=run, args=(prec, chi, both, i)) for i, (prec, chi) in enumerate(cases)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    for i, (prec, _) in enumerate(cases):
+        assert not isinstance(both[i], Exception), both[i]
+        assert abs(both[i] - alone[i]) < (1e-12 if prec == "fp64" else 1e-6)
+        assert abs(both[i] - exact.onsager_lnZ(Kh, Kv)) < (1e-9 if prec == "fp64" else TOL[prec])
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_yang_magnetisation(g, prec):
     K = 0.5
