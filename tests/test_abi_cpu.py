@@ -55,6 +55,20 @@ def test_workspace_sizing(g):
         assert g.lib().kh_workspace_bytes(ctypes.byref(c)) == 0
 
 
+@pytest.mark.parametrize("D,chi,prec,ok", [(4, 96, "fp64", True), (4, 97, "fp64", False),
+                                            (4, 144, "fp32", True), (4, 145, "tf32x3", False),
+                                            (2, 28, "fp64", True), (3, 12, "fp64", True)])
+def test_workspace_sizing_at_the_jacobi_limits(g, D, chi, prec, ok):
+    """The projector's one-CTA Jacobi takes k = chi + 16 up to 112 (FP64) or
+    160 (FP32 family); below n = chi D^2 <= k the dense path takes k = n.
+    Larger configurations are rejected (0 bytes), the limits themselves are
+    accepted."""
+    import ctypes
+    c = g.default_config(D, chi, prec)
+    b = g.lib().kh_workspace_bytes(ctypes.byref(c))
+    assert (b > 0) == ok
+
+
 @pytest.mark.parametrize("gamma", ["x", "y", "z"])
 def test_host_gates_match_oracle(g, gamma):
     from oracle import model
