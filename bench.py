@@ -197,18 +197,24 @@ def roofline_entry(cat, c, bound, prec, pk, pk_src):
 
 
 def roofline_for(prec, prof, pk, pk_src):
-    """Roofline of the dominant timed kernel category that has an algorithmic
-    flop model (the latency-bound projector SVD kernels have none), plus the
-    half-system product's own tensor-core entry.  At D = 4 the site
-    contraction is the double-layer GEMM, on tensor cores in the TF32 modes."""
+    """`roofline`: the timed kernel category with an algorithmic flop model
+    that takes the most time -- on the bench workload the CholQR2
+    orthonormalisation of the projector subspace (Gram matrices, one-CTA
+    Cholesky factor and inverse, basis products; latency-bound, reported
+    against the CUDA-core peak).  `roofline_tensor_core`: the tcgen05
+    category that takes the most time (the double-layer site contraction or
+    the half-system product; None when no tensor-core mode is in use)."""
     tc = prec in ("tf32", "tf32x3", "bf16")
     bounds = {"half_system_product": "tensor" if tc else "alu", "site_layer": "tensor" if tc else "alu",
-              "subspace_gemm": "alu"}
-    kernels = {k: v for k, v in prof.items() if k in bounds and v["flops"] > 0}
+              "subspace_gemm": "alu", "cholqr_orth": "alu"}
+    kernels = {k: v for k, v in prof.items() if k in bounds and v["flops"] > 0 and v["launches"] > 0}
     cat = max(kernels, key=lambda k: kernels[k]["ms"])
     main = roofline_entry(cat, kernels[cat], bounds[cat], prec, pk, pk_src)
-    tc_entry = roofline_entry("half_system_product", prof["half_system_product"], bounds["half_system_product"],
-                              prec, pk, pk_src)
+    tc_entry = None
+    tc_cats = [k for k in ("site_layer", "half_system_product") if k in kernels] if tc else []
+    if tc_cats:
+        tcat = max(tc_cats, key=lambda k: kernels[k]["ms"])
+        tc_entry = roofline_entry(tcat, kernels[tcat], "tensor", prec, pk, pk_src)
     return main, tc_entry
 
 

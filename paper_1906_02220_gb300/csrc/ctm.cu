@@ -624,11 +624,20 @@ void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T*
 template void cholqr2<float>(const float*, int, int, double, float*, float*, double*, float*, cudaStream_t);
 template void cholqr2<double>(const double*, int, int, double, double*, double*, double*, double*, cudaStream_t);
 
+// Algorithmic flops of one CholQR2 of an n x k block: two symmetric Gram
+// matrices (n k (k+1) each), one Cholesky factor and triangular inverse
+// (k^3/3 each; the second pass is a Newton-Schulz step, O(k^2)), Q1 = Y X1
+// with triangular X1 (n k^2) and Q = Q1 X2 with dense X2 (2 n k^2).
+static double cholqr2_flops(int n, int k) {
+    const double N = n, K = k;
+    return 5.0 * N * K * K + 2.0 * N * K + 2.0 * K * K * K / 3.0;
+}
+
 template <typename T>
 void Engine<T>::orth(const T* Y, int n, int k, T* Uo) {
     prof_begin(8);
     cholqr2<T>(Y, n, k, cfg.svd_cut, Qt, Xk, dscr + DscrOff::kGram, Uo, st);
-    prof_end(8, 0.0);
+    prof_end(8, cholqr2_flops(n, k));
 }
 
 // Half-system product Mt = Q_{s+3} Q_s (= M^T), the largest single GEMM of a

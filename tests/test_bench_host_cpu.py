@@ -53,9 +53,31 @@ def test_roofline_reports_the_longest_category_with_a_flop_model():
             "projector_svd": {"launches": 50, "ms": 9.0, "flops": 0.0}}      # no flop model: never chosen
     main, tc = bench.roofline_for("tf32x3", prof, PK, "measured")
     assert main["kernel"] == "site_layer" and main["bound"] == "tensor"
-    assert tc["kernel"] == "half_system_product"
-    main32, _ = bench.roofline_for("fp32", prof, PK, "measured")
-    assert main32["bound"] == "alu"
+    assert tc["kernel"] == "site_layer"
+    main32, tc32 = bench.roofline_for("fp32", prof, PK, "measured")
+    assert main32["bound"] == "alu" and tc32 is None
+
+
+def test_roofline_on_the_measured_bench_profile():
+    """Category times of a default bench run on one GB300 (5 timed steps);
+    flops of the CholQR2 category from its model 5 n k^2 + 2 n k + 2 k^3 / 3
+    at n = 1024, k = 80 per call."""
+    n, k, calls = 1024, 80, 1040
+    prof = {"projector_svd": {"launches": 520, "ms": 275.996, "flops": 0.0},
+            "cholqr_orth": {"launches": calls, "ms": 108.986,
+                            "flops": calls * (5.0 * n * k * k + 2.0 * n * k + 2.0 * k ** 3 / 3.0)},
+            "absorb": {"launches": 520, "ms": 51.933, "flops": 0.0},
+            "corners": {"launches": 520, "ms": 45.647, "flops": 0.0},
+            "als_gauge": {"launches": 25, "ms": 41.958, "flops": 0.0},
+            "svd_jacobi": {"launches": 520, "ms": 41.714, "flops": 1029.0},
+            "site_layer": {"launches": 1560, "ms": 31.019, "flops": 837518622720.0},
+            "subspace_gemm": {"launches": 1040, "ms": 24.917, "flops": 174483046400.0},
+            "half_system_product": {"launches": 520, "ms": 15.782, "flops": 1116691496960.0},
+            "metric": {"launches": 40, "ms": 5.183, "flops": 0.0}}
+    main, tc = bench.roofline_for("tf32x3", prof, PK, "measured")
+    assert main["kernel"] == "cholqr_orth" and main["bound"] == "alu" and main["traffic"] is None
+    assert 0.3 < main["achieved"] < 0.34 and main["frac"] < 0.005          # ~0.32 TFLOP/s: latency-bound
+    assert tc["kernel"] == "site_layer" and abs(tc["achieved"] - 27.0) < 0.1
 
 
 class _Done:
