@@ -130,7 +130,8 @@ kh_status ctm_build_composite(kh_ctx* ctx, int slot, int gamma, const double* ho
  * NULL).  Also marks the projector subspaces cold. */
 kh_status ctm_init(kh_ctx* ctx, int slot, const double* host_edge);
 
-/* Copy the environment (and warm subspaces) of src_slot into dst_slot. */
+/* Copy the environment (and warm subspaces with their live-column masks) of
+ * src_slot into dst_slot. */
 kh_status ctm_copy_env(kh_ctx* ctx, int dst_slot, int src_slot);
 
 /* CTM sweeps (left, up, right, down moves) on slot.  Runs until the

@@ -498,6 +498,9 @@ void Engine<T>::copy_env(int dst, int src) {
     KH_CUDA(cudaMemcpyAsync(a.C, b.C, sizeof(double) * 4 * chi2, cudaMemcpyDeviceToDevice, st));
     KH_CUDA(cudaMemcpyAsync(a.E, b.E, sizeof(double) * 4 * E1, cudaMemcpyDeviceToDevice, st));
     KH_CUDA(cudaMemcpyAsync(a.Vw, b.Vw, sizeof(T) * 4LL * dm.n * dm.kk, cudaMemcpyDeviceToDevice, st));
+    // the live-column masks belong to the warm subspaces: without them the
+    // first warm move would refill columns by the destination's old mask
+    KH_CUDA(cudaMemcpyAsync(a.live, b.live, sizeof(int) * 4LL * dm.kk, cudaMemcpyDeviceToDevice, st));
     a.env_valid = b.env_valid;
     a.prev_valid = false;
     for (int q = 0; q < 4; ++q) a.warm[q] = b.warm[q];
