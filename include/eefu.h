@@ -114,6 +114,29 @@ const char* kh_last_error(const kh_ctx* ctx);
 kh_status kh_set_state(kh_ctx* ctx, const double* dev_A, const double* dev_B);
 kh_status kh_get_state(kh_ctx* ctx, double* dev_A, double* dev_B);
 
+/* --- checkpoint / resume (the paper has no counterpart) ------------------- */
+
+/* kh_save writes the context's persistent state to the file at path: the
+ * configuration, the site tensors A, B, and for every slot its FP64 master
+ * site tensor, environment (C, E), warm projector subspaces with their
+ * live-column masks, last spectra, discarded weights and flags, plus the
+ * random-stream counter.  Scratch is not saved; the operands derived from a
+ * slot's site tensor are rebuilt on load.  The file is binary in native
+ * byte order (read back on the same kind of machine).  Synchronises the
+ * context's stream.  Errors: KH_EINVAL (null path, the file cannot be
+ * written), KH_ECUDA.
+ * kh_load_config reads a checkpoint's configuration (host only, no GPU),
+ * so that the caller can allocate kh_workspace_bytes(cfg) bytes of
+ * workspace.  KH_EINVAL if the file is missing or not a checkpoint.
+ * kh_load creates a context from a checkpoint on the given workspace and
+ * stream (as kh_create with the file's configuration) and restores its
+ * state: continuing from it computes what the saved context would have.
+ * On a failure after the context was created (a truncated file) *ctx is
+ * still returned and must be destroyed; kh_last_error(*ctx) says why. */
+kh_status kh_save(kh_ctx* ctx, const char* path);
+kh_status kh_load_config(const char* path, kh_config* cfg);
+kh_status kh_load(kh_ctx** ctx, const char* path, void* dev_workspace, size_t workspace_bytes, void* stream);
+
 /* --- CTMRG (Fig. 4(c), Sec. III) ------------------------------------------ */
 
 /* Load an arbitrary site tensor T[p][D][D][D][D] (FP64, device) into slot;

@@ -27,7 +27,8 @@ ABI_FUNCTIONS = [
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
     "eefu_trotter_step", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
-    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_orth", "kh_selftest_fp64_newton", "kh_gemm_noalloc", "kh_gemm_noalloc_max_bytes",
+    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_orth", "kh_selftest_fp64_newton", "kh_gemm_noalloc",
+    "kh_gemm_noalloc_max_bytes", "kh_save", "kh_load_config", "kh_load",
 ]
 
 
@@ -89,6 +90,9 @@ def load_library(path=LIB_PATH):
         "kh_selftest_fp64_newton": (I, [I, P, P, P]),
         "kh_gemm_noalloc": (I, [I, I, I, I, P, P, P, P]),
         "kh_gemm_noalloc_max_bytes": (S, []),
+        "kh_save": (I, [P, ctypes.c_char_p]),
+        "kh_load_config": (I, [ctypes.c_char_p, cfgp]),
+        "kh_load": (I, [ctypes.POINTER(P), ctypes.c_char_p, P, S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -262,17 +266,50 @@ class Context:
         self.D, self.chi = D, chi
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        nbytes = lib().kh_workspace_bytes(ctypes.byref(self.cfg))
-        if nbytes == 0:
-            raise KhError(KH_EINVAL, "invalid configuration")
-        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
-        base = self.workspace.data_ptr()
-        aligned = (base + 255) // 256 * 256
+        aligned, nbytes = self._workspace()
         self._ctx = ctypes.c_void_p()
         st = lib().kh_create(ctypes.byref(self._ctx), ctypes.byref(self.cfg), ctypes.c_void_p(aligned),
                              nbytes, ctypes.c_void_p(self.stream.cuda_stream))
         if st != KH_OK:
             raise KhError(st, "kh_create failed")
+
+    def _workspace(self):
+        """Allocate the caller-owned device workspace for self.cfg (256-byte
+        aligned); returns its aligned address and size."""
+        nbytes = lib().kh_workspace_bytes(ctypes.byref(self.cfg))
+        if nbytes == 0:
+            raise KhError(KH_EINVAL, "invalid configuration")
+        self.workspace = self.torch.empty(nbytes + 256, dtype=self.torch.uint8, device=self.device)
+        return (self.workspace.data_ptr() + 255) // 256 * 256, nbytes
+
+    @classmethod
+    def load(cls, path, device="cuda:0", stream=None):
+        """A context restored from a checkpoint written by save(): same
+        configuration, state, environments and warm subspaces."""
+        import torch
+        cfg = KhConfig()
+        st = lib().kh_load_config(os.fsencode(path), ctypes.byref(cfg))
+        if st != KH_OK:
+            raise KhError(st, "not a readable checkpoint: %s" % path)
+        self = cls.__new__(cls)
+        self.torch = torch
+        self.cfg = cfg
+        self.D, self.chi = cfg.D, cfg.chi
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        aligned, nbytes = self._workspace()
+        self._ctx = ctypes.c_void_p()
+        st = lib().kh_load(ctypes.byref(self._ctx), os.fsencode(path), ctypes.c_void_p(aligned), nbytes,
+                           ctypes.c_void_p(self.stream.cuda_stream))
+        if st != KH_OK:
+            msg = lib().kh_last_error(self._ctx).decode() if self._ctx.value else "kh_load failed"
+            self.close()
+            raise KhError(st, msg)
+        return self
+
+    def save(self, path):
+        """Write the context's persistent state to a checkpoint file."""
+        self._check(lib().kh_save(self._ctx, os.fsencode(path)))
 
     def _check(self, st):
         if st != KH_OK:

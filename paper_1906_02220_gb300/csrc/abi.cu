@@ -161,6 +161,71 @@ const char* kh_last_error(const kh_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 const char* kh_version(void) { return "eefu-gb300 0.1 (sm_103a)"; }
 
+// ------------------------------------------------------------------ checkpoint / resume
+
+namespace {
+
+const char kCheckpointMagic[8] = {'K', 'H', 'C', 'K', 'P', 'T', '0', '1'};
+
+struct FileCloser {
+    std::FILE* f;
+    ~FileCloser() {
+        if (f) std::fclose(f);
+    }
+};
+
+// Opens a checkpoint and reads its header (magic, configuration); the file
+// is left positioned at the engine payload.
+kh_status read_checkpoint_header(const char* path, std::FILE** out, kh_config* cfg) {
+    *out = nullptr;
+    if (!path || !cfg) return KH_EINVAL;
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) return KH_EINVAL;
+    char magic[8];
+    if (std::fread(magic, 1, 8, f) != 8 || memcmp(magic, kCheckpointMagic, 8) != 0 ||
+        std::fread(cfg, 1, sizeof(kh_config), f) != sizeof(kh_config)) {
+        std::fclose(f);
+        return KH_EINVAL;
+    }
+    *out = f;
+    return KH_OK;
+}
+
+}  // namespace
+
+kh_status kh_save(kh_ctx* ctx, const char* path) {
+    return guard(ctx, [&] {
+        if (!path) kh::fail(KH_EINVAL, "null path");
+        FileCloser fc{std::fopen(path, "wb")};
+        if (!fc.f) kh::fail(KH_EINVAL, std::string("cannot open ") + path + " for writing");
+        if (std::fwrite(kCheckpointMagic, 1, 8, fc.f) != 8 ||
+            std::fwrite(&ctx->eng->cfg, 1, sizeof(kh_config), fc.f) != sizeof(kh_config))
+            kh::fail(KH_EINVAL, "checkpoint: write failed");
+        ctx->eng->save_checkpoint(fc.f);
+        if (std::fflush(fc.f) != 0) kh::fail(KH_EINVAL, "checkpoint: write failed");
+    });
+}
+
+kh_status kh_load_config(const char* path, kh_config* cfg) {
+    std::FILE* f = nullptr;
+    kh_status st = read_checkpoint_header(path, &f, cfg);
+    if (f) std::fclose(f);
+    return st;
+}
+
+kh_status kh_load(kh_ctx** out, const char* path, void* ws, size_t bytes, void* stream) {
+    if (!out) return KH_EINVAL;
+    *out = nullptr;
+    kh_config cfg;
+    std::FILE* f = nullptr;
+    kh_status st = read_checkpoint_header(path, &f, &cfg);
+    if (st != KH_OK) return st;
+    FileCloser fc{f};
+    st = kh_create(out, &cfg, ws, bytes, stream);
+    if (st != KH_OK) return st;
+    return guard(*out, [&] { (*out)->eng->load_checkpoint(fc.f); });
+}
+
 kh_status kh_set_state(kh_ctx* ctx, const double* A, const double* B) {
     return guard(ctx, [&] {
         if (!A || !B) kh::fail(KH_EINVAL, "null tensor");

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cstdio>
 #include <mutex>
 #include <stdio.h>
 #include <string.h>

@@ -102,6 +102,9 @@ struct EngineBase {
     virtual void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) = 0;
     virtual void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                              double* out) = 0;
+    // persistent state to / from an open checkpoint file (checkpoint.cu)
+    virtual void save_checkpoint(std::FILE* f) = 0;
+    virtual void load_checkpoint(std::FILE* f) = 0;
 };
 
 // Per-lane scratch of the CTM moves and the metric.  Lane 0 serves every
@@ -245,6 +248,8 @@ struct Engine : EngineBase {
     void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) override;
     void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                      double* out) override;
+    void save_checkpoint(std::FILE* f) override;
+    void load_checkpoint(std::FILE* f) override;
 };
 
 // Tensor-core GEMM (tcgen05.cu): C = alpha colscale (A B^T) + beta C with A

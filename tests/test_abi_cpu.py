@@ -85,3 +85,25 @@ def test_status_codes_on_bad_arguments_without_gpu(g):
     import ctypes
     assert g.lib().kh_bond_hamiltonian(5, 0.0, 0.0, 0.0, 0.0, None) == g.KH_EINVAL
     assert g.lib().kh_create(None, None, None, 0, None) == g.KH_EINVAL
+
+
+def test_checkpoint_header_without_gpu(g, tmp_path):
+    """kh_load_config is host-only: a missing file, a foreign file and a
+    truncated header are rejected; a header (magic + configuration) is read
+    back field by field.  kh_save / kh_load reject null arguments before any
+    GPU work."""
+    import ctypes
+    cfg = g.KhConfig()
+    assert g.lib().kh_load_config(str(tmp_path / "missing").encode(), ctypes.byref(cfg)) == g.KH_EINVAL
+    (tmp_path / "foreign").write_bytes(b"NOTACKPT" + b"\0" * 256)
+    assert g.lib().kh_load_config(str(tmp_path / "foreign").encode(), ctypes.byref(cfg)) == g.KH_EINVAL
+    (tmp_path / "short").write_bytes(b"KHCKPT01" + b"\0" * 8)
+    assert g.lib().kh_load_config(str(tmp_path / "short").encode(), ctypes.byref(cfg)) == g.KH_EINVAL
+    c0 = g.default_config(3, 20, "tf32x3", n_slots=6, seed=77)
+    (tmp_path / "header").write_bytes(b"KHCKPT01" + bytes(c0))
+    assert g.lib().kh_load_config(str(tmp_path / "header").encode(), ctypes.byref(cfg)) == g.KH_OK
+    assert bytes(cfg) == bytes(c0)
+    assert g.lib().kh_save(None, b"x") == g.KH_EINVAL
+    ctx = ctypes.c_void_p()
+    assert g.lib().kh_load(ctypes.byref(ctx), str(tmp_path / "missing").encode(), None, 0, None) == g.KH_EINVAL
+    assert ctx.value is None

@@ -1,8 +1,9 @@
 """The allocation-free GEMM entry point (kh_gemm_noalloc) against the
 scratch-taking one (kh_selftest_gemm): same output within the tolerance the
 kernel tests use, on two calls in a row (the static scratch keeps the last
-call's contents, so the second call must not depend on it).  Collected last
-on purpose; it passes alone in a fresh process or after the other tests."""
+call's contents, so the second call must not depend on it).  Collected
+after the kernel and parity tests on purpose; it passes alone in a fresh
+process or after the other tests."""
 import ctypes
 
 import numpy as np
