@@ -219,7 +219,7 @@ __global__ void init_state_kernel(double* A, double* B, int D) {
 
 template <typename T>
 Engine<T>::Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s) {
-    cfg = c;
+    memcpy(&cfg, &c, sizeof(kh_config));   // byte copy: a checkpoint holds the caller's exact configuration
     st = s;
     lanes[0].st = s;
     dm = make_dims(c, sizeof(T) == 8);
