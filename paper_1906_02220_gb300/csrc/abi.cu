@@ -16,6 +16,14 @@ struct kh_ctx {
 
 namespace {
 
+// NVTX range over one ABI call, named after it (tracing; a no-op unless a
+// tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+#define KH_RANGE() NvtxRange kh_nvtx_range_(__func__)
+
 template <typename F>
 kh_status guard(kh_ctx* ctx, F&& f) {
     if (!ctx || !ctx->eng) return KH_EINVAL;
@@ -129,6 +137,7 @@ size_t kh_workspace_bytes(const kh_config* c) {
 }
 
 kh_status kh_create(kh_ctx** out, const kh_config* c, void* ws, size_t bytes, void* stream) {
+    KH_RANGE();
     if (!out || !c) return KH_EINVAL;
     *out = nullptr;
     kh_ctx* ctx = new kh_ctx();
@@ -194,6 +203,7 @@ kh_status read_checkpoint_header(const char* path, std::FILE** out, kh_config* c
 }  // namespace
 
 kh_status kh_save(kh_ctx* ctx, const char* path) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!path) kh::fail(KH_EINVAL, "null path");
         FileCloser fc{std::fopen(path, "wb")};
@@ -207,6 +217,7 @@ kh_status kh_save(kh_ctx* ctx, const char* path) {
 }
 
 kh_status kh_load_config(const char* path, kh_config* cfg) {
+    KH_RANGE();
     std::FILE* f = nullptr;
     kh_status st = read_checkpoint_header(path, &f, cfg);
     if (f) std::fclose(f);
@@ -214,6 +225,7 @@ kh_status kh_load_config(const char* path, kh_config* cfg) {
 }
 
 kh_status kh_load(kh_ctx** out, const char* path, void* ws, size_t bytes, void* stream) {
+    KH_RANGE();
     if (!out) return KH_EINVAL;
     *out = nullptr;
     kh_config cfg;
@@ -227,6 +239,7 @@ kh_status kh_load(kh_ctx** out, const char* path, void* ws, size_t bytes, void* 
 }
 
 kh_status kh_set_state(kh_ctx* ctx, const double* A, const double* B) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!A || !B) kh::fail(KH_EINVAL, "null tensor");
         ctx->eng->set_state(A, B);
@@ -234,6 +247,7 @@ kh_status kh_set_state(kh_ctx* ctx, const double* A, const double* B) {
 }
 
 kh_status kh_get_state(kh_ctx* ctx, double* A, double* B) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!A || !B) kh::fail(KH_EINVAL, "null tensor");
         ctx->eng->get_state(A, B);
@@ -241,6 +255,7 @@ kh_status kh_get_state(kh_ctx* ctx, double* A, double* B) {
 }
 
 kh_status ctm_set_tensor(kh_ctx* ctx, int slot, const double* T, int p) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot) || !T) kh::fail(KH_EINVAL, "bad slot or tensor");
         ctx->eng->set_tensor(slot, T, p);
@@ -248,6 +263,7 @@ kh_status ctm_set_tensor(kh_ctx* ctx, int slot, const double* T, int p) {
 }
 
 kh_status ctm_build_composite(kh_ctx* ctx, int slot, int gamma, const double* gate) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot)) kh::fail(KH_EINVAL, "bad slot");
         ctx->eng->build_composite(slot, gamma, gate);
@@ -255,6 +271,7 @@ kh_status ctm_build_composite(kh_ctx* ctx, int slot, int gamma, const double* ga
 }
 
 kh_status ctm_init(kh_ctx* ctx, int slot, const double* edge) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot)) kh::fail(KH_EINVAL, "bad slot");
         ctx->eng->init_env(slot, edge);
@@ -262,6 +279,7 @@ kh_status ctm_init(kh_ctx* ctx, int slot, const double* edge) {
 }
 
 kh_status ctm_copy_env(kh_ctx* ctx, int dst, int src) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, dst) || !slot_ok(ctx, src)) kh::fail(KH_EINVAL, "bad slot");
         ctx->eng->copy_env(dst, src);
@@ -270,6 +288,7 @@ kh_status ctm_copy_env(kh_ctx* ctx, int dst, int src) {
 
 kh_status ctm_sweep(kh_ctx* ctx, int slot, int max_sweeps, int min_sweeps, double tol, int* done,
                     double* delta) {
+    KH_RANGE();
     kh_status s = KH_OK;
     int n = 0;
     double dl = 0.0;
@@ -288,6 +307,7 @@ kh_status ctm_sweep(kh_ctx* ctx, int slot, int max_sweeps, int min_sweeps, doubl
 }
 
 kh_status ctm_projectors(kh_ctx* ctx, int slot, int dir, double* spec, double* trunc) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot) || dir < 0 || dir > 3) kh::fail(KH_EINVAL, "bad slot or dir");
         ctx->eng->projectors_out(slot, dir, spec, trunc);
@@ -295,6 +315,7 @@ kh_status ctm_projectors(kh_ctx* ctx, int slot, int dir, double* spec, double* t
 }
 
 kh_status ctm_get_env(kh_ctx* ctx, int slot, double* C, double* E) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot)) kh::fail(KH_EINVAL, "bad slot");
         ctx->eng->get_env(slot, C, E);
@@ -302,6 +323,7 @@ kh_status ctm_get_env(kh_ctx* ctx, int slot, double* C, double* E) {
 }
 
 kh_status ctm_metric(kh_ctx* ctx, int slot, double* N) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot) || !N) kh::fail(KH_EINVAL, "bad slot");
         ctx->eng->metric(slot, N);
@@ -309,6 +331,7 @@ kh_status ctm_metric(kh_ctx* ctx, int slot, double* N) {
 }
 
 kh_status ctm_kappa(kh_ctx* ctx, int slot, double* kappa) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot) || !kappa) kh::fail(KH_EINVAL, "bad slot");
         *kappa = ctx->eng->kappa(slot);
@@ -316,6 +339,7 @@ kh_status ctm_kappa(kh_ctx* ctx, int slot, double* kappa) {
 }
 
 kh_status ctm_expval(kh_ctx* ctx, int slot, const double* ops, int n_ops, double* vals) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!slot_ok(ctx, slot) || !ops || !vals) kh::fail(KH_EINVAL, "bad arguments");
         ctx->eng->expval(slot, ops, n_ops, vals);
@@ -324,6 +348,7 @@ kh_status ctm_expval(kh_ctx* ctx, int slot, const double* ops, int n_ops, double
 
 kh_status eefu_apply_gate(kh_ctx* ctx, int gamma, const double* gate, int mx, int mn, double tol,
                           double* info) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!gate || mx < 1) kh::fail(KH_EINVAL, "bad gate or sweep count");
         ctx->eng->apply_gate(gamma, gate, mx, mn, tol, info);
@@ -332,6 +357,7 @@ kh_status eefu_apply_gate(kh_ctx* ctx, int gamma, const double* gate, int mx, in
 
 kh_status observables(kh_ctx* ctx, const double* H, double hA, double hB, int mx, int mn, double tol,
                       double* out) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!H || !out || mx < 1) kh::fail(KH_EINVAL, "bad arguments");
         ctx->eng->observables(H, hA, hB, mx, mn, tol, out);
@@ -339,12 +365,14 @@ kh_status observables(kh_ctx* ctx, const double* H, double hA, double hB, int mx
 }
 
 kh_status kh_bond_hamiltonian(int gamma, double J, double Kg, double hA, double hB, double* H) {
+    KH_RANGE();
     if (gamma < 0 || gamma > 2 || !H) return KH_EINVAL;
     bond_h(gamma, J, Kg, hA, hB, H);
     return KH_OK;
 }
 
 kh_status kh_gate(const double* H, double tau, double* g) {
+    KH_RANGE();
     if (!H || !g) return KH_EINVAL;
     gate_from_h(H, tau, g);
     return KH_OK;
@@ -352,6 +380,7 @@ kh_status kh_gate(const double* H, double tau, double* g) {
 
 kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta,
                             int mx, int mn, double tol, double* info) {
+    KH_RANGE();
     return guard(ctx, [&] {
         if (!Kxyz || mx < 1) kh::fail(KH_EINVAL, "bad arguments");
         static const int order[5] = {0, 1, 2, 1, 0};
@@ -377,6 +406,7 @@ kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA
 unsigned long long kh_launch_count(void) { return kh::g_launches.load(std::memory_order_relaxed); }
 
 kh_status kh_profile(kh_ctx* ctx, int enable, double* out) {
+    KH_RANGE();
     return guard(ctx, [&] {
         kh::EngineBase* e = ctx->eng;
         if (enable) {

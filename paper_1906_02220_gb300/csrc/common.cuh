@@ -3,6 +3,7 @@
 // strided batched GEMM on CUDA cores, reductions, casts).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <atomic>

@@ -43,11 +43,15 @@ struct Dims {
 
 // ------------------------------------------------------------------ engine
 
-// CUDA-event timing of kernel categories (bench instrumentation only):
+// Kernel categories: an NVTX range each (always; a no-op unless a tracing
+// tool is attached) and CUDA-event timing (bench instrumentation, when on):
 // 0 = half-system product Mt = Q_{s+3} Q_s, 1 = two-layer site contractions,
 // 2 = enlarged corners (all), 3 = projector SVD (excluding Mt),
 // 4 = absorption, 5 = environment metric, 6 = ALS + gauge,
 // 7 = one-sided Jacobi SVD, 8 = CholQR orthonormalisation, 9 = subspace GEMMs.
+constexpr const char* kProfNames[10] = {"half_system_product", "site_layer", "corners", "projector_svd",
+                                        "absorb", "metric", "als_gauge", "svd_jacobi", "cholqr_orth",
+                                        "subspace_gemm"};
 struct ProfCat {
     std::vector<cudaEvent_t> a, b;
     int used = 0;
@@ -63,6 +67,7 @@ struct EngineBase {
     static constexpr int kProfCats = 10;
     ProfCat prof[kProfCats];
     void prof_begin(int cat) {
+        nvtxRangePushA(kProfNames[cat]);
         if (!prof_on) return;
         ProfCat& c = prof[cat];
         if (c.used == (int)c.a.size()) {
@@ -75,6 +80,7 @@ struct EngineBase {
         KH_CUDA(cudaEventRecord(c.a[c.used], st));
     }
     void prof_end(int cat, double flops) {
+        nvtxRangePop();
         if (!prof_on) return;
         ProfCat& c = prof[cat];
         KH_CUDA(cudaEventRecord(c.b[c.used], st));
