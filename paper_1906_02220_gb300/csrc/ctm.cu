@@ -315,9 +315,14 @@ void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
     KH_LAUNCHED();
 }
 
+// max that keeps a NaN once it has seen one (fmax drops NaN operands): a
+// non-finite environment must reach the host's spectrum check
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
+
 // spectrum (first chi values, zero-padded), S^-1/2 with cut-off, discarded
 // weight.  One block; every element handled by its own thread (a serial loop
-// here would pay a global-memory round trip per value).
+// here would pay a global-memory round trip per value).  A NaN singular value
+// is passed on to the spectrum and the discarded weight (not clamped to 0).
 template <typename T>
 __global__ void finalize_spectrum_kernel(const T* sv, int k, int chi, double cut, const double* normM2,
                                          double* spec, T* isq, double* trunc) {
@@ -326,10 +331,11 @@ __global__ void finalize_spectrum_kernel(const T* sv, int k, int chi, double cut
     const double s0 = fmax((double)sv[0], 0.0);
     double kept = 0.0;
     for (int j = threadIdx.x; j < chi; j += blockDim.x) {
-        double s = (j < nkeep) ? fmax((double)sv[j], 0.0) : 0.0;
+        const double raw = (j < nkeep) ? (double)sv[j] : 0.0;
+        const double s = raw != raw ? raw : fmax(raw, 0.0);
         kept += s * s;
         bool keep = (s0 > 0.0) && (s > cut * s0);
-        spec[j] = keep ? s : 0.0;
+        spec[j] = s != s ? s : (keep ? s : 0.0);
         isq[j] = keep ? (T)rsqrt(s) : T(0);
     }
     for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
@@ -339,8 +345,8 @@ __global__ void finalize_spectrum_kernel(const T* sv, int k, int chi, double cut
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         double tot = *normM2;
-        double tr = (tot > 0.0) ? (tot - t) / tot : 0.0;
-        *trunc = tr > 0.0 ? tr : 0.0;
+        double tr = (tot > 0.0) ? (tot - t) / tot : (tot != tot ? tot : 0.0);
+        *trunc = tr != tr ? tr : (tr > 0.0 ? tr : 0.0);
     }
 }
 
@@ -372,16 +378,16 @@ __global__ void delta_kernel(const double* spec, double* prev, int chi, int prev
     double d = 0.0;
     for (int e = t; e < 4 * chi; e += blockDim.x) {
         double v = spec[e] * inv[e / chi];
-        d = fmax(d, fabs(v - prev[e]));
+        d = nan_max(d, fabs(v - prev[e]));
         prev[e] = v;
     }
-    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    for (int o = 16; o > 0; o >>= 1) d = nan_max(d, __shfl_xor_sync(0xffffffffu, d, o));
     if (lane == 0) red[w] = d;
     __syncthreads();
     if (t == 0) {
         double m = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
-        *delta = prev_valid ? m : INFINITY;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = nan_max(m, red[i]);
+        *delta = m != m ? m : (prev_valid ? m : INFINITY);   // NaN is reported even on a first sweep
     }
 }
 
