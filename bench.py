@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 
 import kh_inputs  # noqa: E402
 
-METRIC = "CTM sweeps/s and eeFU Trotter steps/s at (D,chi); TC TFLOP/s vs peak; err vs FP64"
+METRIC = "CTM sweeps/s and eeFU Trotter steps/s at (D,χ); TC TFLOP/s vs peak; err vs FP64"
 WORKLOAD = "kitaev_D4_chi64"
 
 
