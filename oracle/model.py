@@ -25,7 +25,11 @@ def couplings(phi, A=1.0):
 def dual_angle(phi):
     """Klein duality tan(phi~) = -tan(phi) - 1 (Sec. II, Eq. 4); returns phi~
     on the branch of the opposite half of the phase diagram (cos phi~ < 0 when
-    cos phi > 0, as in the paper's pairs -63 <-> -136.09 deg)."""
+    cos phi > 0, as in the paper's pairs -63 <-> -136.09 deg).  At the Kitaev
+    points cos(phi) = 0 (J = 0, so J~ = -J = 0 and K~ = K + 2J = K) the map is
+    the identity: the two self-dual points of Sec. II."""
+    if abs(np.cos(phi)) < 1e-12:
+        return phi
     t = -np.tan(phi) - 1.0
     base = np.arctan(t)                     # in (-pi/2, pi/2)
     cand = [base, base + np.pi, base - np.pi]
@@ -35,7 +39,10 @@ def dual_angle(phi):
 
 
 def dual_amplitude(phi, phi_dual, A=1.0):
-    """A~ = -A cos(phi)/cos(phi~) so that J~ = -J (Sec. V, Eq. 14 context)."""
+    """A~ = -A cos(phi)/cos(phi~) so that J~ = -J (Sec. V, Eq. 14 context);
+    A at the self-dual Kitaev points, where both cosines vanish."""
+    if abs(np.cos(phi_dual)) < 1e-12:
+        return A
     return -A * np.cos(phi) / np.cos(phi_dual)
 
 

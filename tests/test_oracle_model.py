@@ -97,6 +97,30 @@ def test_duality_pairs_printed_in_paper():
             assert abs(model.dual_amplitude(phi, pd) - A_dual) < 0.005
 
 
+def test_duality_is_an_involution_and_maps_the_su2_points_onto_each_other():
+    """Applied twice the duality is the identity (J~~ = J, K~~ = K); the four
+    SU(2)-symmetric points of Sec. II (-45, 0, 135, 180 deg) map onto each
+    other, and the duals of -45 and 135 deg are pure Heisenberg (K~ = 0): the
+    hidden SU(2) symmetry of those two points."""
+    for phi_deg in np.linspace(-179.0, 179.0, 37):
+        phi = np.deg2rad(phi_deg)
+        J, K = model.couplings(phi)
+        pd = model.dual_angle(phi)
+        Jd, Kd = model.couplings(pd, model.dual_amplitude(phi, pd))
+        assert abs(Jd + J) < 1e-12 and abs(Kd - (K + 2 * J)) < 1e-12
+        pdd = model.dual_angle(pd)
+        Jdd, Kdd = model.couplings(pdd, model.dual_amplitude(pd, pdd, model.dual_amplitude(phi, pd)))
+        assert abs(Jdd - J) < 1e-12 and abs(Kdd - K) < 1e-12
+    pairs = {-45.0: 180.0, 0.0: 135.0, 135.0: 0.0, 180.0: -45.0}
+    for phi_deg, want in pairs.items():
+        pd = model.dual_angle(np.deg2rad(phi_deg))
+        assert abs(np.cos(pd) - np.cos(np.deg2rad(want))) < 1e-12
+        assert abs(np.sin(pd) - np.sin(np.deg2rad(want))) < 1e-12
+        Jd, Kd = model.couplings(pd, model.dual_amplitude(np.deg2rad(phi_deg), pd))
+        if phi_deg in (-45.0, 135.0):
+            assert abs(Kd) < 1e-12
+
+
 @pytest.mark.parametrize("phi_deg", [-63.0, -17.0, 30.0])
 def test_duality_spectrum_on_klein_cluster(phi_deg):
     """The Klein map (4-sublattice pi rotations; the 2x2 torus is compatible)
