@@ -44,3 +44,14 @@ def site_moments(X):
         out["A" + name] = float(np.real(np.trace(OA @ X.T)) / np.trace(X))
         out["B" + name] = float(np.real(np.trace(OB @ X.T)) / np.trace(X))
     return out
+
+
+def order_parameters(mom):
+    """Order parameters from the sublattice moments of ``site_moments`` (Sec.
+    V).  Ferromagnetic (also the stripy order, measured as the ferromagnetic
+    order of the dual Hamiltonian): m = 2 sqrt(sum_a <S^a>^2), <S^a> read as
+    the sublattice average (<S^a_A> + <S^a_B>)/2.  Antiferromagnetic: the
+    staggered m = sqrt(sum_a <S^a_A - S^a_B>^2)."""
+    fm = 2.0 * np.sqrt(sum((0.5 * (mom["A" + a] + mom["B" + a])) ** 2 for a in "xyz"))
+    af = np.sqrt(sum((mom["A" + a] - mom["B" + a]) ** 2 for a in "xyz"))
+    return {"m_fm": float(fm), "m_af": float(af)}

@@ -64,6 +64,26 @@ def test_field_only_closed_form(hA, hB):
     assert abs(r["E_site"] - 0.5 * (eA + eB)) < 1e-12
 
 
+@pytest.mark.parametrize("hA,hB", [(0.6, 0.6), (0.6, -0.6)])
+def test_order_parameters_in_a_pure_field(hA, hB):
+    """J = K = 0 in a field: every spin is free, <S^z> = tanh(beta h / 2) / 2.
+    A uniform field gives m_FM = tanh(beta h / 2) and m_AF = 0; a staggered
+    field gives m_AF = tanh(beta h / 2) and m_FM = 0 (the factor 2 of the
+    ferromagnetic definition and its absence in the staggered one both make
+    a saturated state read 1)."""
+    from oracle import observables
+    st = _fresh(2, 4, J=0.0, K=0.0, hA=hA, hB=hB)
+    for _ in range(6):
+        eefu.trotter_step(st, 0.05)
+    r = eefu.measure(st)
+    m = observables.order_parameters(r)
+    t = np.tanh(0.3 * 0.6 / 2.0)
+    if hA == hB:
+        assert abs(m["m_fm"] - t) < 1e-12 and m["m_af"] < 1e-12
+    else:
+        assert abs(m["m_af"] - t) < 1e-12 and m["m_fm"] < 1e-12
+
+
 def test_kh_high_temperature_against_ed_and_series():
     """D=4 eeFU at beta=0.05, 0.1 against 8- and 12-site ED: the eeFU value must
     sit within the finite-size spread |E8-E12| (+ Trotter margin) of E12, and
