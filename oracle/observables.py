@@ -55,3 +55,13 @@ def order_parameters(mom):
     fm = 2.0 * np.sqrt(sum((0.5 * (mom["A" + a] + mom["B" + a])) ** 2 for a in "xyz"))
     af = np.sqrt(sum((mom["A" + a] - mom["B" + a]) ** 2 for a in "xyz"))
     return {"m_fm": float(fm), "m_af": float(af)}
+
+
+def specific_heat(betas, energies):
+    """C = dE/dT = -beta^2 dE/dbeta per site (the specific heat of Sec. V) by
+    central differences along an imaginary-time trajectory on a uniform beta
+    grid; returns (interior betas, C there)."""
+    b = np.asarray(betas, dtype=np.float64)
+    e = np.asarray(energies, dtype=np.float64)
+    dEdb = (e[2:] - e[:-2]) / (b[2:] - b[:-2])
+    return b[1:-1], -b[1:-1] ** 2 * dEdb

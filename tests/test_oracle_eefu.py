@@ -64,6 +64,19 @@ def test_field_only_closed_form(hA, hB):
     assert abs(r["E_site"] - 0.5 * (eA + eB)) < 1e-12
 
 
+def test_specific_heat_of_decoupled_z_dimers():
+    """K_z only: decoupled dimers, no Trotter error, E(beta) = -(K_z/8) tanh(beta K_z/4),
+    so C = beta^2 K_z^2/32 sech^2(beta K_z/4); central differences on the
+    trajectory (step 0.05) agree to O(dbeta^2)."""
+    from oracle import observables
+    Kz = 1.3
+    st = _fresh(2, 6, J=0.0, K=0.0, K_gamma={"x": 0.0, "y": 0.0, "z": Kz})
+    res = eefu.evolve(st, 0.05, 8, measure_every=1)
+    b, C = observables.specific_heat([r["beta"] for r in res], [r["E_site"] for r in res])
+    want = b ** 2 * Kz ** 2 / 32.0 / np.cosh(b * Kz / 4.0) ** 2
+    assert len(b) == 6 and np.abs(C - want).max() < 1e-5
+
+
 @pytest.mark.parametrize("hA,hB", [(0.6, 0.6), (0.6, -0.6)])
 def test_order_parameters_in_a_pure_field(hA, hB):
     """J = K = 0 in a field: every spin is free, <S^z> = tanh(beta h / 2) / 2.
