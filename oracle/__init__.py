@@ -22,7 +22,9 @@ the Kitaev-Heisenberg model at finite temperature", arXiv:1906.02220):
                       quadruple (double-layer) tensor; the environment metric.
 * ``bond``         -- Fig. 3(b) and Sec. III: the environment-weighted bond
                       update A'-B' -> A''-B''.
-* ``observables``  -- energy per site, <S^a> per sublattice (Sec. V).
+* ``observables``  -- energy per site, <S^a> per sublattice, the printed
+                      order parameters, the specific heat along a
+                      trajectory (Sec. V).
 * ``eefu``         -- the imaginary-time driver of Sec. III.
 * ``exact``        -- independent pins: exact diagonalisation of honeycomb
                       clusters, Onsager's free energy, Yang's magnetisation,
