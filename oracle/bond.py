@@ -116,6 +116,25 @@ def als(Tp, N, D, tol=1e-12, max_iter=50, reg=1e-12, init=None):
                         history=history)
 
 
+def cost_gradient(A2, B2, Tp, N):
+    """Gradient of d = <T''-T'|N|T''-T'> with respect to A'' and B'' (same
+    shapes as A'', B'').  With B'' fixed the cost is a quadratic form in
+    a = A'' as [(u,r,k),(sA,aA)]: d = tr(a^T R_A a) - 2 tr(a^T S_A) + <T'|N|T'>
+    (the normal-equation matrices of the bond update), so dd/da =
+    (R_A + R_A^T) a - 2 S_A; likewise for B''.  The reference for gradient
+    checks of the bond cost."""
+    D = A2.shape[-1]
+    Dv = Tp.shape[1]
+    m = Dv * Dv * D
+    RA, SA = normal_equations_A(B2, Tp, N, D)
+    a = A2.transpose(2, 3, 4, 0, 1).reshape(m, 4)
+    gA = ((RA + RA.T) @ a - 2.0 * SA).reshape(Dv, Dv, D, 2, 2).transpose(3, 4, 0, 1, 2)
+    RB, SB = normal_equations_B(A2, Tp, N, D)
+    b = B2.transpose(2, 3, 4, 0, 1).reshape(m, 4)
+    gB = ((RB + RB.T) @ b - 2.0 * SB).reshape(Dv, Dv, D, 2, 2).transpose(3, 4, 0, 1, 2)
+    return gA, gB
+
+
 def balance_gauge(A2, B2):
     """Balanced SVD split of the bond; sign and scale conventions in the
     module docstring.  T'' is unchanged up to the overall scale."""

@@ -152,6 +152,33 @@ def test_bond_update_eckart_young():
     assert info0["rel_cost"] < 1e-26
 
 
+def test_bond_cost_gradient_against_central_differences():
+    """The analytic gradient of the bond cost along 8 random unit directions
+    in (A'', B'') against central finite differences (h = 1e-6, FP64); the
+    ALS optimum has zero gradient in both factors."""
+    D = 2
+    Tp = kh_inputs.random_composite(D, 5)
+    rng = np.random.default_rng(13)
+    G = rng.standard_normal((D ** 4, D ** 4))
+    N = G @ G.T / D ** 4 + 0.1 * np.eye(D ** 4)
+    A2 = rng.standard_normal((2, 2, D, D, D))
+    B2 = rng.standard_normal((2, 2, D, D, D))
+    gA, gB = bond.cost_gradient(A2, B2, Tp, N)
+    h = 1e-6
+    for _ in range(8):
+        dA = rng.standard_normal(A2.shape)
+        dB = rng.standard_normal(B2.shape)
+        nrm = np.sqrt(np.sum(dA ** 2) + np.sum(dB ** 2))
+        dA, dB = dA / nrm, dB / nrm
+        fd = (bond.cost(A2 + h * dA, B2 + h * dB, Tp, N)[0] - bond.cost(A2 - h * dA, B2 - h * dB, Tp, N)[0]) / (2 * h)
+        an = np.sum(gA * dA) + np.sum(gB * dB)
+        assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (fd, an)
+    A3, B3, _ = bond.als(Tp, N, D, tol=0.0, max_iter=400, reg=0.0)
+    gA3, gB3 = bond.cost_gradient(A3, B3, Tp, N)
+    scale = np.sqrt(np.sum(bond.cost_gradient(A2, B2, Tp, N)[0] ** 2))
+    assert np.abs(gA3).max() < 1e-6 * scale and np.abs(gB3).max() < 1e-6 * scale
+
+
 def test_bond_update_monotone_and_gauge_invariant():
     D = 2
     Tp = kh_inputs.random_composite(D, 4)
