@@ -205,6 +205,25 @@ def expval_matrix(T, N, Tbra=None):
     return T.reshape(p, -1) @ N @ Tbra.reshape(p, -1).T
 
 
+def correlation_length(env, a, direction=0):
+    """Correlation length in lattice constants along the horizontal
+    (direction 0) or vertical (1) axis: xi = 1 / ln|lambda_1 / lambda_2| of the
+    channel transfer matrix, one row of double-layer sites between the two
+    boundary edges, E1 a E3; the vertical channel is the same object in the
+    frame turned by a quarter (up edge E2, down edge E4, site rotate(a, 1)), as
+    in the up move of a sweep.  0 when the channel has rank one."""
+    if direction == 0:
+        up, dn, site = env.E[0], env.E[2], a
+    else:
+        up, dn, site = env.E[1], env.E[3], rotate(a, 1)
+    chi, d2 = up.shape[0], a.shape[0]
+    T = np.einsum("auc,lurv,dvb->albcrd", up, site, dn, optimize=True).reshape(chi * d2 * chi, -1)
+    w = np.sort(np.abs(np.linalg.eigvals(T)))[::-1]
+    if w[1] <= 1e-14 * w[0]:
+        return 0.0
+    return float(1.0 / np.log(w[0] / w[1]))
+
+
 # ---------------------------------------------------------------- partition-function ratios
 
 def kappa(env, a):

@@ -146,3 +146,27 @@ def test_onsager_with_reflection_asymmetric_bond_weights(hh, hv):
     a, env, info = _run(T, 16)
     assert info["delta"] < 1e-12
     assert abs(np.log(ctmrg.kappa(env, a)) - exact.onsager_lnZ(Kh, Kv)) < 1e-10
+
+
+@pytest.mark.filterwarnings("ignore::scipy.linalg.LinAlgWarning")
+@pytest.mark.parametrize("Kh", [0.3, 0.6, 1.0])
+def test_correlation_length_of_decoupled_chains(Kh):
+    """K_v = 0: the rows are independent 1D Ising chains, the environment is
+    exact, and the channel transfer matrix reduces to the chain's, whose
+    eigenvalue ratio is tanh K_h: xi_x = -1 / ln tanh K_h; nothing is
+    correlated along y."""
+    T = exact.ising_peps(Kh, 0.0)
+    a, env, info = _run(T, 8)
+    assert abs(ctmrg.correlation_length(env, a, 0) - (-1.0 / np.log(np.tanh(Kh)))) < 1e-12
+    assert ctmrg.correlation_length(env, a, 1) < 0.05
+
+
+def test_correlation_length_vertical_channel_is_the_rotated_horizontal_one():
+    """On a network without reflection symmetry (directed bond weights), xi
+    along y of T equals xi along x of T turned by a quarter (its own CTMRG)."""
+    T = _directed_ising(0.3, 0.2, 0.4, -0.7)
+    a, env, _ = _run(T, 16, tol=1e-14)
+    Tr = T.transpose(0, 2, 3, 4, 1)            # new (l,u,r,d) = old (u,r,d,l)
+    ar, envr, _ = _run(Tr, 16, tol=1e-14)
+    assert abs(ctmrg.correlation_length(env, a, 1) - ctmrg.correlation_length(envr, ar, 0)) < 1e-9
+    assert abs(ctmrg.correlation_length(env, a, 0) - ctmrg.correlation_length(envr, ar, 1)) < 1e-9
