@@ -19,7 +19,9 @@ the Kitaev-Heisenberg model at finite temperature", arXiv:1906.02220):
 * ``peps``         -- Fig. 3: site tensors, the beta=0 purification; Fig. 4(b)
                       and Sec. III: the gamma-composite on the rhombic lattice.
 * ``ctmrg``        -- Fig. 4(c) and Sec. III: square-lattice CTMRG on the
-                      quadruple (double-layer) tensor; the environment metric.
+                      quadruple (double-layer) tensor; the environment metric;
+                      the correlation length of Sec. IV from the channel
+                      transfer matrix.
 * ``bond``         -- Fig. 3(b) and Sec. III: the environment-weighted bond
                       update A'-B' -> A''-B''.
 * ``observables``  -- energy per site, <S^a> per sublattice, the printed
