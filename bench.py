@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--obs-sweeps", type=int, default=2, help="CTM sweeps per mapping in the observables")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP64 and (D, chi) = (6, 144) lines measured after the main one")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: = --steps")
     ap.add_argument("--kernel", default="", choices=["", "tc_gemm"],
                     help="profiling mode: run one library kernel on --size^3 operands instead of the bench")
@@ -173,13 +175,6 @@ def _peak(bound, prec, pk, pk_src):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12, "FP32 CUDA-core FMA peak 152 SM x 128 x 2 x %.0f MHz" % sm_mhz
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the bench
-# workload (profiles/eefu_kitaev_D4_chi64_top_kernels_full.md); the kernels
-# they describe must not have changed since, otherwise the entry is null.
-NCU_TRAFFIC = {("kitaev_D4_chi64", "tf32x3", "half_system_product"): 16.798976e6,
-               ("kitaev_D4_chi64", "tf32x3", "site_layer"): 8.934912e6}
-
-
 def roofline_entry(cat, c, bound, prec, pk, pk_src):
     if c["launches"] == 0 or c["ms"] <= 0:
         return None
@@ -188,7 +183,7 @@ def roofline_entry(cat, c, bound, prec, pk, pk_src):
     achieved = per_launch_flops / per_launch_s / 1e12
     peak, src = _peak(bound, prec, pk, pk_src)
     out = {"bound": bound, "kernel": cat, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-           "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((WORKLOAD, prec, cat)), "peak_source": src,
+           "frac": achieved / peak, "traffic": None, "peak_source": src,
            "flops_per_launch": per_launch_flops,
            "launches": c["launches"], "avg_launch_us": per_launch_s * 1e6}
     if bound == "tensor" and prec == "tf32x3":
@@ -197,25 +192,97 @@ def roofline_entry(cat, c, bound, prec, pk, pk_src):
 
 
 def roofline_for(prec, prof, pk, pk_src):
-    """`roofline`: the timed kernel category with an algorithmic flop model
-    that takes the most time -- on the bench workload the CholQR2
-    orthonormalisation of the projector subspace (Gram matrices, one-CTA
-    Cholesky factor and inverse, basis products; latency-bound, reported
-    against the CUDA-core peak).  `roofline_tensor_core`: the tcgen05
-    category that takes the most time (the double-layer site contraction or
-    the half-system product; None when no tensor-core mode is in use)."""
+    """`roofline`: the enlarged-corner step of a CTM move (the two corners
+    C E E (T, T) of a move, row a3 of the hot path), the contraction the
+    method spends its flops on: achieved = its algorithmic flops per move
+    (2 (2 chi^3 D^2 + 2 chi^3 D^4 + 4 p chi^2 D^6), the layered count whatever
+    form runs) / its average duration per move, against the tensor-core peak
+    of the contraction precision (the CUDA-core peak for FP32 / FP64).
+    Companion entries: the half-system product (a4), the absorption (a6) and
+    the CholQR2 orthonormalisation of the projector subspace (latency-bound,
+    against the CUDA-core peak).  `traffic` is null: these are categories of
+    several launches, and no DRAM counters of the current kernels are stored
+    with the benchmark."""
     tc = prec in ("tf32", "tf32x3", "bf16")
-    bounds = {"half_system_product": "tensor" if tc else "alu", "site_layer": "tensor" if tc else "alu",
-              "subspace_gemm": "alu", "cholqr_orth": "alu"}
-    kernels = {k: v for k, v in prof.items() if k in bounds and v["flops"] > 0 and v["launches"] > 0}
-    cat = max(kernels, key=lambda k: kernels[k]["ms"])
-    main = roofline_entry(cat, kernels[cat], bounds[cat], prec, pk, pk_src)
-    tc_entry = None
-    tc_cats = [k for k in ("site_layer", "half_system_product") if k in kernels] if tc else []
-    if tc_cats:
-        tcat = max(tc_cats, key=lambda k: kernels[k]["ms"])
-        tc_entry = roofline_entry(tcat, kernels[tcat], "tensor", prec, pk, pk_src)
-    return main, tc_entry
+    bounds = {"corners": "tensor" if tc else "alu", "half_system_product": "tensor" if tc else "alu",
+              "absorb": "tensor" if tc else "alu", "cholqr_orth": "alu"}
+    out = {}
+    for cat, b in bounds.items():
+        c = prof.get(cat)
+        if c and c["flops"] > 0 and c["launches"] > 0:
+            out[cat] = roofline_entry(cat, c, b, prec, pk, pk_src)
+    return out
+
+
+def step_flops(D, chi, sweeps, p=16):
+    """Algorithmic flops of the CTM sweeps of one step by the per-move model
+    F_move = 8 chi^3 D^4 + 12 p chi^2 D^6 + 2 chi^3 D^6 (4 moves per sweep)."""
+    f_move = 8.0 * chi ** 3 * D ** 4 + 12.0 * p * chi ** 2 * D ** 6 + 2.0 * chi ** 3 * D ** 6
+    return 4.0 * f_move * sweeps
+
+
+class Workload:
+    """One context of the library with the benchmark's step: a Trotter step
+    (fixed CTM sweeps per layer) followed by the observables (fixed sweeps per
+    mapping), on its own stream."""
+
+    def __init__(self, g, dev, D, chi, prec, a, w, seed):
+        import torch
+        self.g, self.dev, self.a, self.w = g, dev, a, w
+        self.D, self.chi, self.prec = D, chi, prec
+        self.A0, self.B0 = kh_inputs.perturbed_product_state(D, seed=seed, eps=0.05)
+        self.stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(self.stream):
+            self.ctx = g.Context(D, chi, prec, device=dev, stream=self.stream,
+                                 svd_cut=1e-12 if prec == "fp64" else 1e-6)
+            self.ctx.set_state(torch.as_tensor(self.A0, device=dev), torch.as_tensor(self.B0, device=dev))
+        self.Hs = [g.bond_hamiltonian(gm, w["J"], w["K"]) for gm in "xyz"]
+
+    def step(self):
+        a, w = self.a, self.w
+        self.ctx.eefu_trotter_step(w["J"], [w["K"]] * 3, w["dbeta"], ctm_max_sweeps=a.ctm_sweeps,
+                                   ctm_min_sweeps=a.ctm_sweeps, ctm_tol=-1.0, info=False)
+        return self.ctx.observables(self.Hs, ctm_max_sweeps=a.obs_sweeps, ctm_min_sweeps=a.obs_sweeps,
+                                    ctm_tol=-1.0)
+
+    def timed(self, steps, warmup, flush=None):
+        """Warm-up, then `steps` steps each bracketed by CUDA events on the
+        context's stream (L2 flushed before each, outside the events).
+        Returns (total ms, last observables)."""
+        import torch
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize(self.dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        last = None
+        for i in range(steps):
+            if flush is not None:
+                with torch.cuda.stream(self.stream):
+                    flush_l2(flush)
+            ev[i][0].record(self.stream)
+            last = self.step()
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize(self.dev)
+        return sum(s.elapsed_time(e) for s, e in ev), last
+
+    def close(self):
+        self.ctx.close()
+
+
+def variant(g, dev, a, w, D, chi, prec, steps, warmup, flush):
+    """A second configuration measured in the same run (one replica, same
+    step definition): steps/s and its CTM-sweep flop rate."""
+    wl = Workload(g, dev, D, chi, prec, a, w, seed=0)
+    ms, last = wl.timed(steps, warmup, flush)
+    wl.close()
+    ms_step = ms / steps
+    sw = sweeps_per_step(a)
+    return {"config": {"D": D, "chi": chi, "prec": prec, "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
+                       "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps},
+            "value": 1e3 / ms_step, "unit": "steps/s", "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
+            "ctm_sweeps_per_s": 1e3 / ms_step * sw,
+            "ctm_sweep_tflops": step_flops(D, chi, sw) / (ms_step * 1e-3) / 1e12,
+            "E_site": last["E_site"] if last else None}
 
 
 def run_ours(a, rank, world, local, pg):
@@ -225,48 +292,24 @@ def run_ours(a, rank, world, local, pg):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     w = workload()
-    D, chi, dbeta, J, K = w["D"], w["chi"], w["dbeta"], w["J"], w["K"]
-    svd_cut = 1e-12 if a.prec == "fp64" else 1e-6
-    A0, B0 = kh_inputs.perturbed_product_state(D, seed=rank, eps=0.05)
-    stream = torch.cuda.Stream(device=dev)
-    with torch.cuda.stream(stream):
-        ctx = g.Context(D, chi, a.prec, device=dev, stream=stream, svd_cut=svd_cut)
-        At = torch.as_tensor(A0, device=dev)
-        Bt = torch.as_tensor(B0, device=dev)
-        ctx.set_state(At, Bt)
-    Hs = [g.bond_hamiltonian(gm, J, K) for gm in "xyz"]
-    Kxyz = [K, K, K]
-
-    def step():
-        ctx.eefu_trotter_step(J, Kxyz, dbeta, ctm_max_sweeps=a.ctm_sweeps, ctm_min_sweeps=a.ctm_sweeps,
-                              ctm_tol=-1.0, info=False)
-        return ctx.observables(Hs, ctm_max_sweeps=a.obs_sweeps, ctm_min_sweeps=a.obs_sweeps, ctm_tol=-1.0)
-
+    D, chi = w["D"], w["chi"]
+    wl = Workload(g, dev, D, chi, a.prec, a, w, seed=rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(a.warmup):
-        step()
+        wl.step()
     torch.cuda.synchronize(dev)
     barrier(pg)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = g.launch_count()
-    ctx.profile_start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    last = None
-    for i in range(a.steps):
-        with torch.cuda.stream(stream):
-            flush_l2(flush)
-        ev[i][0].record(stream)
-        last = step()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize(dev)
-    prof = ctx.profile_stop()
+    wl.ctx.profile_start()
+    t_ms, last = wl.timed(a.steps, 0, flush)
+    prof = wl.ctx.profile_stop()
     launches = g.launch_count() - launches0
     clk = clocks.stop()
     barrier(pg)
     torch.cuda.synchronize(dev)
-    t_ms = sum(s.elapsed_time(e) for s, e in ev)
     t_max = max_over_ranks(pg, t_ms)
     value = a.steps * world / (t_max * 1e-3)
 
@@ -274,19 +317,19 @@ def run_ours(a, rank, world, local, pg):
     ne = a.e2e_steps or a.steps
     hA = torch.empty((2, 2, D, D, D), dtype=torch.float64, pin_memory=True)
     hB = torch.empty_like(hA)
-    dA, dB = ctx.get_state()
+    dA, dB = wl.ctx.get_state()
     hA.copy_(dA)
     hB.copy_(dB)
     torch.cuda.synchronize(dev)
     barrier(pg)
     t0 = time.perf_counter()
     for _ in range(ne):
-        with torch.cuda.stream(stream):
+        with torch.cuda.stream(wl.stream):
             dA.copy_(hA, non_blocking=True)
             dB.copy_(hB, non_blocking=True)
-        ctx.set_state(dA, dB)
-        r = step()
-        dA, dB = ctx.get_state()
+        wl.ctx.set_state(dA, dB)
+        wl.step()
+        dA, dB = wl.ctx.get_state()
         hA.copy_(dA)
         hB.copy_(dB)
     torch.cuda.synchronize(dev)
@@ -299,36 +342,51 @@ def run_ours(a, rank, world, local, pg):
     out = None
     if rank == 0:
         pk, pk_src = peaks()
-        roof, roof_tc = roofline_for(a.prec, prof, pk, pk_src)
+        roofs = roofline_for(a.prec, prof, pk, pk_src)
         err = None
         if not a.no_fp64_check and a.prec != "fp64":
-            err = fp64_check(a, g, dev, A0, B0, w, Hs, last, a.warmup + a.steps)
-        cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, A0, B0)   # N = 1 only
+            err = fp64_check(a, g, dev, wl.A0, wl.B0, w, wl.Hs, last, a.warmup + a.steps)
+        variants = []
+        if not a.no_variants and world == 1:
+            # the plain FP64 GPU form of the same workload, and the largest
+            # single-precision configuration (D, chi) = (6, 144)
+            variants.append(variant(g, dev, a, w, D, chi, "fp64", 2, 3, flush))
+            variants.append(variant(g, dev, a, w, 6, 144, a.prec, 2, 3, flush))
+        cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, wl.A0, wl.B0)   # N = 1 only
+        sw = sweeps_per_step(a)
         out = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64"}.get(a.prec, a.prec),
             "data": "synthetic (seeded perturbed beta=0 product state)",
-            "config": {"workload": WORKLOAD, "D": D, "chi": chi, "J": J, "K": K, "dbeta": dbeta,
+            "config": {"workload": WORKLOAD, "D": D, "chi": chi, "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
                        "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
                        "prec": a.prec, "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MB write outside the timed events)"},
-            "ctm_sweeps_per_s": value * sweeps_per_step(a),
+            "ctm_sweeps_per_s": value * sw,
+            "ctm_sweep_tflops": step_flops(D, chi, sw) / (t_max / a.steps * 1e-3) / 1e12,
             "E_site": last["E_site"] if last else None,
             "err_vs_fp64": err,
-            "roofline": roof,
-            "roofline_tensor_core": roof_tc,
+            "roofline": roofs.get("corners"),
+            "roofline_half_system_product": roofs.get("half_system_product"),
+            "roofline_absorb": roofs.get("absorb"),
+            "roofline_projector_orth": roofs.get("cholqr_orth"),
             "profile": prof,
+            "variants": variants,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
         }
+    wl.close()
     return out
 
 
 def fp64_check(a, g, dev, A0, B0, w, Hs, last, nsteps):
-    """|E_site(prec) - E_site(fp64)| / max(|E|, 1) after the same steps on the GPU FP64 path."""
+    """|E_site(prec) - E_site(fp64)| / max(|E|, 1) after the same steps on the
+    GPU FP64 path (a consistency check of the precisions at the bench's fixed
+    sweep counts; the parity of each against the CPU oracle is the test
+    suite's)."""
     import torch
     D, chi = w["D"], w["chi"]
     ctx = g.Context(D, chi, "fp64", device=dev, svd_cut=1e-12)
@@ -364,9 +422,9 @@ def cpu_baseline(a, w, A0, B0):
     scale = 5 + 3 * a.obs_sweeps / a.ctm_sweeps
     step_s = t_layer * scale
     return {"value": 1.0 / step_s, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one gate layer (%d CTM sweeps + metric + ALS) of the bench workload, %.1f s, scaled x%.2f "
-                      "to a full step (5 layers + 3 x %d observable sweeps)" % (a.ctm_sweeps, t_layer, scale,
-                                                                                 a.obs_sweeps)}
+            "sample": "one gate layer (%d CTM sweeps + metric + ALS) of the bench workload, %.1f s wall, "
+                      "extrapolated x%.2f to a full step (5 layers + 3 x %d observable sweeps)"
+                      % (a.ctm_sweeps, t_layer, scale, a.obs_sweeps)}
 
 
 def run_reference(a, rank, world):
@@ -381,15 +439,17 @@ def run_reference(a, rank, world):
     step_s = statistics.mean(ts) * scale
     value = 1.0 / step_s
     cpu = {"value": value, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-           "sample": "per step: one gate layer (%d CTM sweeps + metric + ALS), scaled x%.2f to a full step"
-                     % (a.ctm_sweeps, scale)}
+           "sample": "per step: one gate layer (%d CTM sweeps + metric + ALS), %.1f s on average, extrapolated "
+                     "x%.2f to a full step (5 layers + 3 x %d observable sweeps); ms_per_step is that "
+                     "extrapolation, the wall time of each timed sample is timed_s_per_step"
+                     % (a.ctm_sweeps, statistics.mean(ts), scale, a.obs_sweeps)}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "D": w["D"], "chi": w["chi"], "J": w["J"], "K": w["K"],
                        "dbeta": w["dbeta"], "ctm_sweeps_per_layer": a.ctm_sweeps,
                        "obs_sweeps_per_mapping": a.obs_sweeps, "prec": "fp64 (CPU oracle)"},
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "timed_s_per_step": statistics.mean(ts), "extrapolation": scale,
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

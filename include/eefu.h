@@ -238,8 +238,10 @@ unsigned long long kh_launch_count(void);
  * context's stream; enable == 0: synchronise, stop, and write host_out[30] =
  * {launches, milliseconds, algorithmic flops} per category: 0 half-system
  * product Mt = Q_{s+3} Q_s (2 n^3 flops, n = chi D^2), 1 two-layer site
- * contractions (4 nb p D^6 flops per call), 2 enlarged corners, 3 projector
- * SVD without Mt, 4 absorption, 5 environment metric, 6 ALS and gauge,
+ * contractions (4 nb p D^6 flops per call), 2 the two enlarged corners of a
+ * move (2 (2 chi^3 D^2 + 2 chi^3 D^4 + 4 p chi^2 D^6) flops), 3 projector
+ * SVD without Mt, 4 absorption (6 chi^3 D^2 + 4 chi^3 D^4 + 4 p chi^2 D^6
+ * flops), 5 environment metric, 6 ALS and gauge,
  * 7 one-sided Jacobi SVD, 8 CholQR orthonormalisation, 9 subspace products
  * M V and M^T U (2 n^2 k flops).  Categories without a flop model report 0,
  * except 7, whose third entry is the total number of Jacobi sweeps;
@@ -300,9 +302,13 @@ kh_status kh_selftest_fp64_newton(int n, const double* dev_x, double* dev_out, v
  * kh_gemm_noalloc_max_bytes() bytes (16 MiB) that every GPU loading the
  * library holds until exit; sizes needing more (kh_selftest_bytes(M, N, K))
  * return KH_EINVAL.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race.  Synchronises stream; no cudaMalloc or cudaFree. */
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * later calls on that device (the lookup is safe when several host threads
+ * make their first calls at once); make that first call before any stream
+ * capture.  A device reset (cudaDeviceReset) discards the array, so the
+ * entry point must not be called on that device afterwards.  All calls
+ * share the array: calls that overlap on the GPU race.  Every call ends by
+ * synchronising stream; no cudaMalloc or cudaFree. */
 size_t kh_gemm_noalloc_max_bytes(void);
 kh_status kh_gemm_noalloc(int prec, int M, int N, int K, const double* dev_A, const double* dev_B, double* dev_C,
                           void* stream);

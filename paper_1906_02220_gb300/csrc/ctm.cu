@@ -943,6 +943,21 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
     if (side) join_side();
 }
 
+// Algorithmic flops of a move's steps, counted as the layered (ket, then
+// bra) contraction whatever form runs: one enlarged corner is X = C E
+// (2 chi^3 D^2), Y = E X (2 chi^3 D^4) and the two site layers (4 p chi^2 D^6);
+// the absorption is C' = P^T (C E), C4 E3 and (C4 E3) P~^T (6 chi^3 D^2 in all),
+// E^T P (2 chi^3 D^4), the two site layers and the product with P~^T
+// (2 chi^3 D^4).
+static double corner_flops(int chi, int D, int p) {
+    const double c = chi, d2 = (double)D * D, d4 = d2 * d2, d6 = d4 * d2;
+    return 2.0 * c * c * c * d2 + 2.0 * c * c * c * d4 + 4.0 * p * c * c * d6;
+}
+static double absorb_flops(int chi, int D, int p) {
+    const double c = chi, d2 = (double)D * D, d4 = d2 * d2, d6 = d4 * d2;
+    return 6.0 * c * c * c * d2 + 4.0 * c * c * c * d4 + 4.0 * p * c * c * d6;
+}
+
 template <typename T>
 void Engine<T>::move(Slot<T>& sl, int s, int slot_id) {
     prof_begin(2);
@@ -975,13 +990,13 @@ void Engine<T>::move(Slot<T>& sl, int s, int slot_id) {
         corner(sl, s, 0);
         corner(sl, (s + 3) & 3, 1);
     }
-    prof_end(2, 0.0);
+    prof_end(2, 2.0 * corner_flops(dm.chi, dm.D, sl.p));
     prof_begin(3);
     projector(sl, s, slot_id);
     prof_end(3, 0.0);
     prof_begin(4);
     absorb(sl, s);
-    prof_end(4, 0.0);
+    prof_end(4, absorb_flops(dm.chi, dm.D, sl.p));
 }
 
 template <typename T>

@@ -18,7 +18,29 @@ constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {nullptr};       // device address per device, set on first use
+// Device address of the array per device, looked up on the first call on that
+// device.  Host threads may make their first calls at the same time: the
+// lookup runs under one lock and the address is published atomically.
+std::atomic<void*> g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_lookup;
+
+// Returns the device address of g_noalloc_scratch on device dev (current).
+cudaError_t scratch_address(int dev, void** out) {
+    void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_scratch_lookup);
+        p = g_scratch_addr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            // The array's name is a host-side stand-in; its address on the
+            // current device comes from the runtime.
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) return e != cudaSuccess ? e : cudaErrorInvalidSymbol;
+            g_scratch_addr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -41,19 +63,13 @@ kh_status kh_gemm_noalloc(int prec, int M, int N, int K, const double* A, const 
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return KH_ECUDA;
-    if (!g_scratch_addr[dev]) {
-        // The array's name is a host-side stand-in; its device address for the
-        // current device comes from the runtime (once per device).
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            fprintf(stderr, "kh_gemm_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-            return KH_ECUDA;
-        }
-        g_scratch_addr[dev] = p;
+    void* scratch = nullptr;
+    cudaError_t e = scratch_address(dev, &scratch);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "kh_gemm_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+        return KH_ECUDA;
     }
-    return kh::selftest_gemm_on(prec, M, N, K, A, B, C, g_scratch_addr[dev], kNoAllocScratchBytes,
-                                (cudaStream_t)stream);
+    return kh::selftest_gemm_on(prec, M, N, K, A, B, C, scratch, kNoAllocScratchBytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

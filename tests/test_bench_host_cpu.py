@@ -35,49 +35,41 @@ def test_fallback_peaks_when_the_measured_file_is_absent(monkeypatch, tmp_path):
 
 def test_roofline_entry_arithmetic():
     c = {"launches": 10, "ms": 1.0, "flops": 1e10}
-    r = bench.roofline_entry("site_layer", c, "tensor", "tf32x3", PK, "measured")
+    r = bench.roofline_entry("corners", c, "tensor", "tf32x3", PK, "measured")
     assert abs(r["achieved"] - 10.0) < 1e-12                 # 1e9 flop per 100 us launch = 10 TFLOP/s
     assert abs(r["frac"] - 10.0 / (1800.0 * 1.1 / 2.25)) < 1e-12
     assert abs(r["avg_launch_us"] - 100.0) < 1e-9 and r["flops_per_launch"] == 1e9
     assert r["mma_passes"] == 3 and r["unit"] == "TFLOP/s"
-    assert r["traffic"] == bench.NCU_TRAFFIC[(bench.WORKLOAD, "tf32x3", "site_layer")]
-    assert bench.roofline_entry("site_layer", c, "tensor", "tf32", PK, "measured")["traffic"] is None
-    assert bench.roofline_entry("site_layer", {"launches": 0, "ms": 0.0, "flops": 0.0}, "tensor", "tf32x3",
+    assert r["traffic"] is None                                # no stored DRAM counters
+    assert bench.roofline_entry("corners", {"launches": 0, "ms": 0.0, "flops": 0.0}, "tensor", "tf32x3",
                                 PK, "measured") is None
 
 
-def test_roofline_reports_the_longest_category_with_a_flop_model():
-    prof = {"half_system_product": {"launches": 4, "ms": 2.0, "flops": 8e9},
-            "site_layer": {"launches": 12, "ms": 3.0, "flops": 6e9},
-            "subspace_gemm": {"launches": 8, "ms": 1.0, "flops": 1e9},
-            "projector_svd": {"launches": 50, "ms": 9.0, "flops": 0.0}}      # no flop model: never chosen
-    main, tc = bench.roofline_for("tf32x3", prof, PK, "measured")
-    assert main["kernel"] == "site_layer" and main["bound"] == "tensor"
-    assert tc["kernel"] == "site_layer"
-    main32, tc32 = bench.roofline_for("fp32", prof, PK, "measured")
-    assert main32["bound"] == "alu" and tc32 is None
-
-
-def test_roofline_on_the_measured_bench_profile():
-    """Category times of a default bench run on one GB300 (5 timed steps);
-    flops of the CholQR2 category from its model 5 n k^2 + 2 n k + 2 k^3 / 3
-    at n = 1024, k = 80 per call."""
-    n, k, calls = 1024, 80, 1040
-    prof = {"projector_svd": {"launches": 520, "ms": 275.996, "flops": 0.0},
-            "cholqr_orth": {"launches": calls, "ms": 108.986,
-                            "flops": calls * (5.0 * n * k * k + 2.0 * n * k + 2.0 * k ** 3 / 3.0)},
-            "absorb": {"launches": 520, "ms": 51.933, "flops": 0.0},
-            "corners": {"launches": 520, "ms": 45.647, "flops": 0.0},
-            "als_gauge": {"launches": 25, "ms": 41.958, "flops": 0.0},
-            "svd_jacobi": {"launches": 520, "ms": 41.714, "flops": 1029.0},
-            "site_layer": {"launches": 1560, "ms": 31.019, "flops": 837518622720.0},
-            "subspace_gemm": {"launches": 1040, "ms": 24.917, "flops": 174483046400.0},
+def test_roofline_is_the_enlarged_corner_step():
+    """The main entry is the two enlarged corners of a move, by their
+    algorithmic (layered) flop count; categories without a flop model are
+    never reported."""
+    D, chi, p = 4, 64, 16
+    per_move = 2 * (2 * chi ** 3 * D ** 2 + 2 * chi ** 3 * D ** 4 + 4 * p * chi ** 2 * D ** 6)
+    prof = {"corners": {"launches": 520, "ms": 45.647, "flops": 520 * per_move},
             "half_system_product": {"launches": 520, "ms": 15.782, "flops": 1116691496960.0},
-            "metric": {"launches": 40, "ms": 5.183, "flops": 0.0}}
-    main, tc = bench.roofline_for("tf32x3", prof, PK, "measured")
-    assert main["kernel"] == "cholqr_orth" and main["bound"] == "alu" and main["traffic"] is None
-    assert 0.3 < main["achieved"] < 0.34 and main["frac"] < 0.005          # ~0.32 TFLOP/s: latency-bound
-    assert tc["kernel"] == "site_layer" and abs(tc["achieved"] - 27.0) < 0.1
+            "cholqr_orth": {"launches": 1040, "ms": 108.986, "flops": 1040 * 3.3273e7},
+            "projector_svd": {"launches": 520, "ms": 275.996, "flops": 0.0}}
+    r = bench.roofline_for("tf32x3", prof, PK, "measured")
+    assert r["corners"]["bound"] == "tensor" and r["corners"]["kernel"] == "corners"
+    assert abs(r["corners"]["flops_per_launch"] - per_move) < 1.0
+    assert abs(r["corners"]["achieved"] - per_move / 87.78e-6 / 1e12) < 0.01
+    assert r["cholqr_orth"]["bound"] == "alu" and "projector_svd" not in r
+    r32 = bench.roofline_for("fp32", prof, PK, "measured")
+    assert r32["corners"]["bound"] == "alu"
+
+
+def test_step_flop_model():
+    """F_move = 8 chi^3 D^4 + 12 p chi^2 D^6 + 2 chi^3 D^6, four moves a sweep:
+    2.4e10 flops per sweep at (D, chi) = (4, 64) and 2.0e12 at (6, 144)."""
+    assert abs(bench.step_flops(4, 64, 1) / 2.4e10 - 1.0) < 0.02
+    assert abs(bench.step_flops(6, 144, 1) / 2.0e12 - 1.0) < 0.02
+    assert bench.step_flops(4, 64, 26) == 26 * bench.step_flops(4, 64, 1)
 
 
 class _Done:

@@ -198,3 +198,43 @@ def test_bond_update_monotone_and_gauge_invariant():
     gb = Bn.reshape(-1, D).T @ Bn.reshape(-1, D)
     assert np.allclose(ga, np.diag(np.diag(ga)), atol=1e-13)
     assert np.allclose(np.diag(ga) / np.trace(ga), np.diag(gb) / np.trace(gb), atol=1e-13)
+
+
+def _gate_layer_gradient_ratio():
+    """Norm of the gradient of the environment-weighted cost at the bond a
+    gate layer returns, over its norm at the truncated-SVD start.
+
+    A truncating layer (J != 0: gate of Schmidt rank 4, bond 4D = 8 cut to
+    D = 2) on a random state.  The metric N is rebuilt from the layer's own
+    converged environment; each point is first rescaled by its optimal
+    factor <T''|N|T'>/<T''|N|T''> (the layer normalises A'', B''), and the
+    gradient is the central-difference-pinned ``bond.cost_gradient``.  The
+    layer minimises <T''-T'|N|T''-T'>, so its result is stationary (ratio ~ the
+    ALS tolerance's square root); the truncated SVD is the optimum for N = 1
+    only, so a layer that weighted the bond by anything else (the identity,
+    a stale or transposed metric) leaves a gradient of the start's size."""
+    D, chi = 2, 8
+    J, K = model.couplings(0.3 * np.pi)
+    A, B = kh_inputs.random_site_tensors(D, 31)
+    st = eefu.State(A, B, eefu.Params(D=D, chi=chi, J=J, K=K, ctm_tol=1e-12))
+    g = st.prm.gate("z", 0.2)
+    eefu.apply_gate(st, "z", g)
+    Tp = peps.composite(A, B, "z", g)
+    N = ctmrg.metric(st.env["z"], D)
+
+    def grad_norm(A2, B2):
+        a, b, _ = bond.cost_terms(A2, B2, Tp, N)
+        gA, gB = bond.cost_gradient((b / a) * A2, B2, Tp, N)
+        return np.sqrt(np.sum(gA ** 2) + np.sum(gB ** 2))
+
+    A2, B2 = peps.to_composite_frame(st.A, st.B, "z")
+    A0, B0, S = bond.svd_init(Tp, D)
+    assert S[D] > 0.05 * S[0]                     # the cut really truncates
+    return grad_norm(A2, B2) / grad_norm(A0, B0)
+
+
+def test_gate_layer_minimises_the_environment_weighted_cost():
+    """Pins the wiring of the bond update inside a gate layer: the bond it
+    returns is a stationary point of the cost weighted by the layer's own
+    environment metric (Fig. 3(b)), not of the plain (N = 1) truncation."""
+    assert _gate_layer_gradient_ratio() < 1e-4

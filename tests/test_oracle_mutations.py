@@ -140,8 +140,16 @@ def pin_balanced_gauge():
     return max(dev) / 1e-13
 
 
+def pin_environment_weighted_layer():
+    """The bond a truncating gate layer returns is stationary for the cost
+    weighted by the layer's own environment metric (gradient ratio against
+    the truncated-SVD start, see test_oracle_eefu)."""
+    from test_oracle_eefu import _gate_layer_gradient_ratio
+    return _gate_layer_gradient_ratio() / 1e-4
+
+
 PINS = [pin_bond_spectrum, pin_beta0, pin_dimer, pin_kz_only, pin_field_only, pin_mappings, pin_onsager,
-        pin_bond_correlations, pin_eckart_young, pin_balanced_gauge]
+        pin_bond_correlations, pin_eckart_young, pin_balanced_gauge, pin_environment_weighted_layer]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda p: p.__name__)
@@ -285,3 +293,11 @@ def test_sublattice_moments_swapped_are_caught(monkeypatch):
         return {("B" if k[0] == "A" else "A") + k[1:]: v for k, v in m.items()}
     monkeypatch.setattr(observables, "site_moments", site_moments)
     assert _fails(pin_field_only)
+
+
+def test_bond_update_without_the_environment_metric_is_caught(monkeypatch):
+    """The gate layer hands the identity instead of N to the bond update: the
+    update degenerates to the plain truncated SVD."""
+    orig = bond.als
+    monkeypatch.setattr(bond, "als", lambda Tp, N, D, *a, **k: orig(Tp, np.eye(N.shape[0]), D, *a, **k))
+    assert _fails(pin_environment_weighted_layer)
