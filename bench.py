@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32x3")
+    ap.add_argument("--proj-fp64", type=int, default=0,
+                    help="1: projector factorisations in FP64 (single-precision modes)")
     ap.add_argument("--ctm-sweeps", type=int, default=4, help="CTM sweeps per gate layer")
     ap.add_argument("--obs-sweeps", type=int, default=2, help="CTM sweeps per mapping in the observables")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -226,7 +228,7 @@ class Workload:
     (fixed CTM sweeps per layer) followed by the observables (fixed sweeps per
     mapping), on its own stream."""
 
-    def __init__(self, g, dev, D, chi, prec, a, w, seed):
+    def __init__(self, g, dev, D, chi, prec, a, w, seed, proj_fp64=0):
         import torch
         self.g, self.dev, self.a, self.w = g, dev, a, w
         self.D, self.chi, self.prec = D, chi, prec
@@ -234,7 +236,8 @@ class Workload:
         self.stream = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(self.stream):
             self.ctx = g.Context(D, chi, prec, device=dev, stream=self.stream,
-                                 svd_cut=1e-12 if prec == "fp64" else 1e-6)
+                                 svd_cut=1e-12 if prec == "fp64" else 1e-6,
+                                 proj_fp64=proj_fp64 if prec != "fp64" else 0)
             self.ctx.set_state(torch.as_tensor(self.A0, device=dev), torch.as_tensor(self.B0, device=dev))
         self.Hs = [g.bond_hamiltonian(gm, w["J"], w["K"]) for gm in "xyz"]
 
@@ -293,7 +296,7 @@ def run_ours(a, rank, world, local, pg):
     torch.cuda.set_device(dev)
     w = workload()
     D, chi = w["D"], w["chi"]
-    wl = Workload(g, dev, D, chi, a.prec, a, w, seed=rank)
+    wl = Workload(g, dev, D, chi, a.prec, a, w, seed=rank, proj_fp64=a.proj_fp64)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(a.warmup):
         wl.step()
@@ -361,7 +364,8 @@ def run_ours(a, rank, world, local, pg):
             "data": "synthetic (seeded perturbed beta=0 product state)",
             "config": {"workload": WORKLOAD, "D": D, "chi": chi, "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
                        "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
-                       "prec": a.prec, "parallelism": "replicas x%d" % world,
+                       "prec": a.prec, "projector_factorisations": "fp64" if (a.proj_fp64 or a.prec == "fp64")
+                       else "fp32", "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MB write outside the timed events)"},
             "ctm_sweeps_per_s": value * sw,
             "ctm_sweep_tflops": step_flops(D, chi, sw) / (t_max / a.steps * 1e-3) / 1e12,

@@ -85,6 +85,13 @@ typedef struct kh_config {
     int als_max_iter;        /* ALS iteration cap                                    */
     double als_reg;          /* Tikhonov shift reg * tr(R)/dim(R) in the normal eqns  */
     uint64_t seed;           /* seed of the counter-based start vectors              */
+    int proj_fp64;           /* 1: in the single-precision modes, the projector
+                                factorisations (the Cholesky factor of the
+                                subspace QR, the Rayleigh-Ritz SVD, S^-1/2 and the
+                                cut-off) run in FP64 arithmetic; their products
+                                with the contraction data stay in the contraction
+                                precision.  The FP64 mode always does.  Limits
+                                k = chi + svd_oversample to the FP64 solver's 112. */
 } kh_config;
 
 typedef struct kh_ctx kh_ctx;   /* opaque; host memory owned by the library */
@@ -185,6 +192,19 @@ kh_status ctm_kappa(kh_ctx* ctx, int slot, double* host_kappa);
 kh_status ctm_expval(kh_ctx* ctx, int slot, const double* host_ops, int n_ops,
                      double* host_vals);
 
+/* Correlation length of slot's network along direction 0 (horizontal: the
+ * column transfer matrix E1 (site) E3) or 1 (vertical: E2 (site) E4), the
+ * length of the paper's scaling analysis (Sec. IV): xi = 1 / ln(|l1| / |l2|)
+ * from the two largest eigenvalues in modulus of the channel transfer matrix
+ * (dimension chi^2 D^2, never formed), by a block power iteration on up to 4
+ * vectors with Rayleigh-Ritz steps every 4 iterations, stopped when
+ * |l2| / |l1| changes by less than tol (relative) or after max_iter.
+ * host_out[3]: xi (0 when |l2| / |l1| < 1e-14), |l2| / |l1|, iterations.
+ * The environment should be converged (ctm_sweep); uses the slot's scratch.
+ * Errors: KH_EINVAL (no environment, direction not 0 or 1), KH_ENUMERIC. */
+kh_status ctm_correlation_length(kh_ctx* ctx, int slot, int direction, int max_iter, double tol,
+                                 double* host_out);
+
 /* --- eeFU bond update (Fig. 3(b), Sec. III) -------------------------------- */
 
 /* One gate layer on direction gamma (0 x, 1 y, 2 z): build the gated
@@ -229,6 +249,21 @@ kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* host_K_xyz, dou
                             double dbeta, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
                             double* host_info);
 
+/* An imaginary-time trajectory (Sec. III, Eq. 6) with its thermodynamics
+ * (Sec. V): n_steps Trotter steps of dbeta as eefu_trotter_step (CTM
+ * arguments mx, mn, tol per gate layer), and after every measure_every-th
+ * step the observables (CTM arguments obs_*).  host_traj receives
+ * n_steps / measure_every rows of 13 doubles: beta (counted from the first
+ * call on this context, which starts at the initial state's beta = 0), E_site,
+ * Hx, Hy, Hz, SxA, SyA, SzA, SxB, SyB, SzB, the largest discarded weight, and
+ * the specific heat per site C = dE/dT = -beta^2 dE/dbeta by central
+ * differences over the measurement grid (NaN in the first and last row).
+ * The couplings and the bias are those of eefu_trotter_step; the bond
+ * energies are measured without the bias, E_site includes it. */
+kh_status eefu_evolve(kh_ctx* ctx, double J, const double* host_K_xyz, double hA, double hB, double dbeta,
+                      int n_steps, int measure_every, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
+                      int obs_max_sweeps, int obs_min_sweeps, double obs_tol, double* host_traj);
+
 /* --- instrumentation (no counterpart in the paper; used by the benchmark) -- */
 
 /* Number of kernels this library has launched since it was loaded. */
@@ -272,6 +307,16 @@ kh_status kh_selftest_symeig(int prec, int k, const double* dev_G, double* dev_W
  * X Q = L S with dev_S descending (k), dev_L, dev_Q k x k (columns = vectors). */
 kh_status kh_selftest_svd(int prec, int k, const double* dev_X, double* dev_S, double* dev_L, double* dev_Q,
                           void* dev_scratch, size_t scratch_bytes, void* stream);
+
+/* The projector SVD of the FP64-projector option (kh_config.proj_fp64) on a
+ * k x k FP64 matrix X (k <= 160): the FP32 one-sided Jacobi SVD followed by
+ * three FP64 Newton refinement steps (first-order corrections L' = L (I + F),
+ * Q' = Q (I + H) from R = I - L^T L, P = I - Q^T Q and T = L^T X Q, pairs
+ * whose gap is below 64 times their coupling only re-orthogonalised).  X Q = L S with dev_S
+ * (k, in the Jacobi's descending order), dev_L, dev_Q k x k (columns =
+ * vectors).  Scratch as for kh_selftest_svd.  Synchronises stream. */
+kh_status kh_selftest_svd_refined(int k, const double* dev_X, double* dev_S, double* dev_L, double* dev_Q,
+                                  void* dev_scratch, size_t scratch_bytes, void* stream);
 
 /* Orthonormal basis of the columns of an n x k FP64 matrix Y (row-major) by
  * the library's ordered CholQR2 (two Cholesky-QR passes, columns taken in

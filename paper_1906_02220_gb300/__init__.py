@@ -25,9 +25,10 @@ ABI_FUNCTIONS = [
     "kh_config_defaults", "kh_workspace_bytes", "kh_create", "kh_destroy", "kh_last_error",
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
-    "ctm_expval", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
-    "eefu_trotter_step", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
-    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_orth", "kh_selftest_fp64_newton", "kh_gemm_noalloc",
+    "ctm_expval", "ctm_correlation_length", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
+    "eefu_trotter_step", "eefu_evolve", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
+    "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_svd_refined", "kh_selftest_orth", "kh_selftest_fp64_newton",
+    "kh_gemm_noalloc",
     "kh_gemm_noalloc_max_bytes", "kh_save", "kh_load_config", "kh_load",
 ]
 
@@ -38,7 +39,7 @@ class KhConfig(ctypes.Structure):
         ("p_max", ctypes.c_int), ("svd_oversample", ctypes.c_int), ("svd_iters_cold", ctypes.c_int),
         ("svd_iters_warm", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int), ("svd_cut", ctypes.c_double),
         ("als_tol", ctypes.c_double), ("als_max_iter", ctypes.c_int), ("als_reg", ctypes.c_double),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("proj_fp64", ctypes.c_int),
     ]
 
 
@@ -75,11 +76,13 @@ def load_library(path=LIB_PATH):
         "ctm_metric": (I, [P, I, P]),
         "ctm_kappa": (I, [P, I, dp]),
         "ctm_expval": (I, [P, I, dp, I, dp]),
+        "ctm_correlation_length": (I, [P, I, I, I, D, dp]),
         "eefu_apply_gate": (I, [P, I, dp, I, I, D, dp]),
         "observables": (I, [P, dp, D, D, I, I, D, dp]),
         "kh_bond_hamiltonian": (I, [I, D, D, D, D, dp]),
         "kh_gate": (I, [dp, D, dp]),
         "eefu_trotter_step": (I, [P, D, dp, D, D, D, I, I, D, dp]),
+        "eefu_evolve": (I, [P, D, dp, D, D, D, I, I, I, I, D, I, I, D, dp]),
         "kh_launch_count": (ctypes.c_ulonglong, []),
         "kh_profile": (I, [P, I, dp]),
         "kh_selftest_bytes": (S, [I, I, I]),
@@ -87,6 +90,7 @@ def load_library(path=LIB_PATH):
         "kh_selftest_symeig": (I, [I, I, P, P, P, P, S, P]),
         "kh_selftest_svd": (I, [I, I, P, P, P, P, P, S, P]),
         "kh_selftest_orth": (I, [I, I, I, D, P, P, P, S, P]),
+        "kh_selftest_svd_refined": (I, [I, P, P, P, P, P, S, P]),
         "kh_selftest_fp64_newton": (I, [I, P, P, P]),
         "kh_gemm_noalloc": (I, [I, I, I, I, P, P, P, P]),
         "kh_gemm_noalloc_max_bytes": (S, []),
@@ -157,6 +161,24 @@ def selftest_svd(X, prec="fp64"):
                                ctypes.c_void_p(base), nb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if st != KH_OK:
         raise KhError(st, "kh_selftest_svd")
+    return S, L, Q
+
+
+def selftest_svd_refined(X):
+    """(S, L, Q) with X Q = L S: FP32 one-sided Jacobi plus three FP64 Newton
+    refinement steps (the FP64-projector option's small SVD)."""
+    import torch
+    k = X.shape[0]
+    S = torch.empty(k, dtype=torch.float64, device=X.device)
+    L = torch.empty((k, k), dtype=torch.float64, device=X.device)
+    Q = torch.empty((k, k), dtype=torch.float64, device=X.device)
+    nb = lib().kh_selftest_bytes(k, k, k)
+    scr = torch.empty(nb + 256, dtype=torch.uint8, device=X.device)
+    base = (scr.data_ptr() + 255) // 256 * 256
+    st = lib().kh_selftest_svd_refined(k, _tptr(X.contiguous()), _tptr(S), _tptr(L), _tptr(Q),
+                                       ctypes.c_void_p(base), nb, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_svd_refined")
     return S, L, Q
 
 
@@ -414,6 +436,13 @@ class Context:
         return v
 
     # ---- eeFU
+    def ctm_correlation_length(self, slot, direction=0, max_iter=400, tol=1e-6):
+        """(xi, |l2|/|l1|, iterations) of slot's channel transfer matrix."""
+        out = np.zeros(3)
+        o, op = _dptr(out)
+        self._check(lib().ctm_correlation_length(self._ctx, slot, direction, max_iter, tol, op))
+        return float(o[0]), float(o[1]), int(o[2])
+
     def eefu_apply_gate(self, gamma, gate, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12, info=True):
         g, gp = _dptr(gate)
         if info:
@@ -438,6 +467,23 @@ class Context:
         self._check(lib().eefu_trotter_step(self._ctx, J, kp, hA, hB, dbeta, ctm_max_sweeps, ctm_min_sweeps,
                                             ctm_tol, None))
         return None
+
+    TRAJ_KEYS = ["beta", "E_site", "Hx", "Hy", "Hz", "Ax", "Ay", "Az", "Bx", "By", "Bz", "trunc", "C"]
+
+    def evolve(self, J, K_xyz, dbeta, n_steps, measure_every=1, hA=0.0, hB=0.0, ctm_max_sweeps=100,
+               ctm_min_sweeps=1, ctm_tol=1e-12, obs_max_sweeps=None, obs_min_sweeps=None, obs_tol=None):
+        """Imaginary-time trajectory: list of dicts (TRAJ_KEYS) per measurement,
+        C the specific heat per site (NaN at the ends of the grid)."""
+        nm = n_steps // measure_every
+        out = np.zeros(max(nm, 1) * len(self.TRAJ_KEYS))
+        o, op = _dptr(out)
+        K, kp = _dptr(np.asarray(K_xyz, dtype=np.float64))
+        st = lib().eefu_evolve(self._ctx, J, kp, hA, hB, dbeta, n_steps, measure_every, ctm_max_sweeps,
+                               ctm_min_sweeps, ctm_tol, obs_max_sweeps or ctm_max_sweeps,
+                               obs_min_sweeps or ctm_min_sweeps, ctm_tol if obs_tol is None else obs_tol, op)
+        self._check(st)
+        rows = o.reshape(-1, len(self.TRAJ_KEYS))[:nm]
+        return [dict(zip(self.TRAJ_KEYS, r.tolist())) for r in rows]
 
     def observables(self, H_xyz, hA=0.0, hB=0.0, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12):
         H = np.ascontiguousarray(np.stack([np.asarray(h, dtype=np.float64) for h in H_xyz]))

@@ -16,6 +16,8 @@ struct kh_ctx {
 
 namespace {
 
+constexpr int kTrajCols = 13;   // beta, the 10 observables, truncation, C
+
 // NVTX range over one ABI call, named after it (tracing; a no-op unless a
 // tool is attached)
 struct NvtxRange {
@@ -338,6 +340,15 @@ kh_status ctm_kappa(kh_ctx* ctx, int slot, double* kappa) {
     });
 }
 
+kh_status ctm_correlation_length(kh_ctx* ctx, int slot, int direction, int max_iter, double tol,
+                                 double* host_out) {
+    KH_RANGE();
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !host_out || max_iter < 1 || !(tol >= 0.0)) kh::fail(KH_EINVAL, "bad arguments");
+        ctx->eng->correlation_length(slot, direction, max_iter, tol, host_out);
+    });
+}
+
 kh_status ctm_expval(kh_ctx* ctx, int slot, const double* ops, int n_ops, double* vals) {
     KH_RANGE();
     return guard(ctx, [&] {
@@ -400,6 +411,52 @@ kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA
             }
         }
         if (info) { info[0] = worst; info[1] = sweeps; info[2] = iters; info[3] = tr; }
+    });
+}
+
+kh_status eefu_evolve(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta, int n_steps,
+                      int measure_every, int mx, int mn, double tol, int obs_mx, int obs_mn, double obs_tol,
+                      double* traj) {
+    KH_RANGE();
+    return guard(ctx, [&] {
+        if (!Kxyz || !traj || mx < 1 || obs_mx < 1 || n_steps < 1 || measure_every < 1 || !(dbeta > 0.0))
+            kh::fail(KH_EINVAL, "bad arguments");
+        static const int order[5] = {0, 1, 2, 1, 0};
+        const double taus[5] = {dbeta / 4, dbeta / 4, dbeta / 2, dbeta / 4, dbeta / 4};
+        double H3[48], G[5][16];
+        for (int g = 0; g < 3; ++g) bond_h(g, J, Kxyz[g], 0.0, 0.0, H3 + 16 * g);
+        for (int l = 0; l < 5; ++l) {
+            double H[16];
+            const int g = order[l];
+            bond_h(g, J, Kxyz[g], g == 2 ? hA : 0.0, g == 2 ? hB : 0.0, H);
+            gate_from_h(H, taus[l], G[l]);
+        }
+        const int nm = n_steps / measure_every;
+        const double beta0 = ctx->eng->beta;
+        for (int n = 1; n <= n_steps; ++n) {
+            for (int l = 0; l < 5; ++l) ctx->eng->apply_gate(order[l], G[l], mx, mn, tol, nullptr);
+            ctx->eng->beta += dbeta;
+            if (n % measure_every == 0) {
+                double* row = traj + (long long)(n / measure_every - 1) * kTrajCols;
+                double out[12];
+                ctx->eng->observables(H3, hA, hB, obs_mx, obs_mn, obs_tol, out);
+                row[0] = beta0 + n * dbeta;
+                for (int i = 0; i < 10; ++i) row[1 + i] = out[i];
+                row[11] = out[10];
+            }
+        }
+        // C = dE/dT = -beta^2 dE/dbeta by central differences on the uniform
+        // measurement grid; NaN at the two ends
+        for (int i = 0; i < nm; ++i) {
+            double* row = traj + (long long)i * kTrajCols;
+            if (i == 0 || i == nm - 1) {
+                row[12] = NAN;
+                continue;
+            }
+            const double* lo = row - kTrajCols;
+            const double* hi = row + kTrajCols;
+            row[12] = -row[0] * row[0] * (hi[1] - lo[1]) / (hi[0] - lo[0]);
+        }
     });
 }
 

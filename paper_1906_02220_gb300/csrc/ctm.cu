@@ -31,6 +31,7 @@ void validate(const kh_config& c) {
         fail(KH_EINVAL, "bad subspace iteration settings");
     if (c.jacobi_max_sweeps < 1) fail(KH_EINVAL, "jacobi_max_sweeps < 1");
     if (!(c.svd_cut >= 0.0) || !(c.als_reg >= 0.0) || c.als_max_iter < 0) fail(KH_EINVAL, "bad tolerances");
+    if (c.proj_fp64 != 0 && c.proj_fp64 != 1) fail(KH_EINVAL, "proj_fp64 must be 0 or 1");
 }
 
 Dims make_dims(const kh_config& c, bool fp64) {
@@ -43,7 +44,7 @@ Dims make_dims(const kh_config& c, bool fp64) {
     d.pmax = c.p_max;
     d.nslots = c.n_slots;
     d.dl_alloc = d.d2 <= 2 * c.p_max;
-    int kmax = fp64 ? 112 : 160;
+    int kmax = (fp64 || c.proj_fp64) ? 112 : 160;      // the FP64 one-CTA Jacobi limit
     if (d.n <= kmax) {
         d.kk = d.n;
         d.full = true;
@@ -161,6 +162,15 @@ void Engine<T>::carve_lane(Carver& cv) {
     mN4 = cv.take<T>((long long)d.D4 * d.D4);
     N = cv.take<double>((long long)d.D4 * d.D4);
     dwork = cv.take<double>(4 * E1 + 16LL * d.D4 + 64);
+    if (proj64()) {
+        Hd = cv.take<double>(kk * kk);
+        Ld = cv.take<double>(kk * kk);
+        Qd = cv.take<double>(kk * kk);
+        Lr = cv.take<double>(kk * kk);
+        Qr = cv.take<double>(kk * kk);
+        Sd = cv.take<double>(kk);
+        Rw = cv.take<double>(svd_refine_scratch((int)kk));
+    }
     sk_elems = 16LL * n * (kk > d.chi ? kk : d.chi);
     skbuf = cv.take<T>(sk_elems);
 }
@@ -262,12 +272,15 @@ __global__ void rand_kernel(T* V, long long tot, uint64_t seed, uint64_t stream)
 // KT x KT register tile G[ti + 16 a][tj + 16 b] and accumulates it over the
 // chunk (in T), then adds it to the FP64 result.
 template <typename T, int KT>
-__global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int n, int k, double* __restrict__ G,
-                                                   int rows_per) {
+__global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, const T* __restrict__ Z2, int n, int k,
+                                                   double* __restrict__ G, int rows_per) {
     extern __shared__ unsigned char smem_raw[];
-    T* Ys = reinterpret_cast<T*>(smem_raw);   // rows_per x k
+    T* Ys = reinterpret_cast<T*>(smem_raw);   // rows_per x k (Z), then rows_per x k (Z2) when given
+    T* Ys2 = Z2 ? Ys + rows_per * k : Ys;
     const int r0 = blockIdx.x * rows_per, nr = min(rows_per, n - r0);
     for (int e = threadIdx.x; e < nr * k; e += blockDim.x) Ys[e] = Z[(long long)r0 * k + e];
+    if (Z2)
+        for (int e = threadIdx.x; e < nr * k; e += blockDim.x) Ys2[e] = Z2[(long long)r0 * k + e];
     __syncthreads();
     const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
     T acc[KT][KT];
@@ -277,12 +290,13 @@ __global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int 
         for (int b = 0; b < KT; ++b) acc[a][b] = T(0);
     for (int r = 0; r < nr; ++r) {
         const T* y = Ys + r * k;
+        const T* y2 = Ys2 + r * k;
         T yi[KT], yj[KT];
 #pragma unroll
         for (int a = 0; a < KT; ++a) {
             const int i = ti + 16 * a, j = tj + 16 * a;
             yi[a] = i < k ? y[i] : T(0);
-            yj[a] = j < k ? y[j] : T(0);
+            yj[a] = j < k ? y2[j] : T(0);
         }
 #pragma unroll
         for (int a = 0; a < KT; ++a)
@@ -298,22 +312,32 @@ __global__ void __launch_bounds__(256) gram_kernel(const T* __restrict__ Z, int 
         }
 }
 
+// G = Z^T Z2 (Z2 = Z when null), k x k, accumulated in T over chunks of 16
+// rows and in FP64 across chunks.
 template <typename T>
-void gram(const T* Z, int n, int k, double* dG, cudaStream_t st) {
+void gram(const T* Z, int n, int k, double* dG, cudaStream_t st, const T* Z2 = nullptr) {
     if (k > 160) fail(KH_EINVAL, "gram: k > 160");
     KH_CUDA(cudaMemsetAsync(dG, 0, sizeof(double) * k * k, st));
-    int rows_per = (int)((48 * 1024) / (sizeof(T) * k));     // stay within the default shared-memory limit
+    const int nmat = Z2 ? 2 : 1;
+    int rows_per = (int)((48 * 1024) / (sizeof(T) * k * nmat));   // stay within the default shared-memory limit
     if (rows_per > 16) rows_per = 16;
     const int grid = (n + rows_per - 1) / rows_per;
-    const size_t sm = sizeof(T) * rows_per * k;
+    const size_t sm = sizeof(T) * rows_per * k * nmat;
     switch ((k + 15) / 16) {
-#define KH_GRAM(KT) case KT: gram_kernel<T, KT><<<grid, 256, sm, st>>>(Z, n, k, dG, rows_per); break;
+#define KH_GRAM(KT) case KT: gram_kernel<T, KT><<<grid, 256, sm, st>>>(Z, Z2, n, k, dG, rows_per); break;
         KH_GRAM(1) KH_GRAM(2) KH_GRAM(3) KH_GRAM(4) KH_GRAM(5)
         KH_GRAM(6) KH_GRAM(7) KH_GRAM(8) KH_GRAM(9) KH_GRAM(10)
 #undef KH_GRAM
     }
     KH_LAUNCHED();
 }
+
+template <typename T>
+void gram2(const T* A, const T* B, int n, int k, double* dG, cudaStream_t st) {
+    gram<T>(A, n, k, dG, st, B);
+}
+template void gram2<float>(const float*, const float*, int, int, double*, cudaStream_t);
+template void gram2<double>(const double*, const double*, int, int, double*, cudaStream_t);
 
 // max that keeps a NaN once it has seen one (fmax drops NaN operands): a
 // non-finite environment must reach the host's spectrum check
@@ -323,8 +347,8 @@ __device__ __forceinline__ double nan_max(double a, double b) { return (b > a ||
 // weight.  One block; every element handled by its own thread (a serial loop
 // here would pay a global-memory round trip per value).  A NaN singular value
 // is passed on to the spectrum and the discarded weight (not clamped to 0).
-template <typename T>
-__global__ void finalize_spectrum_kernel(const T* sv, int k, int chi, double cut, const double* normM2,
+template <typename TS, typename T>
+__global__ void finalize_spectrum_kernel(const TS* sv, int k, int chi, double cut, const double* normM2,
                                          double* spec, T* isq, double* trunc) {
     __shared__ double red[32];
     const int nkeep = min(chi, k);
@@ -375,10 +399,13 @@ __global__ void delta_kernel(const double* spec, double* prev, int chi, int prev
         if (lane == 0) inv[w] = s > 0.0 ? rsqrt(s) : 1.0;
     }
     __syncthreads();
+    // the previous spectra count only when they belong to the same run: after
+    // a reset (prev_valid == 0) they may hold anything, a NaN of a failed run
+    // included, and only the current spectra can make the change NaN
     double d = 0.0;
     for (int e = t; e < 4 * chi; e += blockDim.x) {
         double v = spec[e] * inv[e / chi];
-        d = nan_max(d, fabs(v - prev[e]));
+        d = nan_max(d, prev_valid ? fabs(v - prev[e]) : (v != v ? v : 0.0));
         prev[e] = v;
     }
     for (int o = 16; o > 0; o >>= 1) d = nan_max(d, __shfl_xor_sync(0xffffffffu, d, o));
@@ -745,6 +772,27 @@ __global__ void add_kernel(const T* a, T* b, long long n) {
         b[i] += a[i];
 }
 
+// The small SVD of the projector (X Q = L S, X k x k): in T by the one-sided
+// Jacobi kernel, or, with proj_fp64 in a single-precision engine, by the FP64
+// kernel on an FP64 copy of X (S stays in Sd for the spectrum and S^-1/2; L
+// and Q are rounded to T for the basis products).
+template <typename T>
+void Engine<T>::rr_svd(const T* X, int k, T* L, T* Qm, double jtol, int nrel, const double* Xd) {
+    svd_jacobi<T>(X, k, Sk, L, Qm, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, nrel);
+    if (proj64()) {
+        // FP64 matrix: the FP64-accumulated one when given, else X widened
+        if (!Xd) {
+            cast<T, double>(X, Hd, (long long)k * k, st);
+            Xd = Hd;
+        }
+        cast<T, double>(L, Ld, (long long)k * k, st);
+        cast<T, double>(Qm, Qd, (long long)k * k, st);
+        svd_refine_fp64(Xd, k, Ld, Qd, Sd, Lr, Qr, Rw, 1e-5, st);
+        cast<double, T>(Lr, L, (long long)k * k, st);
+        cast<double, T>(Qr, Qm, (long long)k * k, st);
+    }
+}
+
 // Top-chi SVD of M = Mt^T, written into (Sk, V = Z1, U = Uf).
 //  full mode (n within the Jacobi limit): one-sided Jacobi SVD of Y = M V_w
 //    (V_w the previous right vectors, identity when cold): Y Q = L S, so
@@ -758,7 +806,8 @@ template <typename T>
 void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
     const int n = dm.n, k = dm.kk, chi = dm.chi;
     const double cut = cfg.svd_cut;
-    const double jtol = sizeof(T) == 8 ? 1e-14 : 2e-6;   // a few times the rounding floor sqrt(k) eps
+    // a few times the rounding floor sqrt(k) eps of the solver's arithmetic
+    const double jtol = sizeof(T) == 8 ? 1e-14 : 2e-6;
     const T* Qa = Q[0];
     const T* Qb = Q[1];
     half_system_product(n);
@@ -776,7 +825,7 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         }
         gemm_rm<T>(n, n, n, Mt, true, Vw, false, Y1, st);                      // Y = M V_w
         prof_begin(7);
-        svd_jacobi<T>(Y1, n, Sk, Uf, Lk, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, chi + 8);   // Y Q = L S
+        rr_svd(Y1, n, Uf, Lk, jtol, chi + 8);                                  // Y Q = L S
         prof_end(7, 0.0);
         gemm_rm<T>(n, n, n, Vw, false, Lk, false, Z1, st);                     // V = V_w Q
         gemm_rm<T>(n, n, n, Z1, true, Z1, false, Y1, st);                      // V^T V
@@ -829,9 +878,14 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         // triangular factor with graded rows, so G's columns (H's rows) are
         // nearly orthogonal already: the one-sided Jacobi of G is the
         // QR-preconditioned Jacobi SVD and needs fewer sweeps than that of H.
-        gemm_rm<T>(k, k, n, Z2, true, Vo, false, Hk, st, T(1), T(0), nullptr, skbuf, sk_elems);
+        if (proj64()) {        // FP64-accumulated G for the FP64 refinement, its rounding for the Jacobi
+            gram2<T>(Z2, Vo, n, k, Hd, st);
+            cast<double, T>(Hd, Hk, (long long)k * k, st);
+        } else {
+            gemm_rm<T>(k, k, n, Z2, true, Vo, false, Hk, st, T(1), T(0), nullptr, skbuf, sk_elems);
+        }
         prof_begin(7);
-        svd_jacobi<T>(Hk, k, Sk, Lk, Qk, cfg.jacobi_max_sweeps, jtol, 0.0, st, flags + 48, chi + 8);   // G Q = L S
+        rr_svd(Hk, k, Lk, Qk, jtol, chi + 8, proj64() ? Hd : nullptr);         // G Q = L S
         prof_end(7, 0.0);
         gemm_rm<T>(n, k, k, Vo, false, Qk, false, Z1, st);                     // right vectors of M: V' Q
         gemm_rm<T>(n, k, k, U, false, Lk, false, Uf, st);                      // left vectors of M: U L
@@ -844,8 +898,12 @@ void Engine<T>::projector(Slot<T>& sl, int dir, int slot_id) {
         KH_LAUNCHED();
         sl.warm[dir] = true;
     }
-    finalize_spectrum_kernel<T><<<1, 128, 0, st>>>(Sk, k, chi, cut, normM2, sl.spec + (long long)dir * chi, isq,
-                                                  sl.trunc + dir);
+    if (proj64())
+        finalize_spectrum_kernel<double, T><<<1, 128, 0, st>>>(Sd, k, chi, cut, normM2, sl.spec + (long long)dir * chi,
+                                                               isq, sl.trunc + dir);
+    else
+        finalize_spectrum_kernel<T, T><<<1, 128, 0, st>>>(Sk, k, chi, cut, normM2, sl.spec + (long long)dir * chi,
+                                                          isq, sl.trunc + dir);
     KH_LAUNCHED();
     const int nkeep = chi < k ? chi : k;
     if (nkeep < chi) {
@@ -1270,7 +1328,7 @@ template <typename T>
 void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cudaStream_t st, bool sorted,
                    double ns_tol, double defer) {
     if (k > jacobi_kmax<T>()) fail(KH_EINVAL, "cholqr: k beyond limit");
-    size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
+    const size_t sm = (size_t)2 * k * (k | 1) * sizeof(T);
     static std::atomic<size_t> granted[kMaxDevices] = {};
     smem_opt_in(cholqr_kernel<T>, sm, granted);
     cholqr_kernel<T><<<1, 1024, sm, st>>>(dG, k, cut_abs, tau, X, sorted ? 1 : 0, ns_tol, defer);

@@ -89,6 +89,7 @@ struct EngineBase {
     }
     kh_config cfg;
     Dims dm;
+    double beta = 0.0;        // inverse temperature reached by eefu_evolve from the initial state
     cudaStream_t st = 0;
     std::string err;
     virtual void set_state(const double* A, const double* B) = 0;
@@ -105,6 +106,7 @@ struct EngineBase {
     virtual void metric(int slot, double* N_out) = 0;
     virtual double kappa(int slot) = 0;
     virtual void expval(int slot, const double* ops, int n_ops, double* vals) = 0;
+    virtual void correlation_length(int slot, int dir, int max_iter, double tol, double* out) = 0;
     virtual void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) = 0;
     virtual void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                              double* out) = 0;
@@ -140,7 +142,11 @@ static_assert(DscrOff::kStage + 16 * 16 * 16 <= DscrOff::kExpvalOut && DscrOff::
                   DscrOff::kNorms + 3 <= DscrOff::kKappa && DscrOff::kKappa + 4 <= DscrOff::kGram,
               "dscr regions overlap");
 
-#define KH_LANE_DPTRS(X) X(dscr) X(N) X(dwork)
+// FP64 scratch of the projector's Rayleigh-Ritz SVD in the single-precision
+// engines with proj_fp64: the matrix Hd, the single-precision factors Ld, Qd,
+// the refined factors Lr, Qr (kk x kk each), singular values Sd (kk) and the
+// refinement's work Rw (svd_refine_scratch(kk)).
+#define KH_LANE_DPTRS(X) X(dscr) X(N) X(dwork) X(Hd) X(Ld) X(Qd) X(Sd) X(Lr) X(Qr) X(Rw)
 template <typename T>
 struct Lane {
 #define KH_DECL(f) T* f = nullptr;
@@ -175,6 +181,9 @@ struct Engine : EngineBase {
     double *N = nullptr, *Tp = nullptr, *A2 = nullptr, *B2 = nullptr, *XA = nullptr, *R = nullptr,
            *S = nullptr, *Xs = nullptr, *Tm = nullptr, *Gt = nullptr, *Wt = nullptr, *Lt = nullptr,
            *Xmat = nullptr, *cost = nullptr, *dwork = nullptr;
+    double *Hd = nullptr, *Ld = nullptr, *Qd = nullptr, *Sd = nullptr, *Lr = nullptr, *Qr = nullptr, *Rw = nullptr;
+    // projector factorisations in FP64 while the contractions run in T = float
+    bool proj64() const { return sizeof(T) == 4 && cfg.proj_fp64 != 0; }
     float *Gtf = nullptr, *Wtf = nullptr, *Ltf = nullptr;
     int* flags = nullptr;
     int* tc_err = nullptr;     // tensor-core kernels' time-out flag
@@ -222,6 +231,7 @@ struct Engine : EngineBase {
                       const std::vector<int>& order);
     void projector(Slot<T>& sl, int dir, int slot_id);
     void orth(const T* Y, int n, int k, T* Uo);
+    void rr_svd(const T* X, int k, T* L, T* Qm, double jtol, int nrel, const double* Xd = nullptr);
     void absorb(Slot<T>& sl, int s);
     void move(Slot<T>& sl, int s, int slot_id);
     void compute_metric(Slot<T>& sl, double* N_out);
@@ -251,6 +261,7 @@ struct Engine : EngineBase {
     void metric(int slot, double* N_out) override;
     double kappa(int slot) override;
     void expval(int slot, const double* ops, int n_ops, double* vals) override;
+    void correlation_length(int slot, int dir, int max_iter, double tol, double* out) override;   // xi.cu
     void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) override;
     void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                      double* out) override;
@@ -274,6 +285,15 @@ void tc_split(const float* x, float* hi, float* lo, long long n, cudaStream_t st
 // ordered CholQR2 (ctm.cu); see Engine::orth.
 template <typename T>
 void cholqr2(const T* Y, int n, int k, double cut, T* tmp, T* Xk, double* dG, T* Uo, cudaStream_t st);
+// G = A^T B (n x k each, T) accumulated in FP64 across row chunks (ctm.cu)
+template <typename T>
+void gram2(const T* A, const T* B, int n, int k, double* dG, cudaStream_t st);
+
+// Three FP64 Newton steps on a single-precision SVD G Q ~ L diag(s) of a k x k
+// FP64 matrix G (refine.cu): refined factors to Lo, Qo, singular values to s.
+size_t svd_refine_scratch(int k);
+void svd_refine_fp64(const double* G, int k, const double* L, const double* Q, double* s, double* Lo, double* Qo,
+                     double* work, double rel_gap, cudaStream_t st);
 
 Dims make_dims(const kh_config& c, bool fp64);
 void validate(const kh_config& c);

@@ -492,138 +492,102 @@ void cholqr_factor(const double* dG, int k, double cut_abs, double tau, T* X, cu
 __device__ __forceinline__ float chol_recip(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double chol_recip(double x) { return 1.0 / x; }
 
-// Right-looking Cholesky with one barrier per column (unscaled columns, the
-// scaling applied at the end), then the inverse of the triangular factor by
-// recursive doubling: the 8 x 8 diagonal blocks are inverted in parallel,
-// and at each level pairs of already inverted diagonal blocks A (above) and
-// C (below) are joined by Li_CA = -Li_CC (L_CA Li_AA), two parallel products
-// per level, the intermediate kept in the unused upper triangle of L.
+// Shared state of the two CholQR factor kernels (shared memory).
 template <typename T>
-__global__ void __launch_bounds__(1024)
-cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted,
-              double ns_tol, double defer) {
-    constexpr int KM = sizeof(T) == 8 ? 112 : 160;   // largest k
-    extern __shared__ unsigned char smem_raw[];
-    const int ld = k | 1;                          // odd row stride: conflict-free column walks
-    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x ld, row-major (lower triangle: L)
-    T* Li = Lm + k * ld;                           // k x ld: L^-1
-    __shared__ T s_inv[KM], s_diag[KM], s_rs[KM];
-    __shared__ int s_perm[KM];
-    __shared__ int s_keep[KM];
-    __shared__ T s_max;
+struct CholShared {
+    static constexpr int KM = sizeof(T) == 8 ? 112 : 160;   // largest k
+    T inv[KM], diag[KM], rs[KM];
+    int perm[KM];
+    int keep[KM];
+    T mx;
+};
+
+// Prologue of the factor kernels: column norms, the Newton-Schulz shortcut
+// (returns true when X was written that way), the order (by norm when
+// sorted), and the scaled, permuted Gram matrix into Lm (k x ld); Li zeroed.
+template <typename T>
+__device__ bool cholqr_prologue(const double* __restrict__ G, int k, double cut_abs, T* __restrict__ X, int sorted,
+                                double ns_tol, T* Lm, T* Li, int ld, CholShared<T>& sh) {
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const T tauT = (T)tau;
-    for (int j = tid; j < k; j += nt) s_diag[j] = (T)fmax(G[(long long)j * k + j], 0.0);
+    for (int j = tid; j < k; j += nt) sh.diag[j] = (T)fmax(G[(long long)j * k + j], 0.0);
     __syncthreads();
     if (ns_tol > 0.0) {
         // Gram of the nonzero columns close to the identity: one Newton-Schulz step
         T dev = T(0);
         for (int e = tid; e < k * k; e += nt) {
             const int i = e / k, j = e % k;
-            if (s_diag[i] > T(0) && s_diag[j] > T(0)) dev = fmax(dev, fabs((T)G[e] - (i == j ? T(1) : T(0))));
+            if (sh.diag[i] > T(0) && sh.diag[j] > T(0)) dev = fmax(dev, fabs((T)G[e] - (i == j ? T(1) : T(0))));
         }
         for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-        if (lane == 0) s_inv[warp] = dev;          // s_inv reused as the reduction buffer (nw <= 32)
+        if (lane == 0) sh.inv[warp] = dev;          // inv reused as the reduction buffer (nw <= 32)
         __syncthreads();
         if (tid == 0) {
             T m = T(0);
-            for (int w = 0; w < nw; ++w) m = fmax(m, s_inv[w]);
-            s_max = m;
+            for (int w = 0; w < nw; ++w) m = fmax(m, sh.inv[w]);
+            sh.mx = m;
         }
         __syncthreads();
-        if (s_max < (T)ns_tol) {
+        if (sh.mx < (T)ns_tol) {
             for (int e = tid; e < k * k; e += nt) {
                 const int i = e / k, j = e % k;
-                const bool live = s_diag[i] > T(0) && s_diag[j] > T(0);
+                const bool live = sh.diag[i] > T(0) && sh.diag[j] > T(0);
                 X[e] = live ? ((i == j ? T(1.5) : T(0)) - T(0.5) * (T)G[e]) : T(0);
             }
-            return;
+            return true;
         }
         __syncthreads();
     }
     if (warp == 0) {
         T m = T(0);
-        for (int j = lane; j < k; j += 32) m = fmax(m, s_diag[j]);
+        for (int j = lane; j < k; j += 32) m = fmax(m, sh.diag[j]);
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) s_max = sqrt(m);
+        if (lane == 0) sh.mx = sqrt(m);
     }
     __syncthreads();
     const T cutT = (T)cut_abs;
     for (int j = tid; j < k; j += nt) {
-        const T dj = s_diag[j];
+        const T dj = sh.diag[j];
         const T nj = sqrt(dj);
-        s_inv[j] = (s_max > T(0) && nj > cutT * s_max) ? T(1) / nj : T(0);
+        sh.inv[j] = (sh.mx > T(0) && nj > cutT * sh.mx) ? T(1) / nj : T(0);
         int rank = j;
         if (sorted) {
             rank = 0;
-            for (int i = 0; i < k; ++i) rank += (s_diag[i] > dj) || (s_diag[i] == dj && i < j);
+            for (int i = 0; i < k; ++i) rank += (sh.diag[i] > dj) || (sh.diag[i] == dj && i < j);
         }
-        s_perm[rank] = j;
+        sh.perm[rank] = j;
     }
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {
         int a = e / k, b = e % k;
-        int pa = s_perm[a], pb = s_perm[b];
-        Lm[a * ld + b] = (T)G[(long long)pa * k + pb] * s_inv[pa] * s_inv[pb];
+        int pa = sh.perm[a], pb = sh.perm[b];
+        Lm[a * ld + b] = (T)G[(long long)pa * k + pb] * sh.inv[pa] * sh.inv[pb];
         Li[a * ld + b] = T(0);
     }
     __syncthreads();
-    // Cholesky: step j leaves the Schur-complement entries a_ij (i > j) in
-    // column j and subtracts a_ij a_cj / d_j from the trailing block; a pivot
-    // d_j <= tau drops direction j (no update, zero column).  A pivot in
-    // (tau, defer) is first rotated to the end of the order (positions
-    // j+1, ..., k-1 move up by one), each column at most once: the nd deferred
-    // columns occupy the last nd positions.
-    const T deferT = (T)defer;
-    int nd = 0;
-    for (int j = 0; j < k;) {
-        const T d = Lm[j * ld + j];              // same value in every thread
-        if (d > tauT && d < deferT && j < k - nd) {
-            // new position a holds old position src(a): a (a < j), a + 1 (j <= a < k-1), j (a = k-1).
-            // Rows j.. of the lower triangle are gathered into Li, then copied back.
-            const int rows = k - j;
-            int pnew = 0;
-            if (tid < rows) pnew = s_perm[tid + 1 < rows ? j + tid + 1 : j];
-            for (int e = tid; e < rows * k; e += nt) {
-                const int a = j + e / k, b = e % k;
-                if (b > a) continue;
-                const int pa = a < k - 1 ? a + 1 : j;
-                const int pb = b < j ? b : (b < k - 1 ? b + 1 : j);
-                Li[a * ld + b] = pa >= pb ? Lm[pa * ld + pb] : Lm[pb * ld + pa];
-            }
-            __syncthreads();
-            for (int e = tid; e < rows * k; e += nt) {
-                const int a = j + e / k, b = e % k;
-                if (b > a) continue;
-                Lm[a * ld + b] = Li[a * ld + b];
-                Li[a * ld + b] = T(0);
-            }
-            if (tid < rows) s_perm[j + tid] = pnew;
-            __syncthreads();
-            ++nd;
-            continue;
-        }
-        if (d > tauT) {
-            const T rd = chol_recip(d);
-            for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
-                const T lij = Lm[i * ld + j] * rd;
-                for (int c = j + 1 + lane; c <= i; c += 32) Lm[i * ld + c] -= lij * Lm[c * ld + j];
-            }
-        }
-        __syncthreads();
-        ++j;
-    }
+    return false;
+}
+
+// Epilogue: Lm holds the Schur-complement entries a_ij (i > j) and pivots
+// d_j = a_jj; pivots <= tau are dropped directions.  Scales the factor,
+// inverts it (8 x 8 diagonal blocks in parallel, then recursive doubling:
+// pairs of inverted diagonal blocks A (above) and C (below) are joined by
+// Li_CA = -Li_CC (L_CA Li_AA), two parallel products per level, the
+// intermediate kept in the unused upper triangle of L) and writes X.
+template <typename T>
+__device__ void cholqr_epilogue(int k, double tau, T* __restrict__ X, T* Lm, T* Li, int ld, CholShared<T>& sh) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const T tauT = (T)tau;
     for (int j = tid; j < k; j += nt) {
         const T d = Lm[j * ld + j];
         const bool keep = d > tauT;
-        s_keep[j] = keep;
-        s_rs[j] = keep ? T(1) / sqrt(d) : T(0);
+        sh.keep[j] = keep;
+        sh.rs[j] = keep ? T(1) / sqrt(d) : T(0);
     }
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {       // L_ij = a_ij / sqrt(d_j); unit diagonal for dropped j
         int i = e / k, j = e % k;
-        if (i > j) Lm[i * ld + j] *= s_rs[j];
-        else if (i == j) Lm[i * ld + i] = s_keep[i] ? sqrt(Lm[i * ld + i]) : T(1);
+        if (i > j) Lm[i * ld + j] *= sh.rs[j];
+        else if (i == j) Lm[i * ld + i] = sh.keep[i] ? sqrt(Lm[i * ld + i]) : T(1);
     }
     __syncthreads();
     // diagonal 8 x 8 blocks of L^-1: lane c < 8 of warp w inverts column c of block w
@@ -687,10 +651,73 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
     // X[perm a][b] = inv[perm a] * Li[b][a]   (Q = Y_s L^-T; dropped b give zero columns)
     for (int e = tid; e < k * k; e += nt) {
         int a = e / k, b = e % k;
-        int pa = s_perm[a];
-        X[(long long)pa * k + b] = s_keep[b] ? s_inv[pa] * Li[b * ld + a] : T(0);
+        int pa = sh.perm[a];
+        X[(long long)pa * k + b] = sh.keep[b] ? sh.inv[pa] * Li[b * ld + a] : T(0);
     }
 }
+
+// Right-looking Cholesky with one barrier per column (unscaled columns, the
+// scaling applied at the end) and pivot deferral (see cholqr_factor).
+template <typename T>
+__global__ void __launch_bounds__(1024)
+cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T* __restrict__ X, int sorted,
+              double ns_tol, double defer) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ CholShared<T> sh;
+    const int ld = k | 1;                          // odd row stride: conflict-free column walks
+    T* Lm = reinterpret_cast<T*>(smem_raw);       // k x ld, row-major (lower triangle: L)
+    T* Li = Lm + k * ld;                           // k x ld: L^-1
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    if (cholqr_prologue<T>(G, k, cut_abs, X, sorted, ns_tol, Lm, Li, ld, sh)) return;
+    const T tauT = (T)tau;
+    // Cholesky: step j leaves the Schur-complement entries a_ij (i > j) in
+    // column j and subtracts a_ij a_cj / d_j from the trailing block; a pivot
+    // d_j <= tau drops direction j (no update, zero column).  A pivot in
+    // (tau, defer) is first rotated to the end of the order (positions
+    // j+1, ..., k-1 move up by one), each column at most once: the nd deferred
+    // columns occupy the last nd positions.
+    const T deferT = (T)defer;
+    int nd = 0;
+    for (int j = 0; j < k;) {
+        const T d = Lm[j * ld + j];              // same value in every thread
+        if (d > tauT && d < deferT && j < k - nd) {
+            // new position a holds old position src(a): a (a < j), a + 1 (j <= a < k-1), j (a = k-1).
+            // Rows j.. of the lower triangle are gathered into Li, then copied back.
+            const int rows = k - j;
+            int pnew = 0;
+            if (tid < rows) pnew = sh.perm[tid + 1 < rows ? j + tid + 1 : j];
+            for (int e = tid; e < rows * k; e += nt) {
+                const int a = j + e / k, b = e % k;
+                if (b > a) continue;
+                const int pa = a < k - 1 ? a + 1 : j;
+                const int pb = b < j ? b : (b < k - 1 ? b + 1 : j);
+                Li[a * ld + b] = pa >= pb ? Lm[pa * ld + pb] : Lm[pb * ld + pa];
+            }
+            __syncthreads();
+            for (int e = tid; e < rows * k; e += nt) {
+                const int a = j + e / k, b = e % k;
+                if (b > a) continue;
+                Lm[a * ld + b] = Li[a * ld + b];
+                Li[a * ld + b] = T(0);
+            }
+            if (tid < rows) sh.perm[j + tid] = pnew;
+            __syncthreads();
+            ++nd;
+            continue;
+        }
+        if (d > tauT) {
+            const T rd = chol_recip(d);
+            for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
+                const T lij = Lm[i * ld + j] * rd;
+                for (int c = j + 1 + lane; c <= i; c += 32) Lm[i * ld + c] -= lij * Lm[c * ld + j];
+            }
+        }
+        __syncthreads();
+        ++j;
+    }
+    cholqr_epilogue<T>(k, tau, X, Lm, Li, ld, sh);
+}
+
 #endif  // KH_JACOBI_KERNEL
 
 }  // namespace kh

@@ -89,6 +89,25 @@ void run_orth(int n, int k, double cut, const double* Y, double* Q, void* scratc
     kh::cast<T, double>(u, Q, (long long)n * k, st);
 }
 
+// FP32 one-sided Jacobi, then one FP64 Newton refinement step (the projector
+// SVD of the FP64-projector option).
+void run_svd_refined(int k, const double* X, double* S, double* L, double* Qm, void* scratch, size_t bytes,
+                     cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    float* x = cv.take<float>((size_t)k * k);
+    float* l = cv.take<float>((size_t)k * k);
+    float* q = cv.take<float>((size_t)k * k);
+    float* sv = cv.take<float>((size_t)k);
+    double* ld = cv.take<double>((size_t)k * k);
+    double* qd = cv.take<double>((size_t)k * k);
+    double* work = cv.take<double>(kh::svd_refine_scratch(k));
+    kh::cast<double, float>(X, x, (long long)k * k, st);
+    kh::svd_jacobi<float>(x, k, sv, l, q, 60, 1e-6, 0.0, st);
+    kh::cast<float, double>(l, ld, (long long)k * k, st);
+    kh::cast<float, double>(q, qd, (long long)k * k, st);
+    kh::svd_refine_fp64(X, k, ld, qd, S, L, Qm, work, 1e-5, st);
+}
+
 __global__ void newton_kernel(const double* __restrict__ x, int n, double* __restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         out[3 * i] = kh::rcp_nr(x[i]);
@@ -166,6 +185,17 @@ kh_status kh_selftest_svd(int prec, int k, const double* X, double* S, double* L
     return run([&] {
         if (prec == KH_FP64) run_svd<double>(k, X, S, L, Qm, scratch, bytes, st);
         else run_svd<float>(k, X, S, L, Qm, scratch, bytes, st);
+        KH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+kh_status kh_selftest_svd_refined(int k, const double* X, double* S, double* L, double* Qm, void* scratch,
+                                  size_t bytes, void* stream) {
+    if (k < 1 || k > 160 || !X || !S || !L || !Qm || !scratch) return KH_EINVAL;
+    if (bytes < kh_selftest_bytes(k, k, k)) return KH_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] {
+        run_svd_refined(k, X, S, L, Qm, scratch, bytes, st);
         KH_CUDA(cudaStreamSynchronize(st));
     });
 }

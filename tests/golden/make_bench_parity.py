@@ -34,6 +34,9 @@ from oracle import eefu  # noqa: E402
 
 CASE = dict(D=4, chi=64, J=0.0, K=1.0, dbeta=0.01, seed=21, svd_cut=1e-6, ctm_tol=1e-10, ctm_max_sweeps=400)
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "bench_parity_D4_chi64.json")
+if len(sys.argv) > 2:                  # python make_bench_parity.py <svd_cut> <output>
+    CASE["svd_cut"] = float(sys.argv[1])
+    OUT = sys.argv[2]
 
 
 def main():

@@ -69,6 +69,21 @@ def test_workspace_sizing_at_the_jacobi_limits(g, D, chi, prec, ok):
     assert (b > 0) == ok
 
 
+@pytest.mark.parametrize("chi,ok", [(96, True), (97, False)])
+def test_fp64_projector_option_takes_the_fp64_limit(g, chi, ok):
+    """With proj_fp64 the single-precision modes factor in FP64, so k =
+    chi + 16 is bounded by the FP64 solver's 112; the FP64 scratch is extra."""
+    import ctypes
+    c = g.default_config(4, chi, "tf32x3", proj_fp64=1)
+    b = g.lib().kh_workspace_bytes(ctypes.byref(c))
+    assert (b > 0) == ok
+    if ok:
+        c0 = g.default_config(4, chi, "tf32x3")
+        assert b > g.lib().kh_workspace_bytes(ctypes.byref(c0))
+    c.proj_fp64 = 2
+    assert g.lib().kh_workspace_bytes(ctypes.byref(c)) == 0
+
+
 @pytest.mark.parametrize("gamma", ["x", "y", "z"])
 def test_host_gates_match_oracle(g, gamma):
     from oracle import model

@@ -96,6 +96,33 @@ def test_one_sided_jacobi_svd(g, prec, k, decades):
     assert np.abs(X @ Q - L * S).max() <= 30 * eps * k * s[0]
 
 
+@pytest.mark.parametrize("k,decades", [(1, 0), (24, 3), (80, 6), (113, 4), (160, 6)])
+def test_fp32_svd_with_fp64_refinement(g, k, decades):
+    """FP32 one-sided Jacobi plus three FP64 Newton steps: singular vectors
+    orthonormal to FP64 rounding, X Q = L S to FP64 rounding where the FP32
+    result already separated the singular values (their gap above ~1e-4 s_1,
+    far beyond the FP32 error ~k 2^-24 s_1), and never worse than the FP32
+    solver elsewhere (pairs whose gap is below 64 times their coupling are only
+    re-orthogonalised)."""
+    import torch
+    rng = np.random.default_rng(3 * k + decades)
+    U, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    s = np.logspace(0, -decades, k)
+    X = (U * s) @ V.T
+    S, L, Q = (t.cpu().numpy() for t in g.selftest_svd_refined(torch.as_tensor(X, device="cuda:0")))
+    eps64, eps32 = 2.3e-16, 1.2e-7
+    assert np.abs(Q.T @ Q - np.eye(k)).max() <= 1e3 * eps64 * k
+    assert np.abs(L.T @ L - np.eye(k)).max() <= 1e3 * eps64 * k
+    ref = np.linalg.svd(X, compute_uv=False)
+    gaps = np.minimum(np.r_[np.inf, -np.diff(ref)], np.r_[-np.diff(ref), np.inf])
+    sep = gaps > 1e-4 * s[0]
+    assert np.abs(S - ref)[sep].max(initial=0.0) <= 1e3 * eps64 * k * s[0]
+    assert np.abs(S - ref).max() <= 30 * eps32 * k * s[0]
+    resid = np.abs(X @ Q - L * S).max(axis=0)
+    assert resid[sep].max(initial=0.0) <= 1e3 * eps64 * k * s[0]
+
+
 def test_fp64_newton_reciprocals_match_ieee(g):
     """The FP64 reciprocal / reciprocal square root / square root used by the
     latency-bound FP64 kernels (Newton-Raphson from FP32 estimates) agree with

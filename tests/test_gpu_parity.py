@@ -440,9 +440,11 @@ def test_small_and_odd_shapes_with_lanes(g, D, chi):
             assert abs(r[key] - ro[key]) < tol * max(1.0, abs(ro[key])), (prec, key, r[key], ro[key])
 
 
-def test_bench_configuration_matches_oracle(g):
+@pytest.mark.parametrize("proj_fp64", [0, 1])
+def test_bench_configuration_matches_oracle(g, proj_fp64):
     """The bench's full size and launch configuration (D = 4, chi = 64, p = 16,
-    3xTF32 contractions, six slots on three lanes) against the oracle's stored
+    3xTF32 contractions, six slots on three lanes; the projector
+    factorisations in FP32 or, proj_fp64 = 1, in FP64) against the oracle's stored
     values (tests/golden/bench_parity_D4_chi64.json, written by
     make_bench_parity.py from oracle/ only): a seeded random state, the z gate
     of a Kitaev step (K = 1, J = 0, dbeta = 0.01) with its CTMRG converged,
@@ -458,7 +460,7 @@ def test_bench_configuration_matches_oracle(g):
     c = gold["case"]
     D, chi = c["D"], c["chi"]
     A, B = kh_inputs.random_site_tensors(D, c["seed"])
-    ctx = g.Context(D, chi, "tf32x3", svd_cut=c["svd_cut"])
+    ctx = g.Context(D, chi, "tf32x3", svd_cut=c["svd_cut"], proj_fp64=proj_fp64)
     ctx.set_state(_t(A), _t(B))
     gate = g.gate(g.bond_hamiltonian("z", c["J"], c["K"]), c["dbeta"] / 2)
     info = ctx.eefu_apply_gate("z", gate, ctm_max_sweeps=400, ctm_min_sweeps=3, ctm_tol=1e-7)
@@ -479,3 +481,89 @@ def test_bench_configuration_matches_oracle(g):
     assert abs(r["trunc"] - ro["trunc"]) < 1e-3 * ro["trunc"] + 1e-5
     del ctx
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_trajectory_specific_heat_of_decoupled_z_dimers(g, prec):
+    """eefu_evolve on the K_z-only model (decoupled z dimers: no Trotter error,
+    D = 2 exact): the energies along the trajectory follow the closed form
+    E(beta) = -(K_z/8) tanh(beta K_z/4), and the library's specific heat is the
+    oracle's central difference of the closed-form energies on the same grid
+    (the finite-difference formula is the same; within 1e-9 relative for FP64,
+    the single-precision energy error over the grid spacing for 3xTF32)."""
+    from oracle import observables
+    Kz, dbeta, n, every = 1.3, 0.05, 12, 2
+    ctx = g.Context(2, 6, prec, svd_cut=CUT[prec])
+    traj = ctx.evolve(0.0, [0.0, 0.0, Kz], dbeta, n, every, ctm_max_sweeps=100,
+                      ctm_tol=1e-12 if prec == "fp64" else 1e-7)
+    assert len(traj) == n // every
+    beta = np.array([r["beta"] for r in traj])
+    assert np.abs(beta - dbeta * every * np.arange(1, n // every + 1)).max() < 1e-12
+    E = np.array([r["E_site"] for r in traj])
+    Eref = exact.kz_only_energy(Kz, beta)
+    etol = 1e-10 if prec == "fp64" else E_TOL
+    assert np.abs(E - Eref).max() < etol
+    b, Cref = observables.specific_heat(beta, Eref)
+    C = np.array([r["C"] for r in traj])
+    assert np.isnan(C[0]) and np.isnan(C[-1])
+    ctol = 2 * etol * beta.max() ** 2 / (2 * dbeta * every)
+    assert np.abs(C[1:-1] - Cref).max() < ctol + 1e-12
+
+
+def test_trajectory_matches_oracle_evolution(g):
+    """eefu_evolve on the Kitaev-Heisenberg model with a bias (D = 2, chi = 8,
+    FP64 path): every measured row (beta, E/site, bond energies, moments) and
+    the specific heat agree with the oracle's trajectory and its central
+    differences."""
+    from oracle import observables
+    J, K = model.couplings(0.3 * np.pi)
+    hA, hB, dbeta, n = 0.2, -0.1, 0.02, 6
+    A, B = kh_inputs.perturbed_product_state(2, seed=5, eps=0.05)
+    st = _oracle_state(2, 8, J, K, A, B, hA=hA, hB=hB, ctm_tol=1e-12, ctm_max_sweeps=300)
+    ref = eefu.evolve(st, dbeta, n, measure_every=1)
+    ctx = g.Context(2, 8, "fp64")
+    ctx.set_state(_t(A), _t(B))
+    traj = ctx.evolve(J, [K, K, K], dbeta, n, 1, hA=hA, hB=hB, ctm_max_sweeps=300, ctm_tol=1e-12)
+    for r, o in zip(traj, ref):
+        assert abs(r["beta"] - o["beta"]) < 1e-12
+        for key in ("E_site", "Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+            assert abs(r[key] - o[key]) < 1e-9 * max(1.0, abs(o[key])), (key, r[key], o[key])
+    _, Cref = observables.specific_heat([o["beta"] for o in ref], [o["E_site"] for o in ref])
+    C = np.array([r["C"] for r in traj])[1:-1]
+    assert np.abs(C - Cref).max() < 1e-9 * 2 * ref[-1]["beta"] ** 2 / (2 * dbeta) + 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("Kh", [0.3, 0.6])
+def test_correlation_length_of_decoupled_chains(g, prec, Kh):
+    """K_v = 0: the rows are independent 1D Ising chains, the environment is
+    exact and the channel transfer matrix reduces to the chain's, whose
+    eigenvalue ratio is tanh K_h: xi_x = -1 / ln tanh K_h (closed form);
+    nothing is correlated along y."""
+    T = exact.ising_peps(Kh, 0.0)
+    ctx = g.Context(2, 8, prec, p_max=2, n_slots=1, svd_cut=CUT[prec])
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 300, 3, 1e-12 if prec == "fp64" else 1e-7, allow_noconv=prec != "fp64")
+    xi, ratio, its = ctx.ctm_correlation_length(0, 0, max_iter=400, tol=1e-10 if prec == "fp64" else 1e-6)
+    want = -1.0 / np.log(np.tanh(Kh))
+    assert abs(xi - want) < (1e-8 if prec == "fp64" else 1e-4) * want, (xi, want, its)
+    xi_y, _, _ = ctx.ctm_correlation_length(0, 1, max_iter=400)
+    assert xi_y < 0.05
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("D,chi,direction", [(2, 8, 0), (2, 12, 1), (3, 6, 0)])
+def test_correlation_length_matches_oracle_on_the_library_environment(g, prec, D, chi, direction):
+    """A generic composite (a perturbed product state's z composite): the
+    library's block power iteration on the channel transfer matrix against the
+    oracle's dense eigenvalues of the same matrix, built from the library's own
+    converged environment (so only the eigen-solve is compared)."""
+    A, B = kh_inputs.perturbed_product_state(D, seed=8, eps=0.3)
+    T = peps.composite(A, B, "z")
+    ctx = g.Context(D, chi, prec, n_slots=1, svd_cut=CUT[prec])
+    ctx.ctm_set_tensor(0, _t(T))
+    ctx.ctm_sweep(0, 300, 3, 1e-12 if prec == "fp64" else 1e-7, allow_noconv=True)
+    xi, ratio, its = ctx.ctm_correlation_length(0, direction, max_iter=800, tol=1e-10 if prec == "fp64" else 1e-7)
+    env = _gpu_env(ctx, 0, D, chi)
+    ref = ctmrg.correlation_length(env, ctmrg.double_tensor(T), direction)
+    assert abs(xi - ref) < (1e-7 if prec == "fp64" else 1e-4) * max(ref, 1e-3), (xi, ref, its)
