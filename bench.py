@@ -41,8 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32x3")
-    ap.add_argument("--proj-fp64", type=int, default=0,
-                    help="1: projector factorisations in FP64 (single-precision modes)")
+    ap.add_argument("--proj-fp64", type=int, default=1,
+                    help="1 (default): the projector SVD in FP64 in the single-precision modes; 0: in FP32")
     ap.add_argument("--ctm-sweeps", type=int, default=4, help="CTM sweeps per gate layer")
     ap.add_argument("--obs-sweeps", type=int, default=2, help="CTM sweeps per mapping in the observables")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -235,8 +235,9 @@ class Workload:
         self.A0, self.B0 = kh_inputs.perturbed_product_state(D, seed=seed, eps=0.05)
         self.stream = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(self.stream):
+            # the library's defaults per precision (single precision: cut 1e-4 s_1,
+            # two subspace iterations per move)
             self.ctx = g.Context(D, chi, prec, device=dev, stream=self.stream,
-                                 svd_cut=1e-12 if prec == "fp64" else 1e-6,
                                  proj_fp64=proj_fp64 if prec != "fp64" else 0)
             self.ctx.set_state(torch.as_tensor(self.A0, device=dev), torch.as_tensor(self.B0, device=dev))
         self.Hs = [g.bond_hamiltonian(gm, w["J"], w["K"]) for gm in "xyz"]
@@ -272,15 +273,16 @@ class Workload:
         self.ctx.close()
 
 
-def variant(g, dev, a, w, D, chi, prec, steps, warmup, flush):
+def variant(g, dev, a, w, D, chi, prec, steps, warmup, flush, proj_fp64=0):
     """A second configuration measured in the same run (one replica, same
     step definition): steps/s and its CTM-sweep flop rate."""
-    wl = Workload(g, dev, D, chi, prec, a, w, seed=0)
+    wl = Workload(g, dev, D, chi, prec, a, w, seed=0, proj_fp64=proj_fp64 if prec != "fp64" else 0)
     ms, last = wl.timed(steps, warmup, flush)
     wl.close()
     ms_step = ms / steps
     sw = sweeps_per_step(a)
-    return {"config": {"D": D, "chi": chi, "prec": prec, "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
+    return {"config": {"D": D, "chi": chi, "prec": prec, "projector_svd": "fp64" if (proj_fp64 or prec == "fp64")
+                       else "fp32", "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
                        "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps},
             "value": 1e3 / ms_step, "unit": "steps/s", "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
             "ctm_sweeps_per_s": 1e3 / ms_step * sw,
@@ -354,7 +356,8 @@ def run_ours(a, rank, world, local, pg):
             # the plain FP64 GPU form of the same workload, and the largest
             # single-precision configuration (D, chi) = (6, 144)
             variants.append(variant(g, dev, a, w, D, chi, "fp64", 2, 3, flush))
-            variants.append(variant(g, dev, a, w, 6, 144, a.prec, 2, 3, flush))
+            variants.append(variant(g, dev, a, w, D, chi, a.prec, 3, 3, flush, proj_fp64=1 - a.proj_fp64))
+            variants.append(variant(g, dev, a, w, 6, 144, a.prec, 2, 3, flush, proj_fp64=a.proj_fp64))
         cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, wl.A0, wl.B0)   # N = 1 only
         sw = sweeps_per_step(a)
         out = {
@@ -364,8 +367,9 @@ def run_ours(a, rank, world, local, pg):
             "data": "synthetic (seeded perturbed beta=0 product state)",
             "config": {"workload": WORKLOAD, "D": D, "chi": chi, "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
                        "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
-                       "prec": a.prec, "projector_factorisations": "fp64" if (a.proj_fp64 or a.prec == "fp64")
-                       else "fp32", "parallelism": "replicas x%d" % world,
+                       "prec": a.prec, "projector_svd": "fp64" if (a.proj_fp64 or a.prec == "fp64") else "fp32",
+                       "svd_cut": wl.ctx.cfg.svd_cut, "svd_iters_warm": wl.ctx.cfg.svd_iters_warm,
+                       "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MB write outside the timed events)"},
             "ctm_sweeps_per_s": value * sw,
             "ctm_sweep_tflops": step_flops(D, chi, sw) / (t_max / a.steps * 1e-3) / 1e12,

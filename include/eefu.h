@@ -86,12 +86,12 @@ typedef struct kh_config {
     double als_reg;          /* Tikhonov shift reg * tr(R)/dim(R) in the normal eqns  */
     uint64_t seed;           /* seed of the counter-based start vectors              */
     int proj_fp64;           /* 1: in the single-precision modes, the projector
-                                factorisations (the Cholesky factor of the
-                                subspace QR, the Rayleigh-Ritz SVD, S^-1/2 and the
-                                cut-off) run in FP64 arithmetic; their products
-                                with the contraction data stay in the contraction
-                                precision.  The FP64 mode always does.  Limits
-                                k = chi + svd_oversample to the FP64 solver's 112. */
+                                SVD is FP64: the Rayleigh-Ritz matrix accumulated
+                                in FP64, its SVD refined to FP64 by Newton steps
+                                from the FP32 Jacobi, S^-1/2 and the cut-off in
+                                FP64; the products with the contraction data stay
+                                in the contraction precision.  The FP64 mode
+                                always computes in FP64.                        */
 } kh_config;
 
 typedef struct kh_ctx kh_ctx;   /* opaque; host memory owned by the library */
@@ -310,7 +310,7 @@ kh_status kh_selftest_svd(int prec, int k, const double* dev_X, double* dev_S, d
 
 /* The projector SVD of the FP64-projector option (kh_config.proj_fp64) on a
  * k x k FP64 matrix X (k <= 160): the FP32 one-sided Jacobi SVD followed by
- * three FP64 Newton refinement steps (first-order corrections L' = L (I + F),
+ * three FP64 Newton refinement steps and a re-orthogonalisation (first-order corrections L' = L (I + F),
  * Q' = Q (I + H) from R = I - L^T L, P = I - Q^T Q and T = L^T X Q, pairs
  * whose gap is below 64 times their coupling only re-orthogonalised).  X Q = L S with dev_S
  * (k, in the Jacobi's descending order), dev_L, dev_Q k x k (columns =

@@ -236,8 +236,14 @@ def default_config(D, chi, prec="fp64", **kw):
     c.D, c.chi, c.prec = D, chi, PREC[prec] if isinstance(prec, str) else int(prec)
     if c.prec != PREC["fp64"]:
         # single-precision paths: the Rayleigh-Ritz SVD is capped (its residual
-        # is below the FP32-level accuracy of the contractions well before)
+        # is below the FP32-level accuracy of the contractions well before);
+        # singular values below 1e-4 s_1 are dropped (the single-precision
+        # subspace iteration does not resolve the spectrum below ~2e-5 s_1),
+        # and two subspace iterations per move keep the warm subspace on the
+        # moving spectrum (one leaves sweep-to-sweep changes ~1e-5 of s_1)
         c.jacobi_max_sweeps = 8
+        c.svd_cut = 1e-4
+        c.svd_iters_warm = 2
     for k, v in kw.items():
         setattr(c, k, v)
     return c

@@ -44,7 +44,7 @@ Dims make_dims(const kh_config& c, bool fp64) {
     d.pmax = c.p_max;
     d.nslots = c.n_slots;
     d.dl_alloc = d.d2 <= 2 * c.p_max;
-    int kmax = (fp64 || c.proj_fp64) ? 112 : 160;      // the FP64 one-CTA Jacobi limit
+    int kmax = fp64 ? 112 : 160;      // the one-CTA Jacobi limits (FP64, FP32)
     if (d.n <= kmax) {
         d.kk = d.n;
         d.full = true;

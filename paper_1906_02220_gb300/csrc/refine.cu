@@ -27,6 +27,8 @@
 // ill-conditioned and only the orthogonality part (f_ij = r_ij / 2,
 // h_ij = p_ij / 2) is applied: the pair's common subspace, which is all the
 // projectors depend on, is kept.
+#include <cooperative_groups.h>
+
 #include "engine.cuh"
 
 namespace kh {
@@ -117,12 +119,170 @@ refine_apply_kernel(const double* __restrict__ L, const double* __restrict__ Q, 
     (blockIdx.y == 0 ? Lo : Qo)[e] = acc;
 }
 
+// All refinement steps in one cooperative launch.  Every CTA (64 threads)
+// owns 8 x 8 output tiles (grid-stride over the (k/8)^2 tiles); the four
+// phases of a step -- R, P, W = L^T G; T = W Q; the corrections; L + L F and
+// Q + Q H -- are separated by grid barriers, and each GEMM-like phase first
+// stages the 8-wide slabs of its operands in shared memory (the FP64 pipe
+// then runs from shared memory instead of waiting on L2 loads).  The factors
+// ping-pong between (L1, Q1) and (Lo, Qo).
+constexpr int kRT = 8;                                     // tile edge
+__global__ void __launch_bounds__(kRT * kRT)
+refine_coop_kernel(const double* __restrict__ G, int k, const double* L0, const double* Q0, double* s_out,
+                   double* Lo, double* Qo, double* work, double rel_gap, int newton_steps) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    extern __shared__ double slab[];                       // 5 slabs of 8 x k
+    const long long kk = (long long)k * k;
+    double *R = work, *P = work + kk, *W = work + 2 * kk, *T = work + 3 * kk, *F = work + 4 * kk,
+           *H = work + 5 * kk, *L1 = work + 6 * kk, *Q1 = work + 7 * kk;
+    const int nt = (k + kRT - 1) / kRT, ntiles = nt * nt;
+    const int tid = threadIdx.x, ti = tid / kRT, tj = tid % kRT;
+    double* s0 = slab;
+    double* s1 = slab + kRT * k;
+    double* s2 = slab + 2 * kRT * k;
+    double* s3 = slab + 3 * kRT * k;
+    double* s4 = slab + 4 * kRT * k;
+    // slab of columns [c0, c0+8) of X (k x k): sl[m * 8 + c] = X[m][c0 + c]
+    auto load_cols = [&](double* sl, const double* X, int c0) {
+        for (int e = tid; e < kRT * k; e += kRT * kRT) {
+            const int m = e / kRT, c = e % kRT;
+            sl[e] = (c0 + c < k) ? X[m * k + c0 + c] : 0.0;
+        }
+    };
+    // slab of rows [r0, r0+8) of X: sl[m * 8 + r] = X[r0 + r][m] (same indexing as a column slab of X^T)
+    auto load_rows = [&](double* sl, const double* X, int r0) {
+        for (int e = tid; e < kRT * k; e += kRT * kRT) {
+            const int r = e / k, m = e % k;
+            sl[m * kRT + r] = (r0 + r < k) ? X[(r0 + r) * k + m] : 0.0;
+        }
+    };
+    const int nsteps = newton_steps + 1;
+    for (int step = 0; step < nsteps; ++step) {
+        const int rem = nsteps - 1 - step;                 // steps after this one; the last writes (Lo, Qo)
+        const double* Li = step == 0 ? L0 : ((rem % 2 == 0) ? L1 : Lo);
+        const double* Qi = step == 0 ? Q0 : ((rem % 2 == 0) ? Q1 : Qo);
+        double* Ln = (rem % 2 == 0) ? Lo : L1;
+        double* Qn = (rem % 2 == 0) ? Qo : Q1;
+        const double gap = step < newton_steps ? rel_gap : INFINITY;
+        // phase 1: R = I - L^T L, P = I - Q^T Q, W = L^T G on tile (I, J)
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int i0 = (t / nt) * kRT, j0 = (t % nt) * kRT;
+            __syncthreads();
+            load_cols(s0, Li, i0);
+            load_cols(s1, Li, j0);
+            load_cols(s2, Qi, i0);
+            load_cols(s3, Qi, j0);
+            load_cols(s4, G, j0);
+            __syncthreads();
+            double r0 = 0.0, r1 = 0.0, p0 = 0.0, p1 = 0.0, w0 = 0.0, w1 = 0.0;
+            int m = 0;
+            for (; m + 1 < k; m += 2) {
+                const double a0 = s0[m * kRT + ti], a1 = s0[(m + 1) * kRT + ti];
+                r0 = fma(a0, s1[m * kRT + tj], r0);
+                r1 = fma(a1, s1[(m + 1) * kRT + tj], r1);
+                p0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], p0);
+                p1 = fma(s2[(m + 1) * kRT + ti], s3[(m + 1) * kRT + tj], p1);
+                w0 = fma(a0, s4[m * kRT + tj], w0);
+                w1 = fma(a1, s4[(m + 1) * kRT + tj], w1);
+            }
+            if (m < k) {
+                const double a0 = s0[m * kRT + ti];
+                r0 = fma(a0, s1[m * kRT + tj], r0);
+                p0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], p0);
+                w0 = fma(a0, s4[m * kRT + tj], w0);
+            }
+            const int i = i0 + ti, j = j0 + tj;
+            if (i < k && j < k) {
+                const double d = (i == j) ? 1.0 : 0.0;
+                R[i * k + j] = d - (r0 + r1);
+                P[i * k + j] = d - (p0 + p1);
+                W[i * k + j] = w0 + w1;
+            }
+        }
+        grid.sync();
+        // phase 2: T = W Q
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int i0 = (t / nt) * kRT, j0 = (t % nt) * kRT;
+            __syncthreads();
+            load_rows(s0, W, i0);
+            load_cols(s1, Qi, j0);
+            __syncthreads();
+            double t0 = 0.0, t1 = 0.0;
+            int m = 0;
+            for (; m + 1 < k; m += 2) {
+                t0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], t0);
+                t1 = fma(s0[(m + 1) * kRT + ti], s1[(m + 1) * kRT + tj], t1);
+            }
+            if (m < k) t0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], t0);
+            const int i = i0 + ti, j = j0 + tj;
+            if (i < k && j < k) T[i * k + j] = t0 + t1;
+        }
+        grid.sync();
+        // phase 3: the corrections (elementwise)
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long e = blockIdx.x * (long long)blockDim.x + tid; e < kk; e += stride) {
+            const int i = (int)(e / k), j = (int)(e % k);
+            const double rij = R[e], pij = P[e];
+            if (i == j) {
+                F[e] = 0.5 * rij;
+                H[e] = 0.5 * pij;
+                s_out[i] = T[e] * (1.0 + 0.5 * (rij + pij));
+                continue;
+            }
+            const double si = T[i * k + i], sj = T[j * k + j];
+            const double big = fmax(fabs(si), fabs(sj));
+            const double coupling = fmax(fabs(T[e]), fabs(T[j * k + i]));
+            if (!(fabs(sj - si) > fmax(gap * big, 64.0 * coupling)) || big == 0.0) {
+                F[e] = 0.5 * rij;
+                H[e] = 0.5 * pij;
+                continue;
+            }
+            const double a = T[e] + sj * rij;
+            const double b = T[j * k + i] + sj * pij;
+            const double inv = 1.0 / ((sj - si) * (sj + si));
+            F[e] = (sj * a + si * b) * inv;
+            H[e] = (si * a + sj * b) * inv;
+        }
+        grid.sync();
+        // phase 4: L' = L + L F, Q' = Q + Q H
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int i0 = (t / nt) * kRT, j0 = (t % nt) * kRT;
+            __syncthreads();
+            load_rows(s0, Li, i0);
+            load_cols(s1, F, j0);
+            load_rows(s2, Qi, i0);
+            load_cols(s3, H, j0);
+            __syncthreads();
+            const int i = i0 + ti, j = j0 + tj;
+            double l0 = 0.0, l1 = 0.0, q0 = 0.0, q1 = 0.0;
+            int m = 0;
+            for (; m + 1 < k; m += 2) {
+                l0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], l0);
+                l1 = fma(s0[(m + 1) * kRT + ti], s1[(m + 1) * kRT + tj], l1);
+                q0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], q0);
+                q1 = fma(s2[(m + 1) * kRT + ti], s3[(m + 1) * kRT + tj], q1);
+            }
+            if (m < k) {
+                l0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], l0);
+                q0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], q0);
+            }
+            if (i < k && j < k) {
+                Ln[i * k + j] = Li[i * k + j] + (l0 + l1);
+                Qn[i * k + j] = Qi[i * k + j] + (q0 + q1);
+            }
+        }
+        if (step + 1 < nsteps) grid.sync();
+    }
+}
+
 }  // namespace
 
-size_t svd_refine_scratch(int k) { return (size_t)6 * k * k; }
+size_t svd_refine_scratch(int k) { return (size_t)8 * k * k; }
 
 // G (k x k, FP64), L and Q (k x k FP64, columns = the single-precision left
-// and right singular vectors, G Q ~ L diag(s)): three Newton steps, the refined
+// and right singular vectors, G Q ~ L diag(s)): three Newton steps and a
+// re-orthogonalisation, the refined
 // factors to Lo, Qo and the refined singular values to s (k).  work:
 // svd_refine_scratch(k) doubles.
 void svd_refine_fp64(const double* G, int k, const double* L, const double* Q, double* s, double* Lo, double* Qo,
@@ -130,18 +290,42 @@ void svd_refine_fp64(const double* G, int k, const double* L, const double* Q, d
     const long long kk = (long long)k * k;
     double *R = work, *P = work + kk, *W = work + 2 * kk, *T = work + 3 * kk, *F = work + 4 * kk, *H = work + 5 * kk;
     const int blocks = (int)((kk + kRefineThreads - 1) / kRefineThreads);
-    // three steps: each squares the residuals of the pairs it rotates (the
-    // FP32 ones, ~k 2^-24, reach FP64 rounding after two; a pair whose
+    {
+        // one cooperative launch when the device allows it and the grid fits
+        int dev = 0, coop = 0, sms = 0, per_sm = 0;
+        KH_CUDA(cudaGetDevice(&dev));
+        KH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        KH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const size_t smem = (size_t)5 * kRT * k * sizeof(double);
+        static std::atomic<size_t> granted[kMaxDevices] = {};
+        smem_opt_in(refine_coop_kernel, smem, granted);
+        KH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_coop_kernel, kRT * kRT, smem));
+        const int ntiles = ((k + kRT - 1) / kRT) * ((k + kRT - 1) / kRT);
+        const int cblocks = std::min(ntiles, per_sm * sms);
+        if (coop && cblocks >= 1) {
+            int newton = 3;
+            void* args[] = {(void*)&G, (void*)&k, (void*)&L, (void*)&Q, (void*)&s, (void*)&Lo, (void*)&Qo,
+                            (void*)&work, (void*)&rel_gap, (void*)&newton};
+            KH_CUDA(cudaLaunchCooperativeKernel((const void*)refine_coop_kernel, dim3(cblocks), dim3(kRT * kRT),
+                                                args, smem, st));
+            KH_LAUNCHED();
+            return;
+        }
+    }
+    // three Newton steps: each squares the residuals of the pairs it rotates
+    // (the FP32 ones, ~k 2^-24, reach FP64 rounding after two; a pair whose
     // correction was near the 1/64 limit needs the third) and re-orthogonalises
-    // the clustered ones
-    for (int step = 0; step < 3; ++step) {
+    // the clustered ones; a fourth step only re-orthogonalises (every pair
+    // treated as clustered), squaring what the last rotation left of R and P
+    for (int step = 0; step < 4; ++step) {
         const double* Li = step == 0 ? L : Lo;
         const double* Qi = step == 0 ? Q : Qo;
         refine_products_kernel<<<blocks, kRefineThreads, 0, st>>>(G, Li, Qi, k, R, P, W);
         KH_LAUNCHED();
         refine_t_kernel<<<blocks, kRefineThreads, 0, st>>>(W, Qi, k, T);
         KH_LAUNCHED();
-        refine_corrections_kernel<<<blocks, kRefineThreads, 0, st>>>(R, P, T, k, rel_gap, F, H, s);
+        refine_corrections_kernel<<<blocks, kRefineThreads, 0, st>>>(R, P, T, k, step < 3 ? rel_gap : INFINITY, F,
+                                                                      H, s);
         KH_LAUNCHED();
         // in place after the first step: each output entry reads its row of the
         // old factor, so the update goes through W and T (free by now) first

@@ -158,18 +158,24 @@ void Engine<T>::correlation_length(int slot, int dir, int max_iter, double tol, 
         // w[a,(lk,lb),b] = sum_{d,v} Y1[(a,l)][(d,v)] dn[(d,v)][b]
         gemm_rm<T>(chi * d2, chi, chi * d2, Y1, false, dn, false, w, st);
     };
-    auto orthonormalise = [&](T* X) {              // modified Gram-Schmidt on the b columns, FP64 scalars
+    // Gram-Schmidt on the b columns with FP64 scalars, the projections applied
+    // twice: a column (nearly) dependent on the earlier ones keeps, after one
+    // pass, components along them of the size of its residual (the transfer
+    // matrix may have fewer than b nonzero eigenvalues); the second pass makes
+    // the normalised residual orthogonal to working precision
+    auto orthonormalise = [&](T* X) {
         KH_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 2 * b, st));
         for (int j = 0; j < b; ++j) {
             T* xj = X + j * nt;
-            for (int i = 0; i < j; ++i) {
-                double* r = sc + 2 * b + i * b + j;
-                KH_CUDA(cudaMemsetAsync(r, 0, sizeof(double), st));
-                dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(X + i * nt, xj, nt, r);
-                KH_LAUNCHED();
-                axpy_dev_kernel<T><<<grid, 256, 0, st>>>(X + i * nt, xj, nt, r, nullptr);
-                KH_LAUNCHED();
-            }
+            for (int pass = 0; pass < 2; ++pass)
+                for (int i = 0; i < j; ++i) {
+                    double* r = sc + 2 * b + i * b + j;
+                    KH_CUDA(cudaMemsetAsync(r, 0, sizeof(double), st));
+                    dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(X + i * nt, xj, nt, r);
+                    KH_LAUNCHED();
+                    axpy_dev_kernel<T><<<grid, 256, 0, st>>>(X + i * nt, xj, nt, r, nullptr);
+                    KH_LAUNCHED();
+                }
             dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(xj, xj, nt, sc + j);
             KH_LAUNCHED();
             scale_rsqrt_kernel<T><<<grid, 256, 0, st>>>(xj, nt, sc + j);

@@ -4,7 +4,7 @@ size (D = 4, chi = 64, p = 16, Kitaev point K = 1, J = 0, dbeta = 0.01).
 
 Calls only the CPU oracle (``oracle/``) on the seeded inputs of
 ``kh_inputs``; nothing here touches the CUDA library.  Run from the repo
-root (about five minutes on eight cores):
+root (about ten minutes on eight cores):
 
     python tests/golden/make_bench_parity.py
 
@@ -15,8 +15,9 @@ single-precision cut-off; the z layer of a Trotter step, g = exp(-(dbeta/2)
 H^z) (Sec. III, Eq. 6); CTMRG of the gated composite converged to 1e-10 in
 the normalised spectra; the metric, ALS and gauge of the bond update
 (Fig. 3(b)); then the three gamma-mapped CTMRGs of the un-gated state and the
-observables of Sec. V.  The cut-off is the single-precision path's (1e-6),
-so both sides apply the same truncation rule.
+observables of Sec. V.  The cut-off is the single-precision path's (1e-4,
+above the resolution floor of its projector spectra), so both sides apply the
+same truncation rule.
 """
 import json
 import os
@@ -32,7 +33,7 @@ if ROOT not in sys.path:
 import kh_inputs  # noqa: E402
 from oracle import eefu  # noqa: E402
 
-CASE = dict(D=4, chi=64, J=0.0, K=1.0, dbeta=0.01, seed=21, svd_cut=1e-6, ctm_tol=1e-10, ctm_max_sweeps=400)
+CASE = dict(D=4, chi=64, J=0.0, K=1.0, dbeta=0.01, seed=21, svd_cut=1e-4, ctm_tol=1e-10, ctm_max_sweeps=400)
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "bench_parity_D4_chi64.json")
 if len(sys.argv) > 2:                  # python make_bench_parity.py <svd_cut> <output>
     CASE["svd_cut"] = float(sys.argv[1])

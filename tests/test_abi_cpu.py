@@ -69,10 +69,11 @@ def test_workspace_sizing_at_the_jacobi_limits(g, D, chi, prec, ok):
     assert (b > 0) == ok
 
 
-@pytest.mark.parametrize("chi,ok", [(96, True), (97, False)])
-def test_fp64_projector_option_takes_the_fp64_limit(g, chi, ok):
-    """With proj_fp64 the single-precision modes factor in FP64, so k =
-    chi + 16 is bounded by the FP64 solver's 112; the FP64 scratch is extra."""
+@pytest.mark.parametrize("chi,ok", [(144, True), (145, False)])
+def test_fp64_projector_option_keeps_the_single_precision_limit(g, chi, ok):
+    """With proj_fp64 the projector SVD is the FP32 Jacobi refined in FP64, so
+    k = chi + 16 keeps the FP32 solver's bound of 160; the FP64 scratch is
+    extra, and only 0 and 1 are accepted."""
     import ctypes
     c = g.default_config(4, chi, "tf32x3", proj_fp64=1)
     b = g.lib().kh_workspace_bytes(ctypes.byref(c))
