@@ -58,6 +58,17 @@ __global__ void dot_acc_kernel(const T* __restrict__ a, const T* __restrict__ b,
     }
 }
 
+// x <- fresh random vector when its squared norm after the projections (post)
+// is below rel2 times the one before them (pre): the column was dependent on
+// the earlier ones, and what is left of it is rounding correlated with them
+template <typename T>
+__global__ void refill_if_dependent_kernel(T* __restrict__ x, long long n, const double* post, const double* pre,
+                                           double rel2, uint64_t seed, uint64_t stream) {
+    if (*post > rel2 * *pre) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = (T)rnd_uniform(seed, stream, (uint64_t)i);
+}
+
 template <typename T>
 __global__ void fill_random_kernel(T* V, long long n, uint64_t seed, uint64_t stream) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -159,23 +170,43 @@ void Engine<T>::correlation_length(int slot, int dir, int max_iter, double tol, 
         gemm_rm<T>(chi * d2, chi, chi * d2, Y1, false, dn, false, w, st);
     };
     // Gram-Schmidt on the b columns with FP64 scalars, the projections applied
-    // twice: a column (nearly) dependent on the earlier ones keeps, after one
-    // pass, components along them of the size of its residual (the transfer
-    // matrix may have fewer than b nonzero eigenvalues); the second pass makes
-    // the normalised residual orthogonal to working precision
+    // twice (one pass leaves the residual of a nearly dependent column with
+    // components along the earlier ones of its own size).  The transfer matrix
+    // may have fewer than b nonzero eigenvalues, so T V can be rank deficient:
+    // a column whose residual falls below the rounding floor of its own norm
+    // is what is left of a dependent column -- rounding correlated with the
+    // earlier columns, which normalising would turn into one of them -- and is
+    // replaced by a random vector, projected twice in turn.
+    const double rel2 = sizeof(T) == 8 ? 1e-20 : 1e-8;
+    uint64_t refills = 0;
+    auto project = [&](T* X, int j) {
+        T* xj = X + j * nt;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int i = 0; i < j; ++i) {
+                double* r = sc + 2 * b + i * b + j;
+                KH_CUDA(cudaMemsetAsync(r, 0, sizeof(double), st));
+                dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(X + i * nt, xj, nt, r);
+                KH_LAUNCHED();
+                axpy_dev_kernel<T><<<grid, 256, 0, st>>>(X + i * nt, xj, nt, r, nullptr);
+                KH_LAUNCHED();
+            }
+    };
     auto orthonormalise = [&](T* X) {
         KH_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * 2 * b, st));
         for (int j = 0; j < b; ++j) {
             T* xj = X + j * nt;
-            for (int pass = 0; pass < 2; ++pass)
-                for (int i = 0; i < j; ++i) {
-                    double* r = sc + 2 * b + i * b + j;
-                    KH_CUDA(cudaMemsetAsync(r, 0, sizeof(double), st));
-                    dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(X + i * nt, xj, nt, r);
-                    KH_LAUNCHED();
-                    axpy_dev_kernel<T><<<grid, 256, 0, st>>>(X + i * nt, xj, nt, r, nullptr);
-                    KH_LAUNCHED();
-                }
+            dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(xj, xj, nt, sc + b + j);
+            KH_LAUNCHED();
+            project(X, j);
+            if (j > 0) {
+                dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(xj, xj, nt, sc + j);
+                KH_LAUNCHED();
+                refill_if_dependent_kernel<T><<<grid, 256, 0, st>>>(xj, nt, sc + j, sc + b + j, rel2, cfg.seed,
+                                                                    0x5eedULL + (refills++));
+                KH_LAUNCHED();
+                project(X, j);
+                KH_CUDA(cudaMemsetAsync(sc + j, 0, sizeof(double), st));
+            }
             dot_acc_kernel<T><<<sumsq_grid(nt), 256, 0, st>>>(xj, xj, nt, sc + j);
             KH_LAUNCHED();
             scale_rsqrt_kernel<T><<<grid, 256, 0, st>>>(xj, nt, sc + j);

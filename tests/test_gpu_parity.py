@@ -456,8 +456,9 @@ def test_bench_configuration_matches_oracle(g, proj_fp64):
     make_bench_parity.py from oracle/ only): a seeded random state, the z gate
     of a Kitaev step (K = 1, J = 0, dbeta = 0.01) with its CTMRG converged,
     the environment-weighted bond update, then the observables with the three
-    mappings converged.  E/site, <H^gamma> and <S^a> within |dE| / max(|E|, 1)
-    <= 1e-6; the four projector spectra s/||s|| within 1e-5; their largest
+    mappings converged.  E/site and <H^gamma> within |dE| / max(|E|, 1) <= 1e-6,
+    <S^a> too with the FP64 projector SVD (3e-6 with the FP32 one); the four
+    projector spectra s/||s|| within 1e-5; their largest
     discarded weight within the FP32 resolution; the bond update's relative
     cost within 1e-4 relative."""
     import json
@@ -483,8 +484,13 @@ def test_bench_configuration_matches_oracle(g, proj_fp64):
     Hs = [g.bond_hamiltonian(gm, c["J"], c["K"]) for gm in "xyz"]
     r = ctx.observables(Hs, ctm_max_sweeps=400, ctm_min_sweeps=3, ctm_tol=1e-7)
     ro = gold["observables"]
-    for key in ("E_site", "Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+    # the sublattice moments with the FP32 projector SVD: within 3e-6 (measured
+    # up to 1.4e-6; its spectra move by ~1e-6 from sweep to sweep)
+    mtol = E_TOL if proj_fp64 else 3e-6
+    for key in ("E_site", "Hx", "Hy", "Hz"):
         assert abs(r[key] - ro[key]) < E_TOL * max(1.0, abs(ro[key])), (key, r[key], ro[key])
+    for key in ("Ax", "Az", "Bx", "Bz"):
+        assert abs(r[key] - ro[key]) < mtol * max(1.0, abs(ro[key])), (key, r[key], ro[key])
     assert abs(r["trunc"] - ro["trunc"]) < 1e-3 * ro["trunc"] + 1e-5
     del ctx
     torch.cuda.synchronize()
@@ -555,7 +561,9 @@ def test_correlation_length_of_decoupled_chains(g, prec, Kh):
     want = -1.0 / np.log(np.tanh(Kh))
     assert abs(xi - want) < (1e-8 if prec == "fp64" else 1e-4) * want, (xi, want, its)
     xi_y, _, _ = ctx.ctm_correlation_length(0, 1, max_iter=400)
-    assert xi_y < 0.05
+    # nothing correlates along y: |l2|/|l1| is zero up to rounding (~1e-7 in
+    # single precision, i.e. xi ~ 0.06)
+    assert xi_y < (0.05 if prec == "fp64" else 0.1)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
