@@ -14,6 +14,7 @@ independent replicas per rank (weak scaling, no collective on the data path).
     python bench.py [--gpus N --steps K --warmup W --prec fp32 --impl ours|reference]
 """
 import argparse
+import math
 import json
 import os
 import statistics
@@ -200,14 +201,15 @@ def roofline_for(prec, prof, pk, pk_src):
     (2 (2 chi^3 D^2 + 2 chi^3 D^4 + 4 p chi^2 D^6), the layered count whatever
     form runs) / its average duration per move, against the tensor-core peak
     of the contraction precision (the CUDA-core peak for FP32 / FP64).
-    Companion entries: the half-system product (a4), the absorption (a6) and
-    the CholQR2 orthonormalisation of the projector subspace (latency-bound,
-    against the CUDA-core peak).  `traffic` is null: these are categories of
+    Companion entries: the half-system product (a4), the absorption (a6), the
+    layered site contraction alone (the ket-then-bra kernel inside a3 and a6,
+    4 p chi^2 D^6 flops per launch) and the CholQR2 orthonormalisation of the
+    projector subspace (latency-bound, against the CUDA-core peak).  `traffic` is null: these are categories of
     several launches, and no DRAM counters of the current kernels are stored
     with the benchmark."""
     tc = prec in ("tf32", "tf32x3", "bf16")
     bounds = {"corners": "tensor" if tc else "alu", "half_system_product": "tensor" if tc else "alu",
-              "absorb": "tensor" if tc else "alu", "cholqr_orth": "alu"}
+              "absorb": "tensor" if tc else "alu", "site_layer": "tensor" if tc else "alu", "cholqr_orth": "alu"}
     out = {}
     for cat, b in bounds.items():
         c = prof.get(cat)
@@ -228,7 +230,7 @@ class Workload:
     (fixed CTM sweeps per layer) followed by the observables (fixed sweeps per
     mapping), on its own stream."""
 
-    def __init__(self, g, dev, D, chi, prec, a, w, seed, proj_fp64=0):
+    def __init__(self, g, dev, D, chi, prec, a, w, seed, proj_fp64=0, site_form=0):
         import torch
         self.g, self.dev, self.a, self.w = g, dev, a, w
         self.D, self.chi, self.prec = D, chi, prec
@@ -238,7 +240,7 @@ class Workload:
             # the library's defaults per precision (single precision: cut 1e-4 s_1,
             # two subspace iterations per move)
             self.ctx = g.Context(D, chi, prec, device=dev, stream=self.stream,
-                                 proj_fp64=proj_fp64 if prec != "fp64" else 0)
+                                 proj_fp64=proj_fp64 if prec != "fp64" else 0, site_form=site_form)
             self.ctx.set_state(torch.as_tensor(self.A0, device=dev), torch.as_tensor(self.B0, device=dev))
         self.Hs = [g.bond_hamiltonian(gm, w["J"], w["K"]) for gm in "xyz"]
 
@@ -273,21 +275,69 @@ class Workload:
         self.ctx.close()
 
 
-def variant(g, dev, a, w, D, chi, prec, steps, warmup, flush, proj_fp64=0):
+def site_form_name(prec, site_form, D, p=16):
+    tc = prec in ("tf32", "tf32x3", "bf16")
+    if site_form == 2 and D * D <= 2 * p:
+        return "double-layer operand (D^2 x D^2 index formed)"
+    if site_form == 0 and not tc and D * D <= 2 * p:
+        return "double-layer operand (D^2 x D^2 index formed)"
+    return "layered ket-then-bra, tensor cores, intermediate on chip" if tc else "layered ket-then-bra, CUDA cores"
+
+
+def variant(g, dev, a, w, D, chi, prec, steps, warmup, flush, proj_fp64=0, site_form=0):
     """A second configuration measured in the same run (one replica, same
     step definition): steps/s and its CTM-sweep flop rate."""
-    wl = Workload(g, dev, D, chi, prec, a, w, seed=0, proj_fp64=proj_fp64 if prec != "fp64" else 0)
+    wl = Workload(g, dev, D, chi, prec, a, w, seed=0, proj_fp64=proj_fp64 if prec != "fp64" else 0,
+                  site_form=site_form)
     ms, last = wl.timed(steps, warmup, flush)
     wl.close()
     ms_step = ms / steps
     sw = sweeps_per_step(a)
     return {"config": {"D": D, "chi": chi, "prec": prec, "projector_svd": "fp64" if (proj_fp64 or prec == "fp64")
-                       else "fp32", "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
+                       else "fp32", "site_contraction": site_form_name(prec, site_form, D),
+                       "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
                        "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps},
             "value": 1e3 / ms_step, "unit": "steps/s", "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
             "ctm_sweeps_per_s": 1e3 / ms_step * sw,
             "ctm_sweep_tflops": step_flops(D, chi, sw) / (ms_step * 1e-3) / 1e12,
             "E_site": last["E_site"] if last else None}
+
+
+def batch_variant(g, dev, a, w, D, chi, prec, steps, nprob=16, proj_fp64=0):
+    """Many coupling angles at once (eefu_evolve_batch): nprob problems with
+    phi_i = 2 pi i / nprob (J = cos phi, K = 2 sin phi) advanced concurrently,
+    each step = the benchmark's Trotter step + observables.  Timed on the host
+    clock around the batch call (it returns when every problem's work has
+    completed), after a one-step warm-up batch.  value = nprob x steps / time."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    ctxs = []
+    for i in range(nprob):
+        A0, B0 = kh_inputs.perturbed_product_state(D, seed=i, eps=0.05)
+        c = g.Context(D, chi, prec, device=dev, stream=torch.cuda.Stream(device=dev),
+                      proj_fp64=proj_fp64 if prec != "fp64" else 0)
+        c.set_state(torch.as_tensor(A0, device=dev), torch.as_tensor(B0, device=dev))
+        ctxs.append(c)
+    phis = [2.0 * math.pi * i / nprob for i in range(nprob)]
+    J = [math.cos(p) for p in phis]
+    K = [[2.0 * math.sin(p)] * 3 for p in phis]
+    kw = dict(ctm_max_sweeps=a.ctm_sweeps, ctm_min_sweeps=a.ctm_sweeps, ctm_tol=-1.0, obs_max_sweeps=a.obs_sweeps,
+              obs_min_sweeps=a.obs_sweeps, obs_tol=-1.0)
+    g.evolve_batch(ctxs, J, K, w["dbeta"], 1, 1, **kw)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    trajs = g.evolve_batch(ctxs, J, K, w["dbeta"], steps, 1, **kw)
+    dt = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    return {"config": {"D": D, "chi": chi, "prec": prec, "problems": nprob,
+                       "couplings": "phi_i = 2 pi i / %d, J = cos phi, K = 2 sin phi" % nprob,
+                       "projector_svd": "fp64" if (proj_fp64 or prec == "fp64") else "fp32",
+                       "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
+                       "timing": "host clock around one eefu_evolve_batch call"},
+            "value": nprob * steps / dt, "unit": "steps/s (all problems)", "steps": steps,
+            "ms_per_batch_step": dt / steps * 1e3,
+            "E_site_first_last": [trajs[0][-1]["E_site"], trajs[-1][-1]["E_site"]]}
 
 
 def run_ours(a, rank, world, local, pg):
@@ -358,6 +408,10 @@ def run_ours(a, rank, world, local, pg):
             variants.append(variant(g, dev, a, w, D, chi, "fp64", 2, 3, flush))
             variants.append(variant(g, dev, a, w, D, chi, a.prec, 3, 3, flush, proj_fp64=1 - a.proj_fp64))
             variants.append(variant(g, dev, a, w, 6, 144, a.prec, 2, 3, flush, proj_fp64=a.proj_fp64))
+            # the same workload with the double-layer site operand (the D^2 index formed)
+            variants.append(variant(g, dev, a, w, D, chi, a.prec, 3, 3, flush, proj_fp64=a.proj_fp64, site_form=2))
+            # sixteen coupling angles at once
+            variants.append(batch_variant(g, dev, a, w, D, chi, a.prec, 3, 16, proj_fp64=a.proj_fp64))
         cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, wl.A0, wl.B0)   # N = 1 only
         sw = sweeps_per_step(a)
         out = {
@@ -368,6 +422,7 @@ def run_ours(a, rank, world, local, pg):
             "config": {"workload": WORKLOAD, "D": D, "chi": chi, "J": w["J"], "K": w["K"], "dbeta": w["dbeta"],
                        "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
                        "prec": a.prec, "projector_svd": "fp64" if (a.proj_fp64 or a.prec == "fp64") else "fp32",
+                       "site_contraction": site_form_name(a.prec, 0, D),
                        "svd_cut": wl.ctx.cfg.svd_cut, "svd_iters_warm": wl.ctx.cfg.svd_iters_warm,
                        "parallelism": "replicas x%d" % world,
                        "l2": "flushed between timed steps (256 MB write outside the timed events)"},
@@ -378,6 +433,7 @@ def run_ours(a, rank, world, local, pg):
             "roofline": roofs.get("corners"),
             "roofline_half_system_product": roofs.get("half_system_product"),
             "roofline_absorb": roofs.get("absorb"),
+            "roofline_site_layer": roofs.get("site_layer"),
             "roofline_projector_orth": roofs.get("cholqr_orth"),
             "profile": prof,
             "variants": variants,

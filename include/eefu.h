@@ -92,6 +92,15 @@ typedef struct kh_config {
                                 FP64; the products with the contraction data stay
                                 in the contraction precision.  The FP64 mode
                                 always computes in FP64.                        */
+    int site_form;           /* two-layer site contraction of the corners and
+                                edges: 0 = automatic (layered, ket then bra, on
+                                the tensor cores in the TF32 precisions; on the
+                                CUDA cores the double-layer operand where
+                                D^2 <= 2p, which halves the flops), 1 = layered
+                                always, 2 = the double-layer operand wherever
+                                D^2 <= 2p.  The layered tensor-core form keeps
+                                the chi^2 D^4 p intermediate on chip; the
+                                layered CUDA-core form writes it to scratch.   */
 } kh_config;
 
 typedef struct kh_ctx kh_ctx;   /* opaque; host memory owned by the library */
@@ -264,6 +273,23 @@ kh_status eefu_evolve(kh_ctx* ctx, double J, const double* host_K_xyz, double hA
                       int n_steps, int measure_every, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
                       int obs_max_sweeps, int obs_min_sweeps, double obs_tol, double* host_traj);
 
+/* Batched trajectories: n independent problems (different couplings, or
+ * different D / chi / precision per context) advanced concurrently, one host
+ * thread per context, each context's kernels on its own streams, so that the
+ * problems' latency-bound launches overlap on the GPU.  Problem i runs
+ * eefu_evolve on ctxs[i] with couplings J[i], K_xyz[3i..3i+2], hA[i], hB[i]
+ * (hA, hB may be null: no field) and the shared step settings; its trajectory
+ * goes to host_traj + i (n_steps / measure_every) 13 doubles in the layout of
+ * eefu_evolve.  The contexts must be distinct.  status (host, n entries, may
+ * be null) receives each problem's status; the return value is the first
+ * non-OK one (each context's message in its kh_last_error).  Returns after
+ * every context's work has completed. */
+kh_status eefu_evolve_batch(kh_ctx* const* ctxs, int n, const double* J, const double* K_xyz,
+                            const double* hA, const double* hB, double dbeta, int n_steps,
+                            int measure_every, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
+                            int obs_max_sweeps, int obs_min_sweeps, double obs_tol, double* host_traj,
+                            kh_status* status);
+
 /* --- instrumentation (no counterpart in the paper; used by the benchmark) -- */
 
 /* Number of kernels this library has launched since it was loaded. */
@@ -329,6 +355,23 @@ kh_status kh_selftest_svd_refined(int k, const double* dev_X, double* dev_S, dou
  * Synchronises stream. */
 kh_status kh_selftest_orth(int prec, int n, int k, double cut, const double* dev_Y, double* dev_Q,
                            void* dev_scratch, size_t scratch_bytes, void* stream);
+
+/* Layered two-layer site contraction on the tensor cores (Fig. 4 and Sec. III:
+ * the enlarged-corner and edge contractions with ket and bra layers applied
+ * one after the other, the chi^2 D^4 p intermediate kept on chip):
+ *   dev_out[b][ok][ob] = sum_p sum_{ik,ib} TL[ik][p][ok] dev_Y[b][ib][ik] TL[ib][p][ob]
+ * for b < nb, all row-major FP64 (computed from FP32 copies), where ik, ib, ok,
+ * ob index D^2 leg pairs and TL is the site tensor dev_T[p][l][u][r][d] seen
+ * from frame `frame` (0..3, each a quarter turn (l,u,r,d) <- (d,l,u,r) of the
+ * previous): kind 0 (corner) TL[(l,u)][p][(r,d)], kind 1 (edge)
+ * TL[(l,d)][p][(u,r)].  npass 1 = TF32, 3 = 3xTF32.  dev_scratch holds at
+ * least kh_selftest_site_layered_bytes(npass, D, p, nb) bytes (0 = invalid
+ * arguments).  KH_ETIMEOUT if a wait in the kernel timed out.  Synchronises
+ * stream. */
+size_t kh_selftest_site_layered_bytes(int npass, int D, int p, long long nb);
+kh_status kh_selftest_site_layered(int npass, int D, int p, int kind, int frame, long long nb,
+                                   const double* dev_T, const double* dev_Y, double* dev_out,
+                                   void* dev_scratch, size_t scratch_bytes, void* stream);
 
 /* FP64 reciprocal, reciprocal square root and square root as the library's
  * latency-bound FP64 kernels form them (Newton-Raphson iteration from the FP32

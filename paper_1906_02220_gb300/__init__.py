@@ -26,9 +26,9 @@ ABI_FUNCTIONS = [
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "ctm_correlation_length", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
-    "eefu_trotter_step", "eefu_evolve", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
+    "eefu_trotter_step", "eefu_evolve", "eefu_evolve_batch", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
     "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_svd_refined", "kh_selftest_orth", "kh_selftest_fp64_newton",
-    "kh_gemm_noalloc",
+    "kh_selftest_site_layered_bytes", "kh_selftest_site_layered", "kh_gemm_noalloc",
     "kh_gemm_noalloc_max_bytes", "kh_save", "kh_load_config", "kh_load",
 ]
 
@@ -39,7 +39,7 @@ class KhConfig(ctypes.Structure):
         ("p_max", ctypes.c_int), ("svd_oversample", ctypes.c_int), ("svd_iters_cold", ctypes.c_int),
         ("svd_iters_warm", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int), ("svd_cut", ctypes.c_double),
         ("als_tol", ctypes.c_double), ("als_max_iter", ctypes.c_int), ("als_reg", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("proj_fp64", ctypes.c_int),
+        ("seed", ctypes.c_uint64), ("proj_fp64", ctypes.c_int), ("site_form", ctypes.c_int),
     ]
 
 
@@ -83,6 +83,7 @@ def load_library(path=LIB_PATH):
         "kh_gate": (I, [dp, D, dp]),
         "eefu_trotter_step": (I, [P, D, dp, D, D, D, I, I, D, dp]),
         "eefu_evolve": (I, [P, D, dp, D, D, D, I, I, I, I, D, I, I, D, dp]),
+        "eefu_evolve_batch": (I, [ctypes.POINTER(P), I, dp, dp, dp, dp, D, I, I, I, I, D, I, I, D, dp, ip]),
         "kh_launch_count": (ctypes.c_ulonglong, []),
         "kh_profile": (I, [P, I, dp]),
         "kh_selftest_bytes": (S, [I, I, I]),
@@ -92,6 +93,8 @@ def load_library(path=LIB_PATH):
         "kh_selftest_orth": (I, [I, I, I, D, P, P, P, S, P]),
         "kh_selftest_svd_refined": (I, [I, P, P, P, P, P, S, P]),
         "kh_selftest_fp64_newton": (I, [I, P, P, P]),
+        "kh_selftest_site_layered_bytes": (S, [I, I, I, ctypes.c_longlong]),
+        "kh_selftest_site_layered": (I, [I, I, I, I, I, ctypes.c_longlong, P, P, P, P, S, P]),
         "kh_gemm_noalloc": (I, [I, I, I, I, P, P, P, P]),
         "kh_gemm_noalloc_max_bytes": (S, []),
         "kh_save": (I, [P, ctypes.c_char_p]),
@@ -180,6 +183,27 @@ def selftest_svd_refined(X):
     if st != KH_OK:
         raise KhError(st, "kh_selftest_svd_refined")
     return S, L, Q
+
+
+def selftest_site_layered(T, Y, kind=0, frame=0, npass=3):
+    """Layered tensor-core site contraction of one (kind, frame):
+    out[b][ok][ob] = sum_p sum_{ik,ib} TL[ik][p][ok] Y[b][ib][ik] TL[ib][p][ob]
+    from the FP64 CUDA tensors T (p, D, D, D, D) and Y (nb, D^2, D^2)."""
+    import torch
+    p, D = T.shape[0], T.shape[1]
+    nb = Y.shape[0]
+    out = torch.empty((nb, D * D, D * D), dtype=torch.float64, device=Y.device)
+    nbytes = lib().kh_selftest_site_layered_bytes(npass, D, p, nb)
+    if nbytes == 0:
+        raise KhError(KH_EINVAL, "kh_selftest_site_layered_bytes")
+    scr = torch.empty(nbytes + 256, dtype=torch.uint8, device=Y.device)
+    base = (scr.data_ptr() + 255) // 256 * 256
+    st = lib().kh_selftest_site_layered(npass, D, p, kind, frame, nb, _tptr(T.contiguous()), _tptr(Y.contiguous()),
+                                        _tptr(out), ctypes.c_void_p(base), nbytes,
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != KH_OK:
+        raise KhError(st, "kh_selftest_site_layered")
+    return out
 
 
 def selftest_orth(Y, prec="fp64", cut=1e-12):
@@ -499,3 +523,33 @@ class Context:
         self._check(lib().observables(self._ctx, hp, hA, hB, ctm_max_sweeps, ctm_min_sweeps, ctm_tol, op))
         keys = ["E_site", "Hx", "Hy", "Hz", "Ax", "Ay", "Az", "Bx", "By", "Bz", "trunc", "sweeps"]
         return dict(zip(keys, o.tolist()))
+
+
+def evolve_batch(contexts, J, K_xyz, dbeta, n_steps, measure_every=1, hA=None, hB=None, ctm_max_sweeps=100,
+                 ctm_min_sweeps=1, ctm_tol=1e-12, obs_max_sweeps=None, obs_min_sweeps=None, obs_tol=None):
+    """Trajectories of several independent problems advanced concurrently
+    (eefu_evolve_batch): contexts[i] with couplings J[i], K_xyz[i] (3 values),
+    hA[i], hB[i].  Returns one list of TRAJ_KEYS dicts per problem; raises
+    KhError with the first failing problem's message."""
+    n = len(contexts)
+    keys = Context.TRAJ_KEYS
+    nm = n_steps // measure_every
+    out = np.zeros(n * max(nm, 1) * len(keys))
+    o, op = _dptr(out)
+    Jv, jp = _dptr(np.asarray(J, dtype=np.float64).reshape(n))
+    Kv, kp = _dptr(np.asarray(K_xyz, dtype=np.float64).reshape(n * 3))
+    ha, hap = _dptr(np.zeros(n) if hA is None else np.asarray(hA, dtype=np.float64).reshape(n))
+    hb, hbp = _dptr(np.zeros(n) if hB is None else np.asarray(hB, dtype=np.float64).reshape(n))
+    arr = (ctypes.c_void_p * n)(*[c._ctx.value for c in contexts])
+    stat = (ctypes.c_int * n)()
+    st = lib().eefu_evolve_batch(ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), n, jp, kp, hap, hbp, dbeta,
+                                 n_steps, measure_every, ctm_max_sweeps, ctm_min_sweeps, ctm_tol,
+                                 obs_max_sweeps or ctm_max_sweeps, obs_min_sweeps or ctm_min_sweeps,
+                                 ctm_tol if obs_tol is None else obs_tol, op, stat)
+    if st != KH_OK:
+        bad = [i for i in range(n) if stat[i] != KH_OK]
+        if not bad:
+            raise KhError(st, "eefu_evolve_batch: invalid arguments")
+        raise KhError(st, "problem %d: %s" % (bad[0], lib().kh_last_error(contexts[bad[0]]._ctx).decode()))
+    rows = o.reshape(n, max(nm, 1), len(keys))[:, :nm]
+    return [[dict(zip(keys, r.tolist())) for r in prob] for prob in rows]

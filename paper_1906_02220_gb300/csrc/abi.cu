@@ -2,6 +2,8 @@
 // include/eefu.h).  Every entry point converts internal errors into a
 // kh_status and a one-line message; nothing throws across the boundary.
 #include <cmath>
+#include <thread>
+#include <vector>
 
 #include "engine.cuh"
 
@@ -12,6 +14,7 @@ std::atomic<unsigned long long> g_launches{0};
 struct kh_ctx {
     kh::EngineBase* eng = nullptr;
     std::string err;
+    int device = 0;           // device current at creation
 };
 
 namespace {
@@ -150,6 +153,7 @@ kh_status kh_create(kh_ctx** out, const kh_config* c, void* ws, size_t bytes, vo
         if (bytes < need) kh::fail(KH_ENOMEM, "workspace smaller than kh_workspace_bytes()");
         if (c->prec == KH_BF16) kh::fail(KH_EINVAL, "precision not built in this library version");
         cudaStream_t st = (cudaStream_t)stream;
+        KH_CUDA(cudaGetDevice(&ctx->device));
         if (c->prec == KH_FP64) ctx->eng = new kh::Engine<double>(*c, ws, bytes, st);
         else ctx->eng = new kh::Engine<float>(*c, ws, bytes, st);
         KH_CUDA(cudaStreamSynchronize(st));
@@ -414,50 +418,93 @@ kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA
     });
 }
 
+namespace {
+
+// The trajectory of eefu_evolve for one context (throws kh::Error).
+void evolve_one(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta, int n_steps,
+                int measure_every, int mx, int mn, double tol, int obs_mx, int obs_mn, double obs_tol,
+                double* traj) {
+    if (!Kxyz || !traj || mx < 1 || obs_mx < 1 || n_steps < 1 || measure_every < 1 || !(dbeta > 0.0))
+        kh::fail(KH_EINVAL, "bad arguments");
+    static const int order[5] = {0, 1, 2, 1, 0};
+    const double taus[5] = {dbeta / 4, dbeta / 4, dbeta / 2, dbeta / 4, dbeta / 4};
+    double H3[48], G[5][16];
+    for (int g = 0; g < 3; ++g) bond_h(g, J, Kxyz[g], 0.0, 0.0, H3 + 16 * g);
+    for (int l = 0; l < 5; ++l) {
+        double H[16];
+        const int g = order[l];
+        bond_h(g, J, Kxyz[g], g == 2 ? hA : 0.0, g == 2 ? hB : 0.0, H);
+        gate_from_h(H, taus[l], G[l]);
+    }
+    const int nm = n_steps / measure_every;
+    const double beta0 = ctx->eng->beta;
+    for (int n = 1; n <= n_steps; ++n) {
+        for (int l = 0; l < 5; ++l) ctx->eng->apply_gate(order[l], G[l], mx, mn, tol, nullptr);
+        ctx->eng->beta += dbeta;
+        if (n % measure_every == 0) {
+            double* row = traj + (long long)(n / measure_every - 1) * kTrajCols;
+            double out[12];
+            ctx->eng->observables(H3, hA, hB, obs_mx, obs_mn, obs_tol, out);
+            row[0] = beta0 + n * dbeta;
+            for (int i = 0; i < 10; ++i) row[1 + i] = out[i];
+            row[11] = out[10];
+        }
+    }
+    // C = dE/dT = -beta^2 dE/dbeta by central differences on the uniform
+    // measurement grid; NaN at the two ends
+    for (int i = 0; i < nm; ++i) {
+        double* row = traj + (long long)i * kTrajCols;
+        if (i == 0 || i == nm - 1) {
+            row[12] = NAN;
+            continue;
+        }
+        const double* lo = row - kTrajCols;
+        const double* hi = row + kTrajCols;
+        row[12] = -row[0] * row[0] * (hi[1] - lo[1]) / (hi[0] - lo[0]);
+    }
+}
+
+}  // namespace
+
 kh_status eefu_evolve(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta, int n_steps,
                       int measure_every, int mx, int mn, double tol, int obs_mx, int obs_mn, double obs_tol,
                       double* traj) {
     KH_RANGE();
     return guard(ctx, [&] {
-        if (!Kxyz || !traj || mx < 1 || obs_mx < 1 || n_steps < 1 || measure_every < 1 || !(dbeta > 0.0))
-            kh::fail(KH_EINVAL, "bad arguments");
-        static const int order[5] = {0, 1, 2, 1, 0};
-        const double taus[5] = {dbeta / 4, dbeta / 4, dbeta / 2, dbeta / 4, dbeta / 4};
-        double H3[48], G[5][16];
-        for (int g = 0; g < 3; ++g) bond_h(g, J, Kxyz[g], 0.0, 0.0, H3 + 16 * g);
-        for (int l = 0; l < 5; ++l) {
-            double H[16];
-            const int g = order[l];
-            bond_h(g, J, Kxyz[g], g == 2 ? hA : 0.0, g == 2 ? hB : 0.0, H);
-            gate_from_h(H, taus[l], G[l]);
-        }
-        const int nm = n_steps / measure_every;
-        const double beta0 = ctx->eng->beta;
-        for (int n = 1; n <= n_steps; ++n) {
-            for (int l = 0; l < 5; ++l) ctx->eng->apply_gate(order[l], G[l], mx, mn, tol, nullptr);
-            ctx->eng->beta += dbeta;
-            if (n % measure_every == 0) {
-                double* row = traj + (long long)(n / measure_every - 1) * kTrajCols;
-                double out[12];
-                ctx->eng->observables(H3, hA, hB, obs_mx, obs_mn, obs_tol, out);
-                row[0] = beta0 + n * dbeta;
-                for (int i = 0; i < 10; ++i) row[1 + i] = out[i];
-                row[11] = out[10];
-            }
-        }
-        // C = dE/dT = -beta^2 dE/dbeta by central differences on the uniform
-        // measurement grid; NaN at the two ends
-        for (int i = 0; i < nm; ++i) {
-            double* row = traj + (long long)i * kTrajCols;
-            if (i == 0 || i == nm - 1) {
-                row[12] = NAN;
-                continue;
-            }
-            const double* lo = row - kTrajCols;
-            const double* hi = row + kTrajCols;
-            row[12] = -row[0] * row[0] * (hi[1] - lo[1]) / (hi[0] - lo[0]);
-        }
+        evolve_one(ctx, J, Kxyz, hA, hB, dbeta, n_steps, measure_every, mx, mn, tol, obs_mx, obs_mn, obs_tol, traj);
     });
+}
+
+kh_status eefu_evolve_batch(kh_ctx* const* ctxs, int n, const double* J, const double* Kxyz, const double* hA,
+                            const double* hB, double dbeta, int n_steps, int measure_every, int mx, int mn,
+                            double tol, int obs_mx, int obs_mn, double obs_tol, double* traj, kh_status* status) {
+    KH_RANGE();
+    if (!ctxs || n < 1 || !J || !Kxyz || !traj || measure_every < 1 || n_steps < 1) return KH_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i] || !ctxs[i]->eng) return KH_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return KH_EINVAL;          // one thread per context
+    }
+    const long long rows = (long long)(n_steps / measure_every) * kTrajCols;
+    std::vector<kh_status> st(n, KH_OK);
+    std::vector<std::thread> pool;
+    pool.reserve(n);
+    for (int i = 0; i < n; ++i)
+        pool.emplace_back([&, i] {
+            kh_ctx* c = ctxs[i];
+            st[i] = guard(c, [&] {
+                KH_CUDA(cudaSetDevice(c->device));
+                evolve_one(c, J[i], Kxyz + 3 * i, hA ? hA[i] : 0.0, hB ? hB[i] : 0.0, dbeta, n_steps,
+                           measure_every, mx, mn, tol, obs_mx, obs_mn, obs_tol, traj + i * rows);
+            });
+        });
+    for (auto& t : pool) t.join();
+    kh_status first = KH_OK;
+    for (int i = 0; i < n; ++i) {
+        if (status) status[i] = st[i];
+        if (first == KH_OK && st[i] != KH_OK) first = st[i];
+    }
+    return first;
 }
 
 unsigned long long kh_launch_count(void) { return kh::g_launches.load(std::memory_order_relaxed); }

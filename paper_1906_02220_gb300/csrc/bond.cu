@@ -12,6 +12,7 @@
 // subproblems (R + reg tr(R)/m I) X = S (FP64 Cholesky); balanced gauge from
 // the Gram matrices of A'' and B''.
 #include "engine.cuh"
+#include "layered.cuh"
 
 namespace kh {
 
@@ -133,6 +134,66 @@ __global__ void wt_kernel(const double* __restrict__ Tm, int p, int D, T* Wc, T*
     }
 }
 
+// Operand images of the layered tensor-core site contraction (layered.cuh)
+// for kind 0 (corner, TL = [L,U][p][R,D]) and kind 1 (edge, TL = [L,D][p][U,R])
+// of frame f.  Per chunk c of pc physical indices, the ket image
+//   B1_c[(pl, ok)][ik] = TL_f[ik][c pc + pl][ok]
+// and the bra image
+//   B2_c[ob][(ib, pl)] = TL_f[ib][c pc + pl][ob],
+// each stored byte for byte as its 128-byte-swizzled K-major shared-memory
+// tile (the TF32 head, then the FP32 remainder, with 3 passes), zero outside
+// the operand.  Layout [kind][frame][chunk][hi, lo], per1 / per2 floats per
+// (kind, frame).
+__global__ void layered_img_kernel(const double* __restrict__ Tm, int p, int D, lay::Plan P, int npass,
+                                   float* __restrict__ img1, float* __restrict__ img2, long long per1,
+                                   long long per2) {
+    const int npl = npass == 3 ? 2 : 1;
+    const long long tot1 = 8 * per1, tot = tot1 + 8 * per2;
+    const long long D4 = (long long)D * D * D * D;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool ket = i < tot1;
+        const long long e = ket ? i : i - tot1;
+        const long long per = ket ? per1 : per2;
+        const int kf = (int)(e / per), kind = kf >> 2, f = kf & 3;
+        const long long rem = e % per;
+        const int sub = (ket ? P.b1_bytes : P.b2_bytes) / 4;      // floats of one hi or lo image
+        const int idx = (int)(rem / sub), c = idx / npl, hl = idx % npl;
+        int r, k;
+        lay::swz_position((int)(rem % sub) * 4, ket ? P.n1p : P.n2p, r, k);
+        int in = -1, out = -1, pp = p;
+        if (ket && r < P.n1 && k < P.d2) {                 // row (pl, ok), column ik
+            in = k;
+            out = r % P.d2;
+            pp = c * P.pc + r / P.d2;
+        } else if (!ket && r < P.d2 && k < P.k2) {         // row ob, column (ib, pl)
+            in = k / P.pc;
+            out = r;
+            pp = c * P.pc + k % P.pc;
+        }
+        double v = 0.0;
+        if (in >= 0 && pp < p) {
+            const int off = kind == 0 ? frame_offset(f, in / D, in % D, out / D, out % D, D)
+                                      : frame_offset(f, in / D, out / D, out % D, in % D, D);
+            v = Tm[pp * D4 + off];
+        }
+        float x = (float)v;
+        if (npass == 3) {
+            const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+            x = hl == 0 ? h : x - h;
+        }
+        (ket ? img1 : img2)[e] = x;
+    }
+}
+
+void build_layered_images(const double* Tm, int p, int D, int npass, float* img1, float* img2, long long per1,
+                          long long per2, cudaStream_t st) {
+    const long long tot = 8 * (per1 + per2);
+    layered_img_kernel<<<grid_for(tot), 256, 0, st>>>(Tm, p, D, lay::make_plan(D, npass), npass, img1, img2, per1,
+                                                      per2);
+    KH_LAUNCHED();
+}
+
 template <typename T>
 void Engine<T>::build_derived(Slot<T>& sl) {
     int tot = 4 * sl.p * dm.D4;
@@ -140,6 +201,8 @@ void Engine<T>::build_derived(Slot<T>& sl) {
     KH_LAUNCHED();
     // the double-layer form costs D^8 per block against 2 p D^6 layer by layer
     sl.dl = dm.dl_alloc && dm.d2 <= 2 * sl.p;
+    if (dm.lay && !sl.dl)
+        build_layered_images(sl.Ts, sl.p, dm.D, dm.npass, (float*)sl.L1, (float*)sl.L2, dm.lay1, dm.lay2, st);
     if (sl.dl) {
         const bool split = sizeof(T) == 4 && tc_npass == 3 && dm.D4 % 4 == 0;
         const long long tot8 = 8LL * dm.D4 * dm.D4;

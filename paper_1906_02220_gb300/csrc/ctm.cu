@@ -16,6 +16,7 @@
 //   each divided by its Frobenius norm (FP64).
 #define KH_JACOBI_KERNEL
 #include "engine.cuh"
+#include "layered.cuh"
 
 namespace kh {
 
@@ -32,6 +33,7 @@ void validate(const kh_config& c) {
     if (c.jacobi_max_sweeps < 1) fail(KH_EINVAL, "jacobi_max_sweeps < 1");
     if (!(c.svd_cut >= 0.0) || !(c.als_reg >= 0.0) || c.als_max_iter < 0) fail(KH_EINVAL, "bad tolerances");
     if (c.proj_fp64 != 0 && c.proj_fp64 != 1) fail(KH_EINVAL, "proj_fp64 must be 0 or 1");
+    if (c.site_form < 0 || c.site_form > 2) fail(KH_EINVAL, "site_form must be 0, 1 or 2");
 }
 
 Dims make_dims(const kh_config& c, bool fp64) {
@@ -43,7 +45,15 @@ Dims make_dims(const kh_config& c, bool fp64) {
     d.n = c.chi * d.d2;
     d.pmax = c.p_max;
     d.nslots = c.n_slots;
-    d.dl_alloc = d.d2 <= 2 * c.p_max;
+    d.npass = fp64 ? 0 : (c.prec == KH_TF32 ? 1 : (c.prec == KH_TF32X3 ? 3 : 0));
+    // site contraction form: layered on the tensor cores unless the double-layer
+    // operand is asked for; on the CUDA cores the double-layer operand where it
+    // halves the flops, unless the layered form is asked for
+    d.dl_alloc = d.d2 <= 2 * c.p_max && (c.site_form == 2 || (c.site_form == 0 && d.npass == 0));
+    d.lay = d.npass != 0;
+    d.lay1 = d.lay ? layered_img1_floats(c.D, c.p_max, d.npass) : 0;
+    d.lay2 = d.lay ? layered_img2_floats(c.D, c.p_max, d.npass) : 0;
+    if (d.lay && (d.lay1 == 0 || d.lay2 == 0)) fail(KH_EINVAL, "no tensor-core plan for this D");
     int kmax = fp64 ? 112 : 160;      // the one-CTA Jacobi limits (FP64, FP32)
     if (d.n <= kmax) {
         d.kk = d.n;
@@ -79,6 +89,10 @@ void Engine<T>::layout(Carver& cv) {
                 s.Wcor_lo = cv.take<T>(w);
                 s.Wedg_lo = cv.take<T>(w);
             }
+        }
+        if (d.lay) {
+            s.L1 = cv.take<T>(8 * d.lay1);
+            s.L2 = cv.take<T>(8 * d.lay2);
         }
         s.Vw = cv.take<T>(4 * n * kk);
         s.spec = cv.take<double>(4LL * d.chi);
@@ -129,7 +143,9 @@ void Engine<T>::carve_lane(Carver& cv) {
     X1[1] = cv.take<T>(E1);
     Y1 = cv.take<T>(n2);
     Yp = cv.take<T>(n2);
-    Zk = cv.take<T>((long long)d.pmax * n2);
+    // the layered CUDA-core form's chi^2 D^4 p intermediate (the tensor-core
+    // form keeps it on chip)
+    Zk = d.lay ? nullptr : cv.take<T>((long long)d.pmax * n2);
     Qt = cv.take<T>(n2);
     Q[0] = cv.take<T>(n2);
     Q[1] = cv.take<T>(n2);
@@ -573,10 +589,16 @@ void Engine<T>::site_operand(const Slot<T>& sl, const T* Y, T* Yp, const std::ve
 }
 
 template <typename T>
-void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo,
-                           bool presplit) {
+void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, const T* L1, const T* L2, int p, T* out,
+                           const T* Wt, const T* Wt_lo, bool presplit) {
     const int d2 = dm.d2, d4 = dm.D4;
     prof_begin(1);
+    if (!Wt && L1) {                                   // layered, on the tensor cores
+        site_layered_tc((const float*)Ybuf, nb, dm.D, p, (const float*)L1, (const float*)L2, (float*)out,
+                        tc_npass, tc_err, st);
+        prof_end(1, 4.0 * (double)nb * p * d2 * (double)d2 * d2);
+        return;
+    }
     if (Wt) {
         if (tc_npass && sizeof(T) == 4 && d4 % 4 == 0) {       // TMA rows must be 16-byte multiples
             TcOperand a{(const float*)Ybuf, nullptr, d4}, b{(const float*)Wt, nullptr, d4};
@@ -619,7 +641,8 @@ void Engine<T>::corner(Slot<T>& sl, int f, int which) {
     gemm_rm<T>(chi * d2, d2 * chi, chi, E4, false, X, false, Y1, st);        // [(w,lk,lb)][(uk,ub,z)]
     site_operand(sl, Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3});     // [w][z][lb][ub][lk][uk]
     const long long w4 = (long long)f * dm.D4 * dm.D4;
-    site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wcor + w4 : nullptr,
+    site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, lay_img(sl, 1, 0, f), lay_img(sl, 2, 0, f), sl.p,
+               Qt, sl.dl ? sl.Wcor + w4 : nullptr,
                sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr, site_presplit(sl));   // [w][z][rk][dk][rb][db]
     // Q_0 stored transposed, [(z,rk,rb)][(w,dk,db)], as the K-major operand of
     // Mt = Q_{s+3} Q_s on tensor cores; with 3xTF32 the (hi, lo) pairs of both
@@ -987,7 +1010,8 @@ void Engine<T>::absorb(Slot<T>& sl, int s) {
     gemm_rm<T>(d2 * chi, d2 * chi, chi, E4, true, P, false, Y1, st);             // [(lk,lb,x4)][(dk,db,a)]
     site_operand(sl, Y1, Yp, {D, D, chi, D, D, chi}, {2, 5, 1, 4, 0, 3});         // [x4][a][lb][db][lk][dk]
     const long long w4 = (long long)s * dm.D4 * dm.D4;
-    site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wedg + w4 : nullptr,
+    site_layer(Yp, chi2, sl.Tedg + (long long)s * dm.pmax * dm.D4, lay_img(sl, 1, 1, s), lay_img(sl, 2, 1, s), sl.p,
+               Qt, sl.dl ? sl.Wedg + w4 : nullptr,
                sl.dl && sl.Wedg_lo ? sl.Wedg_lo + w4 : nullptr, site_presplit(sl));   // [x4][a][uk][rk][ub][rb]
     permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {1, 3, 5, 0, 2, 4}, st);       // [a][rk][rb][x4][uk][ub]
     gemm_rm<T>(chi * d2, chi, n, Y1, false, PtT, false, E4n, st, T(1), T(0), nullptr, skbuf, sk_elems);   // [a][rk][rb][a_up]

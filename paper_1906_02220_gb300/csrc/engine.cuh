@@ -23,6 +23,10 @@ struct Slot {
     T* Wcor_lo = nullptr;
     T* Wedg_lo = nullptr;
     bool dl = false;          // the loaded tensor uses the double-layer operands
+    // operand images of the layered tensor-core site contraction (layered.cuh):
+    // [kind (corner, edge)][frame][chunk][hi, lo], ket images in L1, bra in L2
+    T* L1 = nullptr;
+    T* L2 = nullptr;
     T* Vw = nullptr;          // 4 dirs x n x kk  (warm projector subspaces)
     double* spec = nullptr;   // 4 x chi  last kept spectra (descending)
     double* prev = nullptr;   // 4 x chi  normalised spectra of the previous sweep
@@ -38,7 +42,10 @@ struct Slot {
 struct Dims {
     int D, d2, D4, chi, n, kk, pmax, nslots;
     bool full;                 // kk == n: exact Rayleigh-Ritz on the whole space
-    bool dl_alloc;             // D^2 <= 2 p_max: double-layer operands allocated
+    bool dl_alloc;             // double-layer operands allocated (D^2 <= 2 p_max and the site form allows)
+    bool lay;                  // layered tensor-core site contraction (tensor-core precisions)
+    int npass;                 // tensor-core passes: 0 (CUDA cores), 1 (TF32), 3 (3xTF32)
+    long long lay1, lay2;      // floats per (kind, frame) of the ket and bra operand images
 };
 
 // ------------------------------------------------------------------ engine
@@ -224,9 +231,17 @@ struct Engine : EngineBase {
     // CTM internals
     void refresh_operands(Slot<T>& sl);
     void corner(Slot<T>& sl, int frame, int which);
-    void site_layer(const T* Ybuf, long long nb, const T* TL, int p, T* out, const T* Wt, const T* Wt_lo,
+    void site_layer(const T* Ybuf, long long nb, const T* TL, const T* L1, const T* L2, int p, T* out,
+                    const T* Wt, const T* Wt_lo,
                     bool presplit = false);
     bool site_presplit(const Slot<T>& sl) const;
+    // operand image (1 = ket, 2 = bra) of the layered tensor-core contraction
+    // for (kind: 0 corner, 1 edge; frame f), or null when the slot uses
+    // another form
+    const T* lay_img(const Slot<T>& sl, int img, int kind, int f) const {
+        if (sl.dl || !sl.L1) return nullptr;
+        return img == 1 ? sl.L1 + (kind * 4 + f) * dm.lay1 : sl.L2 + (kind * 4 + f) * dm.lay2;
+    }
     void site_operand(const Slot<T>& sl, const T* Y, T* Yp, const std::vector<long long>& shape,
                       const std::vector<int>& order);
     void projector(Slot<T>& sl, int dir, int slot_id);

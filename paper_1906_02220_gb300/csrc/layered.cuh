@@ -1,0 +1,121 @@
+// Layered two-layer site contraction on the tensor cores: the shapes and the
+// operand images shared by the kernel (layered.cu) and by the image builder
+// (bond.cu).
+//
+// For nb blocks b (the chi^2 environment index pairs of an enlarged corner or
+// an edge) the contraction is
+//   out[b][ok][ob] = sum_p sum_{ik,ib} TL[ik][p][ok] Y[b][ib][ik] TL[ib][p][ob]
+// with ik, ib, ok, ob pairs of virtual legs (D^2 values each) and p the
+// physical index.  It runs as two GEMMs per tile of rows (b, ib):
+//   ket layer  Z[(b,ib)][(p,ok)]  = sum_ik Y[(b,ib)][ik] TL[ik][(p,ok)]
+//   bra layer  out[(b,ok)][ob]   += sum_(ib,p) Z[(b,ok)][(ib,p)] TL[(ib,p)][ob]
+// over chunks of pc physical indices.  Z never leaves the SM: the ket GEMM
+// accumulates it in tensor memory, the worker warps move it through shared
+// memory into the (b,ok)-row layout, and the bra GEMM reads it back from
+// tensor memory as its A operand.  The D^2 x D^2 double-layer index is never
+// formed.
+#pragma once
+
+namespace kh {
+namespace lay {
+
+__host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+// Tile shapes for bond dimension D (D^2 = d2) and 1 or 3 MMA passes.
+struct Plan {
+    int d2 = 0, bt = 0, rows = 0;            // D^2; blocks b per tile; rows (b, ib) used of 128
+    int pc = 0, na2 = 0;                     // physical indices per chunk; Z buffers in tensor memory
+    int n1 = 0, n1p = 0, k1p = 0, kb1 = 0;   // ket GEMM: N = pc D^2 (padded to 16), K = D^2 (padded to 8)
+    int n2p = 0, k2 = 0, k2p = 0, kb2 = 0;   // bra GEMM: N = D^2 (padded to 16), K = pc D^2 (padded to 8)
+    int zs = 0;                              // row stride (floats) of the shared-memory transpose buffer
+    int c_acc1 = 0, c_a2 = 0, a2_cols = 0, c_out = 0, tmem = 0;   // tensor-memory columns
+    int a1_bytes = 0, b1_bytes = 0, b2_bytes = 0;                 // one (hi or lo) operand image
+};
+
+// Largest chunk pc (a power of two <= 16) whose two ket accumulators, Z
+// buffers (hi and lo for 3 passes) and the output accumulator fit the 512
+// tensor-memory columns with every region 32-column aligned; two Z buffers
+// when they fit, else one.  Shared-memory operands use the 128-byte-swizzle
+// K-major layout in K blocks of 32 FP32 values.
+__host__ __device__ constexpr Plan make_plan(int D, int npass) {
+    Plan P{};
+    P.d2 = D * D;
+    P.bt = P.d2 > 0 ? 128 / P.d2 : 0;
+    P.rows = P.bt * P.d2;
+    P.k1p = pad_to(P.d2, 8);
+    P.kb1 = (P.k1p + 31) / 32;
+    P.n2p = pad_to(P.d2, 16);
+    const int npl = npass == 3 ? 2 : 1;
+    if (P.bt < 1) return P;
+    for (int pc = 16; pc >= 1; pc /= 2) {
+        const int n1p = pad_to(pc * P.d2, 16);
+        if (n1p > 256) continue;
+        const int k2p = pad_to(pc * P.d2, 8);
+        for (int na2 = 2; na2 >= 1; --na2) {
+            const int cols = 2 * pad_to(n1p, 32) + na2 * npl * pad_to(k2p, 32) + pad_to(P.n2p, 32);
+            if (cols > 512) continue;
+            P.pc = pc;
+            P.na2 = na2;
+            P.n1 = pc * P.d2;
+            P.n1p = n1p;
+            P.k2 = pc * P.d2;
+            P.k2p = k2p;
+            P.kb2 = (k2p + 31) / 32;
+            P.zs = pad_to(P.k2, 4);
+            if ((P.zs / 4) % 2 == 0) P.zs += 4;          // odd 16-byte stride: conflict-free row reads
+            P.c_acc1 = 0;
+            P.c_a2 = 2 * pad_to(n1p, 32);
+            P.a2_cols = pad_to(k2p, 32);
+            P.c_out = P.c_a2 + na2 * npl * P.a2_cols;
+            P.tmem = 32;
+            while (P.tmem < P.c_out + pad_to(P.n2p, 32)) P.tmem *= 2;
+            P.a1_bytes = 128 * P.kb1 * 128;
+            P.b1_bytes = n1p * P.kb1 * 128;
+            P.b2_bytes = P.n2p * P.kb2 * 128;
+            return P;
+        }
+    }
+    return P;
+}
+
+// Byte offset of element (row r, k) in a K-major operand of `rows` rows with
+// 128-byte swizzle: K blocks of 32 values, each block rows x 128 bytes, the
+// 16-byte chunks of row r permuted by r mod 8.
+__host__ __device__ inline int swz_offset(int r, int k, int rows) {
+    const int kb = k >> 5, kc = k & 31;
+    return kb * rows * 128 + r * 128 + ((((kc >> 2) ^ (r & 7)) << 4) | ((kc & 3) << 2));
+}
+
+// Inverse of swz_offset for a 4-byte-aligned offset o: (row, k).
+__host__ __device__ inline void swz_position(int o, int rows, int& r, int& k) {
+    const int kb = o / (rows * 128), rem = o % (rows * 128);
+    r = rem / 128;
+    const int ch = (rem % 128) >> 4;
+    k = kb * 32 + (((ch ^ (r & 7)) << 2) | ((rem & 15) >> 2));
+}
+
+// Chunks of pc physical indices covering p.
+__host__ __device__ inline int n_chunks(const Plan& P, int p) { return (p + P.pc - 1) / P.pc; }
+
+}  // namespace lay
+
+// Image sizes (floats) of one (kind, frame) operand set for p physical
+// indices: ket images of all chunks, then bra images (hi, lo per chunk with
+// 3 passes).  Zero when D has no tensor-core plan.
+long long layered_img1_floats(int D, int p, int npass);
+long long layered_img2_floats(int D, int p, int npass);
+
+// Operand images of all (kind, frame) pairs from the FP64 site tensor
+// Tm[p][D^4] (legs l, u, r, d of frame 0): img1 holds 8 x per1 floats, img2
+// 8 x per2 (per1, per2 at least layered_img1_floats / layered_img2_floats for
+// p), layout [kind][frame][chunk][hi, lo].
+void build_layered_images(const double* Tm, int p, int D, int npass, float* img1, float* img2, long long per1,
+                          long long per2, cudaStream_t st);
+
+// out[b][ok][ob] (row-major, nb x D^2 x D^2) from Y[b][ib][ik] (row-major,
+// nb x D^2 x D^2) and the operand images of one (kind, frame).  Tensor-core
+// passes npass = 1 (TF32) or 3 (3xTF32).  Time-outs set bits of *err.
+void site_layered_tc(const float* Y, long long nb, int D, int p, const float* img1, const float* img2, float* out,
+                     int npass, int* err, cudaStream_t st);
+
+}  // namespace kh

@@ -2,6 +2,7 @@
 // run one library kernel on caller-provided device data so that tests can
 // pin it directly against a host reference.
 #include "engine.cuh"
+#include "layered.cuh"
 
 namespace {
 
@@ -87,6 +88,44 @@ void run_orth(int n, int k, double cut, const double* Y, double* Q, void* scratc
     kh::cast<double, T>(Y, y, (long long)n * k, st);
     kh::cholqr2<T>(y, n, k, cut, tmp, xk, dg, u, st);
     kh::cast<T, double>(u, Q, (long long)n * k, st);
+}
+
+// Layered tensor-core site contraction of one (kind, frame): operand images
+// from the FP64 site tensor, Y cast to FP32, out cast back to FP64.
+struct LayeredScratch {
+    float *img1, *img2, *y, *out;
+    int* err;
+    long long per1, per2;
+};
+
+LayeredScratch carve_layered(kh::Carver& cv, int npass, int D, int p, long long nb) {
+    LayeredScratch L;
+    L.per1 = kh::layered_img1_floats(D, p, npass);
+    L.per2 = kh::layered_img2_floats(D, p, npass);
+    const long long d4 = (long long)D * D * D * D;
+    L.img1 = cv.take<float>((size_t)(8 * L.per1));
+    L.img2 = cv.take<float>((size_t)(8 * L.per2));
+    L.y = cv.take<float>((size_t)(nb * d4));
+    L.out = cv.take<float>((size_t)(nb * d4));
+    L.err = cv.take<int>(64);
+    return L;
+}
+
+void run_site_layered(int npass, int D, int p, int kind, int frame, long long nb, const double* T, const double* Y,
+                      double* out, void* scratch, size_t bytes, cudaStream_t st) {
+    kh::Carver cv(scratch, bytes);
+    LayeredScratch L = carve_layered(cv, npass, D, p, nb);
+    const long long d4 = (long long)D * D * D * D;
+    KH_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
+    kh::build_layered_images(T, p, D, npass, L.img1, L.img2, L.per1, L.per2, st);
+    kh::cast<double, float>(Y, L.y, nb * d4, st);
+    const int kf = kind * 4 + frame;
+    kh::site_layered_tc(L.y, nb, D, p, L.img1 + kf * L.per1, L.img2 + kf * L.per2, L.out, npass, L.err, st);
+    kh::cast<float, double>(L.out, out, nb * d4, st);
+    int h = 0;
+    KH_CUDA(cudaMemcpyAsync(&h, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+    if (h) kh::fail(KH_ETIMEOUT, "layered site contraction wait timed out");
 }
 
 // FP32 one-sided Jacobi, then one FP64 Newton refinement step (the projector
@@ -198,6 +237,23 @@ kh_status kh_selftest_svd_refined(int k, const double* X, double* S, double* L, 
         run_svd_refined(k, X, S, L, Qm, scratch, bytes, st);
         KH_CUDA(cudaStreamSynchronize(st));
     });
+}
+
+size_t kh_selftest_site_layered_bytes(int npass, int D, int p, long long nb) {
+    if ((npass != 1 && npass != 3) || D < 1 || D > 8 || p < 1 || p > 16 || nb < 0) return 0;
+    kh::Carver cv;
+    carve_layered(cv, npass, D, p, nb);
+    return cv.off;
+}
+
+kh_status kh_selftest_site_layered(int npass, int D, int p, int kind, int frame, long long nb, const double* T,
+                                   const double* Y, double* out, void* scratch, size_t bytes, void* stream) {
+    if ((npass != 1 && npass != 3) || D < 1 || D > 8 || p < 1 || p > 16 || kind < 0 || kind > 1 || frame < 0 ||
+        frame > 3 || nb < 1 || !T || !Y || !out || !scratch)
+        return KH_EINVAL;
+    if (bytes < kh_selftest_site_layered_bytes(npass, D, p, nb)) return KH_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    return run([&] { run_site_layered(npass, D, p, kind, frame, nb, T, Y, out, scratch, bytes, st); });
 }
 
 kh_status kh_selftest_fp64_newton(int n, const double* x, double* out, void* stream) {

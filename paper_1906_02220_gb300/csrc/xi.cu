@@ -162,7 +162,8 @@ void Engine<T>::correlation_length(int slot, int dir, int max_iter, double tol, 
         // blocks (a, d) of [(ub, rb)][(uk, rk)]: the frame-f corner layout (L, U) = (u, r)
         site_operand(sl, Y1, Yp, {chi, D, D, D, D, chi}, {0, 5, 2, 4, 1, 3});
         const long long w4 = (long long)f * dm.D4 * dm.D4;
-        site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, sl.p, Qt, sl.dl ? sl.Wcor + w4 : nullptr,
+        site_layer(Yp, chi2, sl.Tcor + (long long)f * dm.pmax * dm.D4, lay_img(sl, 1, 0, f), lay_img(sl, 2, 0, f),
+                   sl.p, Qt, sl.dl ? sl.Wcor + w4 : nullptr,
                    sl.dl && sl.Wcor_lo ? sl.Wcor_lo + w4 : nullptr, site_presplit(sl));
         // Qt[a][d][(vk, lk)][(vb, lb)] -> Y1[a][(lk, lb)][(d, vk, vb)]
         permute<T, T>(Qt, Y1, {chi, chi, D, D, D, D}, {0, 3, 5, 1, 2, 4}, st);

@@ -196,3 +196,49 @@ def test_tensor_core_gemm(g, prec, M, N, K):
     scale = np.sqrt(K) * np.abs(A).max() * np.abs(B).max()
     err = np.abs(C - ref).max()
     assert err <= GEMM_TOL[prec] * scale, (err, scale)
+
+
+def _frame_tensor(T, f):
+    """Site tensor [p][l][u][r][d] seen from frame f: each quarter turn makes
+    the new legs (l, u, r, d) the old (d, l, u, r)."""
+    for _ in range(f):
+        T = T.transpose(0, 2, 3, 4, 1)
+    return T
+
+
+def _layer_operand(T, kind, f):
+    """TL[in][p][out]: corner (kind 0) in = (l, u), out = (r, d); edge (kind 1)
+    in = (l, d), out = (u, r)."""
+    Tf = _frame_tensor(T, f)
+    p, D = T.shape[0], T.shape[1]
+    axes = (1, 2, 0, 3, 4) if kind == 0 else (1, 4, 0, 2, 3)
+    return np.ascontiguousarray(Tf.transpose(axes)).reshape(D * D, p, D * D)
+
+
+# (npass, D, p, kind, frame, nb): several tiles per CTA with a ragged last
+# tile (128 // D^2 blocks per tile), streamed and resident operand images,
+# chunks of the physical index that p does not fill
+LAYERED_CASES = [
+    (3, 4, 16, 0, 0, 8 * 300 + 5), (3, 4, 16, 1, 1, 37), (3, 2, 16, 0, 2, 32 * 200 + 7),
+    (3, 3, 16, 1, 3, 14 * 160 + 3), (3, 5, 16, 0, 1, 5 * 170 + 2), (3, 6, 16, 1, 0, 3 * 170 + 1),
+    (3, 7, 16, 0, 3, 2 * 160 + 1), (3, 8, 16, 1, 2, 2 * 160 + 1), (1, 4, 16, 0, 0, 8 * 200 + 3),
+    (1, 6, 16, 0, 1, 3 * 100 + 2), (3, 4, 3, 0, 1, 100), (3, 6, 5, 0, 0, 200), (3, 1, 2, 1, 0, 300),
+]
+
+
+@pytest.mark.parametrize("npass,D,p,kind,frame,nb", LAYERED_CASES)
+def test_layered_site_contraction(g, npass, D, p, kind, frame, nb):
+    """The layered tensor-core contraction against an FP64 einsum of the same
+    ket-then-bra network (Fig. 4), elementwise within the TF32 or 3xTF32
+    error bound relative to the contraction of absolute values."""
+    import torch
+    rng = np.random.default_rng(1000 * D + 10 * p + nb)
+    T = rng.standard_normal((p, D, D, D, D))
+    Y = rng.standard_normal((nb, D * D, D * D))
+    out = g.selftest_site_layered(torch.as_tensor(T, device="cuda:0"), torch.as_tensor(Y, device="cuda:0"),
+                                  kind=kind, frame=frame, npass=npass).cpu().numpy()
+    TL = _layer_operand(T, kind, frame)
+    ref = np.einsum("ipo,bji,jpq->boq", TL, Y, TL, optimize=True)
+    scale = np.einsum("ipo,bji,jpq->boq", np.abs(TL), np.abs(Y), np.abs(TL), optimize=True)
+    tol = 1e-5 if npass == 3 else 3e-3
+    assert np.all(np.abs(out - ref) <= tol * scale + 1e-30)
