@@ -12,13 +12,14 @@
 //                          ket:  acc1[c % 2]  = Y_tile * B1_c    (A, B in shared memory)
 //                          bra:  out         += Z_c   * B2_c    (A = Z in tensor memory)
 //                        and commits each group to an mbarrier;
-//   warps 2-5 (workers)  load the Y tile (hi/lo split) into shared memory, read
-//                        acc1 row (b, ib) per thread, scatter it into a
-//                        shared-memory buffer in (b, ok) row order, read back
-//                        row (b, ok), split it into TF32 hi/lo and store it to
-//                        tensor memory as the bra GEMM's A operand; at the end
-//                        of a tile they read the output accumulator and store
-//                        out rows (b, ok).
+//   warps 2-9 (workers)  two sets of four warps, the chunks of even and odd
+//                        global index: load the Y tile (hi/lo split) into
+//                        shared memory, read acc1 row (b, ib) per thread,
+//                        scatter it into the set's shared-memory buffer in
+//                        (b, ok) row order, read back row (b, ok), split it into
+//                        TF32 hi/lo and store it to tensor memory as the bra
+//                        GEMM's A operand; at the end of a tile the first set
+//                        reads the output accumulator and stores out rows (b, ok).
 // With 3 passes every product is A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32-level
 // accuracy from TF32 inputs).  Every wait is bounded: on time-out the kernel
 // raises a flag, the roles drain, tensor memory is freed and the kernel
@@ -35,7 +36,8 @@ namespace lay {
 
 using namespace tc;
 
-constexpr int THREADS = 192;
+constexpr int NSET = 2;                        // worker sets (4 warps each), chunks split by parity
+constexpr int THREADS = 64 + 128 * NSET;
 constexpr int MAXST = 16;
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
@@ -47,7 +49,8 @@ constexpr uint32_t idesc(int n) {
 struct Bars {
     uint64_t b1_full[MAXST], b1_empty[MAXST], b2_full[MAXST], b2_empty[MAXST];
     uint64_t acc1_full[2], acc1_empty[2], a2_full[2], a2_empty[2];
-    uint64_t a1_full, a1_empty, out_full, out_empty, zs_w, zs_r, drain;
+    uint64_t zs_w[NSET], zs_r[NSET];
+    uint64_t a1_full, a1_empty, out_full, out_empty, drain;
 };
 
 // Bounded wait made uniform over the warp: false on time-out or abort.
@@ -99,12 +102,14 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
             mbar_init(&bars.a2_full[j], 128);
             mbar_init(&bars.a2_empty[j], 1);
         }
-        mbar_init(&bars.a1_full, 128);
+        mbar_init(&bars.a1_full, 128 * NSET);
         mbar_init(&bars.a1_empty, 1);
         mbar_init(&bars.out_full, 1);
         mbar_init(&bars.out_empty, 128);
-        mbar_init(&bars.zs_w, 128);
-        mbar_init(&bars.zs_r, 128);
+        for (int s = 0; s < NSET; ++s) {
+            mbar_init(&bars.zs_w[s], 128);
+            mbar_init(&bars.zs_r[s], 128);
+        }
         mbar_init(&bars.drain, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -247,31 +252,33 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
         }
     } else {
         // ---------------------------------------------------------- workers
-        const int wt = threadIdx.x - 64;                 // 0..127
+        const int wt = threadIdx.x - 64;                 // 0 .. 128 NSET - 1
+        const int set = wt >> 7;                         // chunks g with g % NSET == set
         const int q = warp & 3;                          // tensor-memory lane quadrant
         const int t = 32 * q + lane;                     // tile row of this thread
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         const long long total_rows = nb * D2;
+        float* zbuf = sZ + set * 128 * P.zs;
         bool ok = true;
 
         // zero the Y tile images once: padding rows and columns stay zero
-        for (int i = wt; i < A1_SZ / 16; i += 128) ((float4*)sA1)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // zeros land before the first tile's values
+        for (int i = wt; i < A1_SZ / 16; i += 128 * NSET) ((float4*)sA1)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        asm volatile("bar.sync 1, %0;" ::"r"(128 * NSET) : "memory");   // zeros land before the first tile's values
 
         // the tile's R D^2 values of Y (contiguous), all loads in flight at once
-        constexpr int YPER = (P.rows * D2 + 127) / 128;
+        constexpr int YPER = (P.rows * D2 + 128 * NSET - 1) / (128 * NSET);
         auto load_y = [&](int tile) {
             const long long e0 = (long long)tile * P.rows * D2, etot = total_rows * D2;
             float yv[YPER];
 #pragma unroll
             for (int j = 0; j < YPER; ++j) {
-                const int i = wt + 128 * j;
+                const int i = wt + 128 * NSET * j;
                 const long long e = e0 + i;
                 yv[j] = (i < P.rows * D2 && e < etot) ? __ldg(Y + e) : 0.f;
             }
 #pragma unroll
             for (int j = 0; j < YPER; ++j) {
-                const int i = wt + 128 * j;
+                const int i = wt + 128 * NSET * j;
                 if (i < P.rows * D2) {
                     const int o = swz_offset(i / D2, i % D2, 128);
                     if (NPASS == 3) {
@@ -290,10 +297,11 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
         if ((int)blockIdx.x < ntiles) load_y(blockIdx.x);
         long long g0 = 0;
         int it = 0;
-        uint32_t zcount = 0;
+        uint32_t zcount = 0;                             // chunks this set has transposed
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it, g0 += nc) {
-            for (int c = 0; c < nc && ok; ++c, ++zcount) {
+            for (int c = 0; c < nc && ok; ++c) {
                 const long long g = g0 + c;
+                if ((int)(g % NSET) != set) continue;
                 const int j = (int)(g & 1);
                 // ---- ket accumulator row (b, ib) -> transpose buffer rows (b, ok)
                 if (!wait_warp(&bars.acc1_full[j], (uint32_t)((g >> 1) & 1), abort_flag)) { ok = false; break; }
@@ -312,7 +320,7 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                     const int b = t / D2, ib = t % D2;
 #pragma unroll
                     for (int ok_ = 0; ok_ < D2; ++ok_) {
-                        float* dst = sZ + (b * D2 + ok_) * P.zs + ib * P.pc;
+                        float* dst = zbuf + (b * D2 + ok_) * P.zs + ib * P.pc;
                         if constexpr (P.pc % 4 == 0) {
 #pragma unroll
                             for (int pl = 0; pl < P.pc; pl += 4)
@@ -325,8 +333,8 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                         }
                     }
                 }
-                mbar_arrive(&bars.zs_w);
-                if (!wait_warp(&bars.zs_w, zcount & 1, abort_flag)) { ok = false; break; }
+                mbar_arrive(&bars.zs_w[set]);
+                if (!wait_warp(&bars.zs_w[set], zcount & 1, abort_flag)) { ok = false; break; }
                 // ---- row (b, ok) of Z -> tensor memory (bra GEMM A operand)
                 const int ja = (int)(g % P.na2);
                 if (!wait_warp(&bars.a2_empty[ja], (uint32_t)((g / P.na2) & 1) ^ 1, abort_flag)) {
@@ -340,7 +348,7 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
 #pragma unroll
                 for (int i = 0; i < K2S; ++i) z[i] = 0.f;
                 if (t < P.rows) {
-                    const float* src = sZ + t * P.zs;
+                    const float* src = zbuf + t * P.zs;
 #pragma unroll
                     for (int i = 0; i < K2R; i += 4) {
                         const float4 w = *(const float4*)(src + i);
@@ -366,8 +374,9 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                 tmem_st_wait();
                 fence_before();
                 mbar_arrive(&bars.a2_full[ja]);
-                mbar_arrive(&bars.zs_r);
-                if (!wait_warp(&bars.zs_r, zcount & 1, abort_flag)) { ok = false; break; }
+                mbar_arrive(&bars.zs_r[set]);
+                if (!wait_warp(&bars.zs_r[set], zcount & 1, abort_flag)) { ok = false; break; }
+                ++zcount;
             }
             if (!ok) break;
             // next tile's Y once the ket GEMMs of this tile have read it
@@ -376,7 +385,8 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                 if (!wait_warp(&bars.a1_empty, it & 1, abort_flag)) { ok = false; break; }
                 load_y(next);
             }
-            // ---- output rows (b, ok)
+            if (set != 0) continue;
+            // ---- output rows (b, ok) (first set)
             if (!wait_warp(&bars.out_full, it & 1, abort_flag)) { ok = false; break; }
             fence_after();
             uint32_t orr[P.n2p / 16][16];
@@ -461,7 +471,7 @@ void launch_layered(const float* Y, long long nb, int p, const float* img1, cons
     if (ntiles_ll > 0x7fffffffLL) fail(KH_EINVAL, "layered site contraction: too many tiles");
     const int ntiles = (int)ntiles_ll;
     if (ntiles == 0) return;
-    const size_t fixed = 1024 + (size_t)NPL * P.a1_bytes + (size_t)128 * P.zs * 4;
+    const size_t fixed = 1024 + (size_t)NPL * P.a1_bytes + (size_t)lay::NSET * 128 * P.zs * 4;
     const size_t s1 = (size_t)NPL * P.b1_bytes, s2 = (size_t)NPL * P.b2_bytes;
     const size_t cap = (size_t)smem_optin_max() - 2048;   // the static barriers share the per-block limit
     int nst1 = 0, nst2 = 0;

@@ -119,43 +119,95 @@ refine_apply_kernel(const double* __restrict__ L, const double* __restrict__ Q, 
     (blockIdx.y == 0 ? Lo : Qo)[e] = acc;
 }
 
-// All refinement steps in one cooperative launch.  Every CTA (64 threads)
-// owns 8 x 8 output tiles (grid-stride over the (k/8)^2 tiles); the four
-// phases of a step -- R, P, W = L^T G; T = W Q; the corrections; L + L F and
-// Q + Q H -- are separated by grid barriers, and each GEMM-like phase first
-// stages the 8-wide slabs of its operands in shared memory (the FP64 pipe
-// then runs from shared memory instead of waiting on L2 loads).  The factors
-// ping-pong between (L1, Q1) and (Lo, Qo).
+// Newton correction (f_ij, h_ij) of entry (i, j) from R, P, T (see above).
+__device__ __forceinline__ void newton_entry(const double* __restrict__ R, const double* __restrict__ P,
+                                             const double* __restrict__ T, int k, double gap, int i, int j,
+                                             double& f, double& h) {
+    const long long e = (long long)i * k + j;
+    const double rij = R[e], pij = P[e];
+    if (i == j) {
+        f = 0.5 * rij;
+        h = 0.5 * pij;
+        return;
+    }
+    const double si = T[(long long)i * k + i], sj = T[(long long)j * k + j];
+    const double tij = T[e], tji = T[(long long)j * k + i];
+    const double big = fmax(fabs(si), fabs(sj));
+    const double coupling = fmax(fabs(tij), fabs(tji));
+    if (!(fabs(sj - si) > fmax(gap * big, 64.0 * coupling)) || big == 0.0) {
+        f = 0.5 * rij;
+        h = 0.5 * pij;
+        return;
+    }
+    const double a = tij + sj * rij;
+    const double b = tji + sj * pij;
+    const double inv = 1.0 / ((sj - si) * (sj + si));
+    f = (sj * a + si * b) * inv;
+    h = (si * a + sj * b) * inv;
+}
+
+// All refinement steps in one cooperative launch.  Every CTA owns 8 x 8
+// output tiles (grid-stride over the (k/8)^2 tiles) with 256 threads: four
+// groups of 64 split each k-long FP64 dot product into quarters (shorter
+// dependent chains, all four SM sub-partitions busy), the partial sums joined
+// in shared memory in a fixed order.  Three phases per step, separated by
+// grid barriers: R, P, W = L^T G; T = W Q; L' = L + L F and Q' = Q + Q H with
+// the corrections F, H formed on the fly from R, P, T for the tile's column
+// slab.  Operands are staged as 8-wide slabs in shared memory (the FP64 pipe
+// then runs from shared memory).  The factors ping-pong between (L1, Q1) and
+// (Lo, Qo).
 constexpr int kRT = 8;                                     // tile edge
-__global__ void __launch_bounds__(kRT * kRT)
+constexpr int kRQ = 4;                                     // K split
+constexpr int kRThreads = kRT * kRT * kRQ;
+__global__ void __launch_bounds__(kRThreads)
 refine_coop_kernel(const double* __restrict__ G, int k, const double* L0, const double* Q0, double* s_out,
                    double* Lo, double* Qo, double* work, double rel_gap, int newton_steps) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
-    extern __shared__ double slab[];                       // 5 slabs of 8 x k
+    extern __shared__ double slab[];                       // 5 slabs of 8 x k, then 3 x kRQ x 64 partial sums
     const long long kk = (long long)k * k;
-    double *R = work, *P = work + kk, *W = work + 2 * kk, *T = work + 3 * kk, *F = work + 4 * kk,
-           *H = work + 5 * kk, *L1 = work + 6 * kk, *Q1 = work + 7 * kk;
+    double *R = work, *P = work + kk, *W = work + 2 * kk, *T = work + 3 * kk, *L1 = work + 6 * kk,
+           *Q1 = work + 7 * kk;
     const int nt = (k + kRT - 1) / kRT, ntiles = nt * nt;
-    const int tid = threadIdx.x, ti = tid / kRT, tj = tid % kRT;
+    const int tid = threadIdx.x, q = tid / (kRT * kRT), e64 = tid % (kRT * kRT), ti = e64 / kRT, tj = e64 % kRT;
+    const int mq0 = q * k / kRQ, mq1 = (q + 1) * k / kRQ;  // this group's part of the sum
     double* s0 = slab;
     double* s1 = slab + kRT * k;
     double* s2 = slab + 2 * kRT * k;
     double* s3 = slab + 3 * kRT * k;
     double* s4 = slab + 4 * kRT * k;
+    double* red = slab + 5 * kRT * k;                      // red[(c * kRQ + q) * 64 + e64]
     // slab of columns [c0, c0+8) of X (k x k): sl[m * 8 + c] = X[m][c0 + c]
     auto load_cols = [&](double* sl, const double* X, int c0) {
-        for (int e = tid; e < kRT * k; e += kRT * kRT) {
+        for (int e = tid; e < kRT * k; e += kRThreads) {
             const int m = e / kRT, c = e % kRT;
             sl[e] = (c0 + c < k) ? X[m * k + c0 + c] : 0.0;
         }
     };
     // slab of rows [r0, r0+8) of X: sl[m * 8 + r] = X[r0 + r][m] (same indexing as a column slab of X^T)
     auto load_rows = [&](double* sl, const double* X, int r0) {
-        for (int e = tid; e < kRT * k; e += kRT * kRT) {
+        for (int e = tid; e < kRT * k; e += kRThreads) {
             const int r = e / k, m = e % k;
             sl[m * kRT + r] = (r0 + r < k) ? X[(r0 + r) * k + m] : 0.0;
         }
+    };
+    // sum over this group's m of a[m][ti] b[m][tj] (two chains)
+    auto dot = [&](const double* a, const double* b) {
+        double x0 = 0.0, x1 = 0.0;
+        int m = mq0;
+        for (; m + 1 < mq1; m += 2) {
+            x0 = fma(a[m * kRT + ti], b[m * kRT + tj], x0);
+            x1 = fma(a[(m + 1) * kRT + ti], b[(m + 1) * kRT + tj], x1);
+        }
+        if (m < mq1) x0 = fma(a[m * kRT + ti], b[m * kRT + tj], x0);
+        return x0 + x1;
+    };
+    // joins the kRQ partial sums of quantity c (group 0 reads them in order)
+    auto joined = [&](int c) {
+        double x = 0.0;
+#pragma unroll
+        for (int g = 0; g < kRQ; ++g) x += red[(c * kRQ + g) * 64 + e64];
+        return x;
     };
     const int nsteps = newton_steps + 1;
     for (int step = 0; step < nsteps; ++step) {
@@ -175,29 +227,16 @@ refine_coop_kernel(const double* __restrict__ G, int k, const double* L0, const 
             load_cols(s3, Qi, j0);
             load_cols(s4, G, j0);
             __syncthreads();
-            double r0 = 0.0, r1 = 0.0, p0 = 0.0, p1 = 0.0, w0 = 0.0, w1 = 0.0;
-            int m = 0;
-            for (; m + 1 < k; m += 2) {
-                const double a0 = s0[m * kRT + ti], a1 = s0[(m + 1) * kRT + ti];
-                r0 = fma(a0, s1[m * kRT + tj], r0);
-                r1 = fma(a1, s1[(m + 1) * kRT + tj], r1);
-                p0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], p0);
-                p1 = fma(s2[(m + 1) * kRT + ti], s3[(m + 1) * kRT + tj], p1);
-                w0 = fma(a0, s4[m * kRT + tj], w0);
-                w1 = fma(a1, s4[(m + 1) * kRT + tj], w1);
-            }
-            if (m < k) {
-                const double a0 = s0[m * kRT + ti];
-                r0 = fma(a0, s1[m * kRT + tj], r0);
-                p0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], p0);
-                w0 = fma(a0, s4[m * kRT + tj], w0);
-            }
+            red[(0 * kRQ + q) * 64 + e64] = dot(s0, s1);
+            red[(1 * kRQ + q) * 64 + e64] = dot(s2, s3);
+            red[(2 * kRQ + q) * 64 + e64] = dot(s0, s4);
+            __syncthreads();
             const int i = i0 + ti, j = j0 + tj;
-            if (i < k && j < k) {
+            if (q == 0 && i < k && j < k) {
                 const double d = (i == j) ? 1.0 : 0.0;
-                R[i * k + j] = d - (r0 + r1);
-                P[i * k + j] = d - (p0 + p1);
-                W[i * k + j] = w0 + w1;
+                R[i * k + j] = d - joined(0);
+                P[i * k + j] = d - joined(1);
+                W[i * k + j] = joined(2);
             }
         }
         grid.sync();
@@ -208,68 +247,40 @@ refine_coop_kernel(const double* __restrict__ G, int k, const double* L0, const 
             load_rows(s0, W, i0);
             load_cols(s1, Qi, j0);
             __syncthreads();
-            double t0 = 0.0, t1 = 0.0;
-            int m = 0;
-            for (; m + 1 < k; m += 2) {
-                t0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], t0);
-                t1 = fma(s0[(m + 1) * kRT + ti], s1[(m + 1) * kRT + tj], t1);
-            }
-            if (m < k) t0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], t0);
+            red[q * 64 + e64] = dot(s0, s1);
+            __syncthreads();
             const int i = i0 + ti, j = j0 + tj;
-            if (i < k && j < k) T[i * k + j] = t0 + t1;
+            if (q == 0 && i < k && j < k) T[i * k + j] = joined(0);
         }
         grid.sync();
-        // phase 3: the corrections (elementwise)
-        const long long stride = (long long)gridDim.x * blockDim.x;
-        for (long long e = blockIdx.x * (long long)blockDim.x + tid; e < kk; e += stride) {
-            const int i = (int)(e / k), j = (int)(e % k);
-            const double rij = R[e], pij = P[e];
-            if (i == j) {
-                F[e] = 0.5 * rij;
-                H[e] = 0.5 * pij;
-                s_out[i] = T[e] * (1.0 + 0.5 * (rij + pij));
-                continue;
+        // refined singular values (one CTA)
+        if (blockIdx.x == 0)
+            for (int i = tid; i < k; i += kRThreads) {
+                const long long e = (long long)i * k + i;
+                s_out[i] = T[e] * (1.0 + 0.5 * (R[e] + P[e]));
             }
-            const double si = T[i * k + i], sj = T[j * k + j];
-            const double big = fmax(fabs(si), fabs(sj));
-            const double coupling = fmax(fabs(T[e]), fabs(T[j * k + i]));
-            if (!(fabs(sj - si) > fmax(gap * big, 64.0 * coupling)) || big == 0.0) {
-                F[e] = 0.5 * rij;
-                H[e] = 0.5 * pij;
-                continue;
-            }
-            const double a = T[e] + sj * rij;
-            const double b = T[j * k + i] + sj * pij;
-            const double inv = 1.0 / ((sj - si) * (sj + si));
-            F[e] = (sj * a + si * b) * inv;
-            H[e] = (si * a + sj * b) * inv;
-        }
-        grid.sync();
-        // phase 4: L' = L + L F, Q' = Q + Q H
+        // phase 3: L' = L + L F, Q' = Q + Q H, the corrections of the tile's
+        // column slab formed from R, P, T
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int i0 = (t / nt) * kRT, j0 = (t % nt) * kRT;
             __syncthreads();
             load_rows(s0, Li, i0);
-            load_cols(s1, F, j0);
             load_rows(s2, Qi, i0);
-            load_cols(s3, H, j0);
+            for (int e = tid; e < kRT * k; e += kRThreads) {
+                const int m = e / kRT, j = j0 + e % kRT;
+                double f = 0.0, h = 0.0;
+                if (j < k) newton_entry(R, P, T, k, gap, m, j, f, h);
+                s1[e] = f;
+                s3[e] = h;
+            }
+            __syncthreads();
+            red[(0 * kRQ + q) * 64 + e64] = dot(s0, s1);
+            red[(1 * kRQ + q) * 64 + e64] = dot(s2, s3);
             __syncthreads();
             const int i = i0 + ti, j = j0 + tj;
-            double l0 = 0.0, l1 = 0.0, q0 = 0.0, q1 = 0.0;
-            int m = 0;
-            for (; m + 1 < k; m += 2) {
-                l0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], l0);
-                l1 = fma(s0[(m + 1) * kRT + ti], s1[(m + 1) * kRT + tj], l1);
-                q0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], q0);
-                q1 = fma(s2[(m + 1) * kRT + ti], s3[(m + 1) * kRT + tj], q1);
-            }
-            if (m < k) {
-                l0 = fma(s0[m * kRT + ti], s1[m * kRT + tj], l0);
-                q0 = fma(s2[m * kRT + ti], s3[m * kRT + tj], q0);
-            }
-            if (i < k && j < k) {
-                Ln[i * k + j] = Li[i * k + j] + (l0 + l1);
-                Qn[i * k + j] = Qi[i * k + j] + (q0 + q1);
+            if (q == 0 && i < k && j < k) {
+                Ln[i * k + j] = Li[i * k + j] + joined(0);
+                Qn[i * k + j] = Qi[i * k + j] + joined(1);
             }
         }
         if (step + 1 < nsteps) grid.sync();
@@ -296,17 +307,17 @@ void svd_refine_fp64(const double* G, int k, const double* L, const double* Q, d
         KH_CUDA(cudaGetDevice(&dev));
         KH_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         KH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const size_t smem = (size_t)5 * kRT * k * sizeof(double);
+        const size_t smem = ((size_t)5 * kRT * k + 3 * kRQ * kRT * kRT) * sizeof(double);
         static std::atomic<size_t> granted[kMaxDevices] = {};
         smem_opt_in(refine_coop_kernel, smem, granted);
-        KH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_coop_kernel, kRT * kRT, smem));
+        KH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_coop_kernel, kRThreads, smem));
         const int ntiles = ((k + kRT - 1) / kRT) * ((k + kRT - 1) / kRT);
         const int cblocks = std::min(ntiles, per_sm * sms);
         if (coop && cblocks >= 1) {
             int newton = 3;
             void* args[] = {(void*)&G, (void*)&k, (void*)&L, (void*)&Q, (void*)&s, (void*)&Lo, (void*)&Qo,
                             (void*)&work, (void*)&rel_gap, (void*)&newton};
-            KH_CUDA(cudaLaunchCooperativeKernel((const void*)refine_coop_kernel, dim3(cblocks), dim3(kRT * kRT),
+            KH_CUDA(cudaLaunchCooperativeKernel((const void*)refine_coop_kernel, dim3(cblocks), dim3(kRThreads),
                                                 args, smem, st));
             KH_LAUNCHED();
             return;
