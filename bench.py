@@ -51,9 +51,12 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP64 and (D, chi) = (6, 144) lines measured after the main one")
     ap.add_argument("--e2e-steps", type=int, default=0, help="default: = --steps")
-    ap.add_argument("--kernel", default="", choices=["", "tc_gemm"],
-                    help="profiling mode: run one library kernel on --size^3 operands instead of the bench")
+    ap.add_argument("--kernel", default="", choices=["", "tc_gemm", "site_layered"],
+                    help="profiling mode: run one library kernel instead of the bench (tc_gemm on --size^3 "
+                         "operands; site_layered: the layered site contraction of --D, --chi, p = 16)")
     ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--D", type=int, default=4)
+    ap.add_argument("--chi", type=int, default=64)
     return ap.parse_args()
 
 
@@ -519,9 +522,28 @@ def run_reference(a, rank, world):
 
 def run_kernel(a):
     """Profiling mode: the tensor-core contraction GEMM on size^3 operands
-    (inputs larger than L2), timed with CUDA events; one JSON line."""
+    (inputs larger than L2), or the layered site contraction of one corner
+    (chi^2 blocks of D^2 x D^2, p = 16, 3xTF32), timed with CUDA events; one
+    JSON line.  The times include the self-test's operand preparation."""
     import torch
     import paper_1906_02220_gb300 as g
+    if a.kernel == "site_layered":
+        gen = torch.Generator(device="cuda:0").manual_seed(0)
+        D, nb = a.D, a.chi * a.chi
+        T = torch.randn((16, D, D, D, D), dtype=torch.float64, device="cuda:0", generator=gen)
+        Y = torch.randn((nb, D * D, D * D), dtype=torch.float64, device="cuda:0", generator=gen)
+        t = []
+        for i in range(a.warmup + a.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.selftest_site_layered(T, Y, 0, 0, 3)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= a.warmup:
+                t.append(e0.elapsed_time(e1))
+        print(json.dumps({"kernel": "site_layered", "D": D, "chi": a.chi, "p": 16, "prec": "tf32x3",
+                          "ms_incl_preparation": min(t), "flops": 4.0 * 16 * nb * D ** 6}))
+        return
     n = a.size
     gen = torch.Generator(device="cuda:0").manual_seed(0)
     A = torch.randn((n, n), dtype=torch.float64, device="cuda:0", generator=gen)

@@ -615,36 +615,57 @@ __device__ void cholqr_epilogue(int k, double tau, T* __restrict__ X, T* Lm, T* 
     // recursive doubling over spans s = 8, 16, 32, ...: A = rows [a0, a0+s),
     // C = rows [a0+s, min(a0+2s, k)); Tm[c][a] = sum_m L[c][m] Li[m][a] stored
     // at Lm[a][c] (upper triangle), then Li[c][a] = -sum_m Li[c][m] Tm[m][a]
+    // Each thread computes a 2 x 2 tile (rows ci, ci+1; columns aj, aj+1): the
+    // sums run over the pair's common range, the extra terms being products
+    // with zeros of the upper triangles of Li (zero from the prologue and the
+    // diagonal-block inversion).
     for (int sp = 8; sp < k; sp *= 2) {
         const int npair = (k + 2 * sp - 1) / (2 * sp);
-        // items: pair p, C row ci (< sp), A column aj (< sp)
-        const int items = npair * sp * sp;
+        const int hs = sp / 2;
+        const int items = npair * hs * hs;          // pair p, C row pair, A column pair
         for (int e = tid; e < items; e += nt) {
-            const int p = e / (sp * sp), rem = e % (sp * sp);
-            const int a0 = p * 2 * sp, ci = a0 + sp + rem / sp, aj = a0 + rem % sp;
+            const int p = e / (hs * hs), rem = e % (hs * hs);
+            const int a0 = p * 2 * sp, ci = a0 + sp + 2 * (rem / hs), aj = a0 + 2 * (rem % hs);
             if (ci >= k) continue;
-            T s0 = T(0), s1 = T(0);
-            int m = aj;
-            for (; m + 1 < a0 + sp; m += 2) {
-                s0 = fma(Lm[ci * ld + m], Li[m * ld + aj], s0);
-                s1 = fma(Lm[ci * ld + m + 1], Li[(m + 1) * ld + aj], s1);
+            const bool r1 = ci + 1 < k;
+            T s00 = T(0), s01 = T(0), s10 = T(0), s11 = T(0);
+            for (int m = aj; m < a0 + sp; ++m) {
+                const T l0 = Lm[ci * ld + m], l1 = r1 ? Lm[(ci + 1) * ld + m] : T(0);
+                const T i0 = Li[m * ld + aj], i1 = Li[m * ld + aj + 1];
+                s00 = fma(l0, i0, s00);
+                s01 = fma(l0, i1, s01);
+                s10 = fma(l1, i0, s10);
+                s11 = fma(l1, i1, s11);
             }
-            if (m < a0 + sp) s0 = fma(Lm[ci * ld + m], Li[m * ld + aj], s0);
-            Lm[aj * ld + ci] = s0 + s1;
+            Lm[aj * ld + ci] = s00;                 // Tm[c][a] at Lm[a][c] (upper triangle)
+            Lm[(aj + 1) * ld + ci] = s01;
+            if (r1) {
+                Lm[aj * ld + ci + 1] = s10;
+                Lm[(aj + 1) * ld + ci + 1] = s11;
+            }
         }
         __syncthreads();
         for (int e = tid; e < items; e += nt) {
-            const int p = e / (sp * sp), rem = e % (sp * sp);
-            const int a0 = p * 2 * sp, ci = a0 + sp + rem / sp, aj = a0 + rem % sp;
+            const int p = e / (hs * hs), rem = e % (hs * hs);
+            const int a0 = p * 2 * sp, ci = a0 + sp + 2 * (rem / hs), aj = a0 + 2 * (rem % hs);
             if (ci >= k) continue;
-            T s0 = T(0), s1 = T(0);
-            int m = a0 + sp;
-            for (; m + 1 <= ci; m += 2) {
-                s0 = fma(Li[ci * ld + m], Lm[aj * ld + m], s0);
-                s1 = fma(Li[ci * ld + m + 1], Lm[aj * ld + m + 1], s1);
+            const bool r1 = ci + 1 < k;
+            const int mend = r1 ? ci + 1 : ci;      // row ci's term at m = ci + 1 is Li[ci][ci+1] = 0
+            T s00 = T(0), s01 = T(0), s10 = T(0), s11 = T(0);
+            for (int m = a0 + sp; m <= mend; ++m) {
+                const T l0 = Li[ci * ld + m], l1 = r1 ? Li[(ci + 1) * ld + m] : T(0);
+                const T t0 = Lm[aj * ld + m], t1 = Lm[(aj + 1) * ld + m];
+                s00 = fma(l0, t0, s00);
+                s01 = fma(l0, t1, s01);
+                s10 = fma(l1, t0, s10);
+                s11 = fma(l1, t1, s11);
             }
-            if (m <= ci) s0 = fma(Li[ci * ld + m], Lm[aj * ld + m], s0);
-            Li[ci * ld + aj] = -(s0 + s1);
+            Li[ci * ld + aj] = -s00;
+            Li[ci * ld + aj + 1] = -s01;
+            if (r1) {
+                Li[(ci + 1) * ld + aj] = -s10;
+                Li[(ci + 1) * ld + aj + 1] = -s11;
+            }
         }
         __syncthreads();
     }
@@ -706,8 +727,34 @@ cholqr_kernel(const double* __restrict__ G, int k, double cut_abs, double tau, T
             continue;
         }
         if (d > tauT) {
+            // trailing update a_ic -= a_ij a_cj / d_j (c <= i): rows
+            // i = j + 1 + warp + nw a, columns c = j + 1 + lane + 32 b; the pivot
+            // column's entries of a thread's rows and columns are loaded first
+            // (independent loads), then only the tile entries below the
+            // diagonal are visited
+            constexpr int RT = (CholShared<T>::KM + 31) / 32;   // rows per warp / columns per lane at nw = 32
             const T rd = chol_recip(d);
-            for (int i = j + 1 + warp; i < k; i += nw) {           // rows by warps, columns by lanes
+            T li[RT], lc[RT];
+#pragma unroll
+            for (int a = 0; a < RT; ++a) {
+                const int i = j + 1 + warp + nw * a, c = j + 1 + lane + 32 * a;
+                li[a] = i < k ? Lm[i * ld + j] : T(0);
+                lc[a] = c < k ? Lm[c * ld + j] : T(0);
+            }
+#pragma unroll
+            for (int a = 0; a < RT; ++a) {
+                const int i = j + 1 + warp + nw * a;
+                if (i >= k) break;
+                const T lia = li[a] * rd;
+#pragma unroll
+                for (int b = 0; b < RT; ++b) {
+                    const int c = j + 1 + lane + 32 * b;
+                    if (c > i) break;
+                    Lm[i * ld + c] -= lia * lc[b];
+                }
+            }
+            // rows beyond the tile (fewer than 32 warps)
+            for (int i = j + 1 + warp + nw * RT; i < k; i += nw) {
                 const T lij = Lm[i * ld + j] * rd;
                 for (int c = j + 1 + lane; c <= i; c += 32) Lm[i * ld + c] -= lij * Lm[c * ld + j];
             }

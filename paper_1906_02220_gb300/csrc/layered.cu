@@ -8,18 +8,18 @@
 //   warp 0 (lanes 0, 1)  bulk-copies the chunk's ket (B1) and bra (B2) operand
 //                        images into shared-memory rings (or once, when all
 //                        chunks fit: resident images);
-//   warp 1               allocates tensor memory; one lane issues
-//                          ket:  acc1[c % 2]  = Y_tile * B1_c    (A, B in shared memory)
-//                          bra:  out         += Z_c   * B2_c    (A = Z in tensor memory)
-//                        and commits each group to an mbarrier;
-//   warps 2-9 (workers)  two sets of four warps, the chunks of even and odd
-//                        global index: load the Y tile (hi/lo split) into
-//                        shared memory, read acc1 row (b, ib) per thread,
-//                        scatter it into the set's shared-memory buffer in
-//                        (b, ok) row order, read back row (b, ok), split it into
-//                        TF32 hi/lo and store it to tensor memory as the bra
-//                        GEMM's A operand; at the end of a tile the first set
-//                        reads the output accumulator and stores out rows (b, ok).
+//   warp 1               allocates tensor memory; one lane issues the ket GEMMs
+//                          acc1[c % 2]  = Y_tile * B1_c    (A, B in shared memory)
+//   warps 2, 3           one lane each issues half of the bra GEMMs' MMAs
+//                          out         += Z_c   * B2_c    (A = Z in tensor memory)
+//                        (each group committed to an mbarrier);
+//   warps 4-7 (workers)  load the Y tile (hi/lo split) into shared memory, read
+//                        acc1 row (b, ib) per thread, scatter it into a
+//                        shared-memory buffer in (b, ok) row order, read back
+//                        row (b, ok), split it into TF32 hi/lo and store it to
+//                        tensor memory as the bra GEMM's A operand; at the end
+//                        of a tile they read the output accumulator and store
+//                        out rows (b, ok).
 // With 3 passes every product is A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32-level
 // accuracy from TF32 inputs).  Every wait is bounded: on time-out the kernel
 // raises a flag, the roles drain, tensor memory is freed and the kernel
@@ -36,8 +36,14 @@ namespace lay {
 
 using namespace tc;
 
-constexpr int NSET = 2;                        // worker sets (4 warps each), chunks split by parity
-constexpr int THREADS = 64 + 128 * NSET;
+constexpr int NSET = 1;                        // worker sets (4 warps each), chunks split by index mod NSET
+// issuing threads (one per warp) of the ket and the bra GEMMs; the bra GEMM
+// has four times the MMAs of the ket GEMM at D = 4.  Eight warps in all keep
+// the per-thread register limit at 255 (a ninth warp on one SM sub-partition
+// would cut it to 168 and spill the workers).
+constexpr int NI1 = 1, NI2 = 2;
+constexpr int WORKER0 = 1 + NI1 + NI2;          // first worker warp
+constexpr int THREADS = 32 * WORKER0 + 128 * NSET;   // producer, issuers, workers
 constexpr int MAXST = 16;
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
@@ -50,7 +56,7 @@ struct Bars {
     uint64_t b1_full[MAXST], b1_empty[MAXST], b2_full[MAXST], b2_empty[MAXST];
     uint64_t acc1_full[2], acc1_empty[2], a2_full[2], a2_empty[2];
     uint64_t zs_w[NSET], zs_r[NSET];
-    uint64_t a1_full, a1_empty, out_full, out_empty, drain;
+    uint64_t a1_full, a1_empty, out_full, out_empty, drain[NI1 + NI2];
 };
 
 // Bounded wait made uniform over the warp: false on time-out or abort.
@@ -92,25 +98,25 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
     if (threadIdx.x == 0) {
         for (int s = 0; s < MAXST; ++s) {
             mbar_init(&bars.b1_full[s], 1);
-            mbar_init(&bars.b1_empty[s], 1);
+            mbar_init(&bars.b1_empty[s], NI1);
             mbar_init(&bars.b2_full[s], 1);
-            mbar_init(&bars.b2_empty[s], 1);
+            mbar_init(&bars.b2_empty[s], NI2);
         }
         for (int j = 0; j < 2; ++j) {
-            mbar_init(&bars.acc1_full[j], 1);
+            mbar_init(&bars.acc1_full[j], NI1);
             mbar_init(&bars.acc1_empty[j], 128);
             mbar_init(&bars.a2_full[j], 128);
-            mbar_init(&bars.a2_empty[j], 1);
+            mbar_init(&bars.a2_empty[j], NI2);
         }
         mbar_init(&bars.a1_full, 128 * NSET);
-        mbar_init(&bars.a1_empty, 1);
-        mbar_init(&bars.out_full, 1);
+        mbar_init(&bars.a1_empty, NI1);
+        mbar_init(&bars.out_full, NI2);
         mbar_init(&bars.out_empty, 128);
         for (int s = 0; s < NSET; ++s) {
             mbar_init(&bars.zs_w[s], 128);
             mbar_init(&bars.zs_r[s], 128);
         }
-        mbar_init(&bars.drain, 1);
+        for (int q = 0; q < NI1 + NI2; ++q) mbar_init(&bars.drain[q], 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -167,17 +173,24 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
             for (int s = 0; s < MAXST; ++s)
                 if (armed[s] && !wait_drain(&full[s], (uint32_t)(armed[s] - 1) & 1)) atomicOr(err, 8);
         }
-    } else if (warp == 1) {
-        // ---------------------------------------------------------- MMA issuer
+    } else if (warp < WORKER0) {
+        // ---------------------------------------------------------- MMA issuers
+        // NI1 threads (warps 1 ..) issue the ket GEMMs, NI2 threads (the next
+        // warps) the bra GEMMs, one thread per warp: these narrow MMAs are
+        // bounded by their issue, not by the tensor pipe, so several issuers
+        // keep more of them in flight.  Issuer q of a GEMM issues the MMAs of
+        // the accumulators a with a % NI == q.
         if (lane == 0) {
             bool ok = true;
             long long g0 = 0;
             int it = 0;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it, g0 += nc) {
-                if (!mbar_wait(&bars.a1_full, it & 1, abort_flag)) { ok = false; break; }
-                fence_after();
-                for (int c = 0; c <= nc && ok; ++c) {
-                    if (c < nc) {                           // ket layer of chunk c
+            const bool ket = warp <= NI1;
+            const int qi = ket ? warp - 1 : warp - 1 - NI1;   // issuer index within its GEMM
+            if (ket) {
+                for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it, g0 += nc) {
+                    if (!mbar_wait(&bars.a1_full, it & 1, abort_flag)) { ok = false; break; }
+                    fence_after();
+                    for (int c = 0; c < nc; ++c) {                      // ket layer of chunk c
                         const long long g = g0 + c;
                         const int s1 = res1 ? c : (int)(g % nst1);
                         const uint32_t ph1 = res1 ? 0u : (uint32_t)((g / nst1) & 1);
@@ -188,27 +201,30 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                             break;
                         }
                         fence_after();
-                        const uint32_t d = tmem + P.c_acc1 + j * pad_to(P.n1p, 32);
+                        // MMAs round-robin over the buffer's nacc1 accumulators
+                        const uint32_t d0 = tmem + P.c_acc1 + j * P.nacc1 * P.acc1_cols;
                         const uint32_t a0 = smem_u32(sA1), b0 = smem_u32(sB1 + (size_t)s1 * B1_SZ);
-                        uint32_t acc = 0;
 #pragma unroll
                         for (int pass = 0; pass < NPASS; ++pass) {
                             const uint32_t ab = a0 + (pass == 2 ? P.a1_bytes : 0);
                             const uint32_t bb = b0 + (pass == 1 ? P.b1_bytes : 0);
 #pragma unroll
                             for (int ks = 0; ks < P.k1p / 8; ++ks) {
+                                const int i = pass * (P.k1p / 8) + ks;
+                                if ((i % P.nacc1) % NI1 != qi) continue;
                                 const uint64_t da = smem_desc(ab + (ks >> 2) * (128 * 128) + (ks & 3) * 32);
                                 const uint64_t db = smem_desc(bb + (ks >> 2) * (P.n1p * 128) + (ks & 3) * 32);
-                                umma_tf32(d, da, db, ID1, acc);
-                                acc = 1;
+                                umma_tf32(d0 + (i % P.nacc1) * P.acc1_cols, da, db, ID1, i >= P.nacc1 ? 1u : 0u);
                             }
                         }
                         umma_commit(&bars.acc1_full[j]);
                         if (!res1) umma_commit(&bars.b1_empty[s1]);
                         if (c == nc - 1) umma_commit(&bars.a1_empty);
                     }
-                    if (c >= 1) {                           // bra layer of chunk c - 1
-                        const int cc = c - 1;
+                }
+            } else {
+                for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it, g0 += nc) {
+                    for (int cc = 0; cc < nc; ++cc) {                   // bra layer of chunk cc
                         const long long g = g0 + cc;
                         const int s2 = res2 ? cc : (int)(g % nst2);
                         const uint32_t ph2 = res2 ? 0u : (uint32_t)((g / nst2) & 1);
@@ -221,19 +237,21 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                             break;
                         }
                         fence_after();
-                        const uint32_t d = tmem + P.c_out;
+                        // MMAs round-robin over the nacc2 output accumulators
+                        const uint32_t d0 = tmem + P.c_out;
                         const uint32_t a2 = tmem + P.c_a2 + ja * NPL * P.a2_cols;
                         const uint32_t b0 = smem_u32(sB2 + (size_t)s2 * B2_SZ);
-                        uint32_t acc = cc > 0 ? 1u : 0u;
 #pragma unroll
                         for (int pass = 0; pass < NPASS; ++pass) {
                             const uint32_t aa = a2 + (pass == 2 ? P.a2_cols : 0);
                             const uint32_t bb = b0 + (pass == 1 ? P.b2_bytes : 0);
 #pragma unroll
                             for (int ks = 0; ks < P.k2p / 8; ++ks) {
+                                const int i = pass * (P.k2p / 8) + ks;
+                                if ((i % P.nacc2) % NI2 != qi) continue;
                                 const uint64_t db = smem_desc(bb + (ks >> 2) * (P.n2p * 128) + (ks & 3) * 32);
-                                umma_tf32_tmem_a(d, aa + ks * 8, db, ID2, acc);
-                                acc = 1;
+                                umma_tf32_tmem_a(d0 + (i % P.nacc2) * P.out_cols, aa + ks * 8, db, ID2,
+                                                 (cc > 0 || i >= P.nacc2) ? 1u : 0u);
                             }
                         }
                         umma_commit(&bars.a2_empty[ja]);
@@ -246,13 +264,14 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                 s_abort = 1;
                 atomicOr(err, 16);
             }
-            // every MMA issued so far completes before tensor memory is freed
-            umma_commit(&bars.drain);
-            if (!wait_drain(&bars.drain, 0)) atomicOr(err, 16);
+            // every MMA this thread issued completes before tensor memory is freed
+            uint64_t* dr = &bars.drain[warp - 1];
+            umma_commit(dr);
+            if (!wait_drain(dr, 0)) atomicOr(err, 16);
         }
     } else {
         // ---------------------------------------------------------- workers
-        const int wt = threadIdx.x - 64;                 // 0 .. 128 NSET - 1
+        const int wt = threadIdx.x - 32 * WORKER0;       // 0 .. 128 NSET - 1
         const int set = wt >> 7;                         // chunks g with g % NSET == set
         const int q = warp & 3;                          // tensor-memory lane quadrant
         const int t = 32 * q + lane;                     // tile row of this thread
@@ -306,14 +325,26 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                 // ---- ket accumulator row (b, ib) -> transpose buffer rows (b, ok)
                 if (!wait_warp(&bars.acc1_full[j], (uint32_t)((g >> 1) & 1), abort_flag)) { ok = false; break; }
                 fence_after();
-                uint32_t vr[P.n1p / 16][16];
+                // the buffer's nacc1 accumulators, summed
+                uint32_t vr[P.nacc1][P.n1p / 16][16];
 #pragma unroll
-                for (int c0 = 0; c0 < P.n1p; c0 += 16)
-                    tmem_ld16_async(tmem + lane_base + (uint32_t)(P.c_acc1 + j * pad_to(P.n1p, 32) + c0), vr[c0 / 16]);
+                for (int a = 0; a < P.nacc1; ++a)
+#pragma unroll
+                    for (int c0 = 0; c0 < P.n1p; c0 += 16)
+                        tmem_ld16_async(tmem + lane_base +
+                                            (uint32_t)(P.c_acc1 + (j * P.nacc1 + a) * P.acc1_cols + c0),
+                                        vr[a][c0 / 16]);
                 tmem_ld_wait();
 #pragma unroll
-                for (int c0 = 0; c0 < P.n1p; c0 += 16) tmem_regs_ready(vr[c0 / 16]);
-                auto v = [&](int n) { return __uint_as_float(vr[n >> 4][n & 15]); };
+                for (int a = 0; a < P.nacc1; ++a)
+#pragma unroll
+                    for (int c0 = 0; c0 < P.n1p; c0 += 16) tmem_regs_ready(vr[a][c0 / 16]);
+                auto v = [&](int n) {
+                    float x = __uint_as_float(vr[0][n >> 4][n & 15]);
+#pragma unroll
+                    for (int a = 1; a < P.nacc1; ++a) x += __uint_as_float(vr[a][n >> 4][n & 15]);
+                    return x;
+                };
                 fence_before();
                 mbar_arrive(&bars.acc1_empty[j]);
                 if (t < P.rows) {
@@ -389,16 +420,25 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
             // ---- output rows (b, ok) (first set)
             if (!wait_warp(&bars.out_full, it & 1, abort_flag)) { ok = false; break; }
             fence_after();
-            uint32_t orr[P.n2p / 16][16];
+            uint32_t orr[P.nacc2][P.n2p / 16][16];
 #pragma unroll
-            for (int c0 = 0; c0 < P.n2p; c0 += 16) tmem_ld16_async(tmem + lane_base + (uint32_t)(P.c_out + c0), orr[c0 / 16]);
+            for (int a = 0; a < P.nacc2; ++a)
+#pragma unroll
+                for (int c0 = 0; c0 < P.n2p; c0 += 16)
+                    tmem_ld16_async(tmem + lane_base + (uint32_t)(P.c_out + a * P.out_cols + c0), orr[a][c0 / 16]);
             tmem_ld_wait();
             float o[P.n2p];
 #pragma unroll
             for (int c0 = 0; c0 < P.n2p; c0 += 16) {
-                tmem_regs_ready(orr[c0 / 16]);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) o[c0 + i] = __uint_as_float(orr[c0 / 16][i]);
+                for (int a = 0; a < P.nacc2; ++a) tmem_regs_ready(orr[a][c0 / 16]);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float x = __uint_as_float(orr[0][c0 / 16][i]);
+#pragma unroll
+                    for (int a = 1; a < P.nacc2; ++a) x += __uint_as_float(orr[a][c0 / 16][i]);
+                    o[c0 + i] = x;
+                }
             }
             fence_before();
             mbar_arrive(&bars.out_empty);

@@ -25,18 +25,26 @@ __host__ __device__ constexpr int pad_to(int x, int m) { return (x + m - 1) / m 
 struct Plan {
     int d2 = 0, bt = 0, rows = 0;            // D^2; blocks b per tile; rows (b, ib) used of 128
     int pc = 0, na2 = 0;                     // physical indices per chunk; Z buffers in tensor memory
+    int nacc1 = 0, nacc2 = 0;                // independent accumulators of the ket and the bra GEMM
     int n1 = 0, n1p = 0, k1p = 0, kb1 = 0;   // ket GEMM: N = pc D^2 (padded to 16), K = D^2 (padded to 8)
     int n2p = 0, k2 = 0, k2p = 0, kb2 = 0;   // bra GEMM: N = D^2 (padded to 16), K = pc D^2 (padded to 8)
     int zs = 0;                              // row stride (floats) of the shared-memory transpose buffer
+    int acc1_cols = 0, out_cols = 0;         // columns of one ket / bra accumulator (32-aligned)
     int c_acc1 = 0, c_a2 = 0, a2_cols = 0, c_out = 0, tmem = 0;   // tensor-memory columns
     int a1_bytes = 0, b1_bytes = 0, b2_bytes = 0;                 // one (hi or lo) operand image
 };
 
-// Largest chunk pc (a power of two <= 16) whose two ket accumulators, Z
-// buffers (hi and lo for 3 passes) and the output accumulator fit the 512
-// tensor-memory columns with every region 32-column aligned; two Z buffers
-// when they fit, else one.  Shared-memory operands use the 128-byte-swizzle
-// K-major layout in K blocks of 32 FP32 values.
+// The tensor core runs consecutive MMAs into one accumulator as a dependent
+// chain; these GEMMs are thin (N = D^2 for the bra layer), so the chain's
+// latency, not the MMA throughput, sets the time.  Each GEMM therefore
+// spreads its MMAs round-robin over nacc independent accumulators (summed
+// when read).  The plan picks pc (a power of two <= 16), the accumulator
+// counts and the Z double buffering that fit the 512 tensor-memory columns
+// (every region 32-column aligned: two ket buffers of nacc1 accumulators, na2
+// Z buffers (hi and lo with 3 passes), nacc2 bra accumulators), minimising a
+// latency model: per chunk one worker hand-off plus the two dependent MMA
+// chains (0.1 of a hand-off per chained MMA).  Shared-memory operands use the
+// 128-byte-swizzle K-major layout in K blocks of 32 FP32 values.
 __host__ __device__ constexpr Plan make_plan(int D, int npass) {
     Plan P{};
     P.d2 = D * D;
@@ -45,35 +53,49 @@ __host__ __device__ constexpr Plan make_plan(int D, int npass) {
     P.k1p = pad_to(P.d2, 8);
     P.kb1 = (P.k1p + 31) / 32;
     P.n2p = pad_to(P.d2, 16);
-    const int npl = npass == 3 ? 2 : 1;
     if (P.bt < 1) return P;
+    const int npl = npass == 3 ? 2 : 1;
+    double best = 1e30;
     for (int pc = 16; pc >= 1; pc /= 2) {
         const int n1p = pad_to(pc * P.d2, 16);
         if (n1p > 256) continue;
         const int k2p = pad_to(pc * P.d2, 8);
-        for (int na2 = 2; na2 >= 1; --na2) {
-            const int cols = 2 * pad_to(n1p, 32) + na2 * npl * pad_to(k2p, 32) + pad_to(P.n2p, 32);
-            if (cols > 512) continue;
-            P.pc = pc;
-            P.na2 = na2;
-            P.n1 = pc * P.d2;
-            P.n1p = n1p;
-            P.k2 = pc * P.d2;
-            P.k2p = k2p;
-            P.kb2 = (k2p + 31) / 32;
-            P.zs = pad_to(P.k2, 4);
-            if ((P.zs / 4) % 2 == 0) P.zs += 4;          // odd 16-byte stride: conflict-free row reads
-            P.c_acc1 = 0;
-            P.c_a2 = 2 * pad_to(n1p, 32);
-            P.a2_cols = pad_to(k2p, 32);
-            P.c_out = P.c_a2 + na2 * npl * P.a2_cols;
-            P.tmem = 32;
-            while (P.tmem < P.c_out + pad_to(P.n2p, 32)) P.tmem *= 2;
-            P.a1_bytes = 128 * P.kb1 * 128;
-            P.b1_bytes = n1p * P.kb1 * 128;
-            P.b2_bytes = P.n2p * P.kb2 * 128;
-            return P;
-        }
+        const int nc = (16 + pc - 1) / pc;                    // chunks at p = 16
+        const int mm1 = (P.k1p / 8) * npass, mm2 = (k2p / 8) * npass;
+        for (int nacc2 = 4; nacc2 >= 1; nacc2 /= 2)
+            for (int nacc1 = 2; nacc1 >= 1; --nacc1)
+                for (int na2 = 2; na2 >= 1; --na2) {
+                    if (nacc1 > mm1 || nacc2 > mm2) continue;
+                    const int cols = 2 * nacc1 * pad_to(n1p, 32) + na2 * npl * pad_to(k2p, 32) +
+                                     nacc2 * pad_to(P.n2p, 32);
+                    if (cols > 512) continue;
+                    const double cost = nc * (1.0 + 0.1 * ((mm1 + nacc1 - 1) / nacc1) +
+                                              0.1 * ((mm2 + nacc2 - 1) / nacc2)) - 0.01 * na2;
+                    if (cost >= best) continue;
+                    best = cost;
+                    P.pc = pc;
+                    P.na2 = na2;
+                    P.nacc1 = nacc1;
+                    P.nacc2 = nacc2;
+                    P.n1 = pc * P.d2;
+                    P.n1p = n1p;
+                    P.k2 = pc * P.d2;
+                    P.k2p = k2p;
+                    P.kb2 = (k2p + 31) / 32;
+                    P.zs = pad_to(P.k2, 4);
+                    if ((P.zs / 4) % 2 == 0) P.zs += 4;          // odd 16-byte stride: conflict-free row reads
+                    P.acc1_cols = pad_to(n1p, 32);
+                    P.out_cols = pad_to(P.n2p, 32);
+                    P.c_acc1 = 0;
+                    P.c_a2 = 2 * nacc1 * P.acc1_cols;
+                    P.a2_cols = pad_to(k2p, 32);
+                    P.c_out = P.c_a2 + na2 * npl * P.a2_cols;
+                    P.tmem = 32;
+                    while (P.tmem < P.c_out + nacc2 * P.out_cols) P.tmem *= 2;
+                    P.a1_bytes = 128 * P.kb1 * 128;
+                    P.b1_bytes = n1p * P.kb1 * 128;
+                    P.b2_bytes = P.n2p * P.kb2 * 128;
+                }
     }
     return P;
 }

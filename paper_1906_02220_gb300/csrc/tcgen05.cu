@@ -34,7 +34,13 @@ struct Cfg {
     static constexpr int STAGE_BYTES = (NPASS == 3 ? 2 : 1) * (A_BYTES + B_BYTES);
     static constexpr int STAGES = (NPASS == 3 ? 3 : 4);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
-    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    // consecutive MMAs into one accumulator form a dependent chain whose
+    // latency exceeds a narrow tile's MMA time: narrow tiles spread their
+    // MMAs round-robin over NACC accumulators (32-column aligned), summed in
+    // the epilogue
+    static constexpr int NACC = BN <= 32 ? 4 : (BN <= 64 ? 2 : 1);
+    static constexpr int ACC_COLS = BN < 32 ? 32 : BN;
+    static constexpr int TMEM_COLS = NACC * ACC_COLS;
     static constexpr uint32_t IDESC = (1u << 4)                     // D: FP32
                                       | (2u << 7) | (2u << 10)      // A, B: TF32
                                       | ((uint32_t)(BN >> 3) << 17) // N / 8
@@ -110,10 +116,13 @@ gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     const uint32_t off = kk * 32;               // 8 TF32 = 32 bytes along K
                     const uint64_t da = smem_desc(a0 + off), db = smem_desc(b0 + off);
-                    umma_tf32(tmem, da, db, G::IDESC, (kt | kk) != 0);
+                    // accumulator of this k-step; its first use (first k-steps of the tile) overwrites
+                    const int i = kt * (BK / 8) + kk;
+                    const uint32_t d = tmem + (uint32_t)((i % G::NACC) * G::ACC_COLS);
+                    umma_tf32(d, da, db, G::IDESC, i >= G::NACC ? 1u : 0u);
                     if (NPASS == 3) {
-                        umma_tf32(tmem, da, smem_desc(b1 + off), G::IDESC, 1u);
-                        umma_tf32(tmem, smem_desc(a1 + off), db, G::IDESC, 1u);
+                        umma_tf32(d, da, smem_desc(b1 + off), G::IDESC, 1u);
+                        umma_tf32(d, smem_desc(a1 + off), db, G::IDESC, 1u);
                     }
                 }
                 umma_commit(&empty_bar[s]);
@@ -127,9 +136,17 @@ gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUte
         const int row = m0 + 32 * q + lane;
         if (mbar_wait(&acc_bar, 0, abort_flag) && !*abort_flag) {
             fence_after();
+            // accumulators a written by the first min(NACC, K steps) k-steps
+            const int nacc = (KT * (BK / 8)) < G::NACC ? KT * (BK / 8) : G::NACC;
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+                for (int a = 1; a < nacc; ++a) {
+                    float w[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * G::ACC_COLS + c0), w);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] += w[j];
+                }
                 if (row < M) {
                     float* crow = C + (long long)row * ldc;
 #pragma unroll
