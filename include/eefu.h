@@ -227,6 +227,24 @@ kh_status eefu_apply_gate(kh_ctx* ctx, int gamma, const double* host_gate,
                           int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
                           double* host_info);
 
+/* Gradient of the bond cost of Fig. 3(b), d = <T''-T'|N|T''-T'>, with respect
+ * to trial factors A'' and B'' (the hand-written adjoint of the eeFU cost):
+ * builds the gated composite T' of the current state into slot gamma and its
+ * metric N as eefu_apply_gate does (ctm_max_sweeps = 0 reuses the slot's
+ * environment as it stands instead of sweeping), then for the caller's
+ * dev_A2 [sA][aA][u][r][k] and dev_B2 [sB][aB][d][l][k] (device, FP64,
+ * 4 D^3 each; u, r the legs of A other than gamma, d, l those of B) writes
+ *   dev_gA = dd/dA'' = (R_A + R_A^T) a - 2 S_A,  dev_gB = dd/dB'' likewise,
+ * where R, S are the normal-equation matrices of that side with the other
+ * factor fixed (same layouts as A'', B''), and host_cost[0] = d, [1] =
+ * <T'|N|T'>, [2] = d evaluated from the B side (equal to [0] up to
+ * rounding).  The state A, B is not changed; the slot's environment is
+ * (warm-started sweeps).  Synchronises the stream. */
+kh_status eefu_cost_gradient(kh_ctx* ctx, int gamma, const double* host_gate,
+                             const double* dev_A2, const double* dev_B2, int ctm_max_sweeps,
+                             int ctm_min_sweeps, double ctm_tol, double* dev_gA, double* dev_gB,
+                             double* host_cost);
+
 /* Observables of the current (un-gated) state: for each gamma a CTMRG of the
  * composite in slot 3+gamma (warm start from its last run, else from slot
  * gamma), then <H^gamma> with host_H = three 4x4 bond Hamiltonians (x, y, z,

@@ -25,7 +25,7 @@ ABI_FUNCTIONS = [
     "kh_config_defaults", "kh_workspace_bytes", "kh_create", "kh_destroy", "kh_last_error",
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
-    "ctm_expval", "ctm_correlation_length", "eefu_apply_gate", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
+    "ctm_expval", "ctm_correlation_length", "eefu_apply_gate", "eefu_cost_gradient", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
     "eefu_trotter_step", "eefu_evolve", "eefu_evolve_batch", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
     "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_svd_refined", "kh_selftest_orth", "kh_selftest_fp64_newton",
     "kh_selftest_site_layered_bytes", "kh_selftest_site_layered", "kh_gemm_noalloc",
@@ -78,6 +78,7 @@ def load_library(path=LIB_PATH):
         "ctm_expval": (I, [P, I, dp, I, dp]),
         "ctm_correlation_length": (I, [P, I, I, I, D, dp]),
         "eefu_apply_gate": (I, [P, I, dp, I, I, D, dp]),
+        "eefu_cost_gradient": (I, [P, I, dp, P, P, I, I, D, P, P, dp]),
         "observables": (I, [P, dp, D, D, I, I, D, dp]),
         "kh_bond_hamiltonian": (I, [I, D, D, D, D, dp]),
         "kh_gate": (I, [dp, D, dp]),
@@ -485,6 +486,23 @@ class Context:
                                           ctm_tol, None))
         return None
 
+    def cost_gradient(self, gamma, gate, A2, B2, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12):
+        """(gA, gB, d, <T'|N|T'>) of the bond cost d = <T''-T'|N|T''-T'> for the
+        gamma-bond update of the current state with the 4 x 4 gate, at the
+        trial factors A2 [sA][aA][u][r][k], B2 [sB][aB][d][l][k] (float64 CUDA
+        tensors); ctm_max_sweeps = 0 reuses the slot's environment."""
+        torch = self.torch
+        A2 = A2.contiguous()
+        B2 = B2.contiguous()
+        gA = torch.empty_like(A2)
+        gB = torch.empty_like(B2)
+        g, gp = _dptr(np.asarray(gate, dtype=np.float64).reshape(16))
+        out = np.zeros(3)
+        o, op = _dptr(out)
+        self._check(lib().eefu_cost_gradient(self._ctx, GAMMA.get(gamma, gamma), gp, _tptr(A2), _tptr(B2),
+                                             ctm_max_sweeps, ctm_min_sweeps, ctm_tol, _tptr(gA), _tptr(gB), op))
+        return gA, gB, float(o[0]), float(o[1])
+
     def eefu_trotter_step(self, J, K_xyz, dbeta, hA=0.0, hB=0.0, ctm_max_sweeps=100, ctm_min_sweeps=1,
                           ctm_tol=1e-12, info=True):
         k, kp = _dptr(np.asarray(K_xyz, dtype=np.float64))
@@ -553,3 +571,29 @@ def evolve_batch(contexts, J, K_xyz, dbeta, n_steps, measure_every=1, hA=None, h
         raise KhError(st, "problem %d: %s" % (bad[0], lib().kh_last_error(contexts[bad[0]]._ctx).decode()))
     rows = o.reshape(n, max(nm, 1), len(keys))[:, :nm]
     return [[dict(zip(keys, r.tolist())) for r in prob] for prob in rows]
+
+
+_BOND_COST = None
+
+
+def bond_cost(ctx, gamma, gate, A2, B2, ctm_max_sweeps=0, ctm_min_sweeps=1, ctm_tol=1e-12):
+    """The bond cost d(A'', B'') = <T''-T'|N|T''-T'> of ctx's current state
+    and gate as a differentiable torch scalar: the forward and backward passes
+    are one eefu_cost_gradient call (the hand-written adjoint); by default
+    the slot's environment is reused (ctm_max_sweeps = 0), so N is fixed."""
+    global _BOND_COST
+    import torch
+    if _BOND_COST is None:
+        class BondCost(torch.autograd.Function):
+            @staticmethod
+            def forward(fctx, a2, b2, c, gm, gt, mx, mn, tol):
+                gA, gB, d, _ = c.cost_gradient(gm, gt, a2.detach(), b2.detach(), mx, mn, tol)
+                fctx.save_for_backward(gA, gB)
+                return torch.tensor(d, dtype=torch.float64, device=a2.device)
+
+            @staticmethod
+            def backward(fctx, go):
+                gA, gB = fctx.saved_tensors
+                return go * gA, go * gB, None, None, None, None, None, None
+        _BOND_COST = BondCost
+    return _BOND_COST.apply(A2, B2, ctx, gamma, gate, ctm_max_sweeps, ctm_min_sweeps, ctm_tol)

@@ -370,6 +370,15 @@ kh_status eefu_apply_gate(kh_ctx* ctx, int gamma, const double* gate, int mx, in
     });
 }
 
+kh_status eefu_cost_gradient(kh_ctx* ctx, int gamma, const double* gate, const double* A2, const double* B2, int mx,
+                             int mn, double tol, double* gA, double* gB, double* cost) {
+    KH_RANGE();
+    return guard(ctx, [&] {
+        if (!gate || !A2 || !B2 || !gA || !gB || !cost || mx < 0) kh::fail(KH_EINVAL, "bad arguments");
+        ctx->eng->cost_gradient(gamma, gate, A2, B2, mx, mn, tol, gA, gB, cost);
+    });
+}
+
 kh_status observables(kh_ctx* ctx, const double* H, double hA, double hB, int mx, int mn, double tol,
                       double* out) {
     KH_RANGE();

@@ -651,11 +651,86 @@ __global__ void gauge_kernel(const double* __restrict__ A2, const double* __rest
     }
 }
 
+// Gradient of the bond cost d = <T''-T'|N|T''-T'> with respect to one factor
+// (Own, layout [ph][a], a = (o1, o2, k)) with the other fixed, from the
+// normal-equation matrices of that side (d = sum_ph Own_ph^T R Own_ph
+// - 2 sum Own[ph][a] S[a][ph] + <T'|N|T'>):
+//   G[ph][a] = sum_a' (R[a][a'] + R[a'][a]) Own[ph][a'] - 2 S[a][ph];
+// the quadratic and linear parts of d are added into *e.
+__global__ void cost_grad_kernel(const double* __restrict__ R, const double* __restrict__ S,
+                                 const double* __restrict__ Own, int m, double* __restrict__ G, double* e) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 4 * m; i += gridDim.x * blockDim.x) {
+        const int ph = i / m, a = i % m;
+        const double* own = Own + (long long)ph * m;
+        double sym = 0.0, row = 0.0;
+        for (int b = 0; b < m; ++b) {
+            const double r1 = R[(long long)a * m + b], r2 = R[(long long)b * m + a];
+            sym += (r1 + r2) * own[b];
+            row += r1 * own[b];
+        }
+        const double sa = S[(long long)a * 4 + ph];
+        G[i] = sym - 2.0 * sa;
+        atomicAdd(e, own[a] * (row - 2.0 * sa));
+    }
+}
+
+template <typename T>
+void Engine<T>::normal_equations(const double* oth, int side, const int* skip) {
+    const int D = dm.D, D4 = dm.D4, m = D * D * D;
+    const int threads = 256;
+    const long long nX = 4LL * dm.d2 * D4 * D, nR = (long long)m * m;
+    const int sgrid = (int)((4LL * m * 32 + threads - 1) / threads);
+    als_x_kernel<<<grid_for(nX), threads, 0, st>>>(N, oth, D, side, XA, skip);
+    KH_LAUNCHED();
+    als_r_kernel<<<grid_for(nR), threads, 0, st>>>(XA, oth, D, side, R, skip);
+    KH_LAUNCHED();
+    als_s_kernel<<<sgrid, threads, 0, st>>>(XA, slots[als_slot].Ts, D, side, S, skip);
+    KH_LAUNCHED();
+}
+
+template <typename T>
+void Engine<T>::cost_gradient(int gamma, const double* gate, const double* A2in, const double* B2in, int mx, int mn,
+                              double tol, double* gA, double* gB, double* cost_out) {
+    if (gamma < 0 || gamma > 2) fail(KH_EINVAL, "gamma must be 0, 1 or 2");
+    if (dm.nslots < 3) fail(KH_EINVAL, "eeFU needs n_slots >= 3");
+    if (mx < 0) fail(KH_EINVAL, "ctm_max_sweeps < 0");
+    Slot<T>& sl = slots[gamma];
+    if (mx == 0 && !sl.env_valid) fail(KH_EINVAL, "no environment to reuse (ctm_max_sweeps = 0)");
+    build_composite(gamma, gamma, gate);
+    if (mx > 0) {
+        double delta = 0.0;
+        sweep(gamma, mx, mn, tol, &delta);
+    } else {
+        refresh_operands(sl);
+    }
+    compute_metric(sl, N);
+    const int D = dm.D, m = D * D * D;
+    const long long own = 4LL * m;
+    KH_CUDA(cudaMemcpyAsync(A2, A2in, sizeof(double) * own, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaMemcpyAsync(B2, B2in, sizeof(double) * own, cudaMemcpyDeviceToDevice, st));
+    KH_CUDA(cudaMemsetAsync(cost, 0, 8 * sizeof(double), st));
+    tnt_kernel<<<grid_for(16LL * dm.D4 * dm.D4), 256, 0, st>>>(sl.Ts, N, dm.D4, cost);
+    KH_LAUNCHED();
+    als_slot = gamma;
+    normal_equations(B2, 0, nullptr);                      // A side (B'' fixed)
+    cost_grad_kernel<<<grid_for(own), 256, 0, st>>>(R, S, A2, m, gA, cost + 5);
+    KH_LAUNCHED();
+    normal_equations(A2, 1, nullptr);                      // B side (A'' fixed)
+    cost_grad_kernel<<<grid_for(own), 256, 0, st>>>(R, S, B2, m, gB, cost + 6);
+    KH_LAUNCHED();
+    double h[8];
+    KH_CUDA(cudaMemcpyAsync(h, cost, sizeof(h), cudaMemcpyDeviceToHost, st));
+    KH_CUDA(cudaStreamSynchronize(st));
+    if (!(h[5] == h[5]) || !(h[6] == h[6])) fail(KH_ENUMERIC, "NaN in the bond cost");
+    cost_out[0] = h[5] + h[0];          // d from the A side
+    cost_out[1] = h[0];                 // <T'|N|T'>
+    cost_out[2] = h[6] + h[0];          // d from the B side (equal up to rounding)
+}
+
 // ------------------------------------------------------------------ ALS driver
 
 template <typename T>
 int Engine<T>::als_run(int gamma, double* rel_cost) {
-    (void)gamma;
     const int D = dm.D, D4 = dm.D4, m = D * D * D, mT = 4 * dm.d2;
     Slot<T>& sl = slots[gamma];
     const double* Tp = sl.Ts;
@@ -681,8 +756,7 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     gemm_rm<double>(mT, D, mT, Tm, true, Wd, false, B2, st, 1.0, 0.0, colsc);
     // initial cost with (A'', B'') from the start: B-side normal equations from A''
     const int threads = 256;
-    const long long nX = 4LL * dm.d2 * D4 * D, nR = (long long)m * m;
-    const int sgrid = (int)((4LL * m * 32 + threads - 1) / threads);
+    const long long nR = (long long)m * m;
     const int cgrid = (int)std::min<long long>(32, (nR + threads - 1) / threads);
     const size_t chol_sm = sizeof(double) * ((size_t)m * (m + 1) + 4 * m);
     const int chol_smem = chol_sm <= 200 * 1024 ? 1 : 0;
@@ -691,14 +765,8 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
         smem_opt_in(chol_solve_kernel, chol_sm, granted);
     }
     const int* done = flags + 1;
-    auto normal_eqs = [&](const double* oth, int side) {
-        als_x_kernel<<<grid_for(nX), threads, 0, st>>>(N, oth, D, side, XA, done);
-        KH_LAUNCHED();
-        als_r_kernel<<<grid_for(nR), threads, 0, st>>>(XA, oth, D, side, R, done);
-        KH_LAUNCHED();
-        als_s_kernel<<<sgrid, threads, 0, st>>>(XA, Tp, D, side, S, done);
-        KH_LAUNCHED();
-    };
+    als_slot = gamma;
+    auto normal_eqs = [&](const double* oth, int side) { normal_equations(oth, side, done); };
     normal_eqs(A2, 1);
     als_cost_kernel<<<cgrid, threads, 0, st>>>(R, S, B2, m, cost, flags + 1, cfg.als_tol, 1, nullptr);
     KH_LAUNCHED();

@@ -115,6 +115,8 @@ struct EngineBase {
     virtual void expval(int slot, const double* ops, int n_ops, double* vals) = 0;
     virtual void correlation_length(int slot, int dir, int max_iter, double tol, double* out) = 0;
     virtual void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) = 0;
+    virtual void cost_gradient(int gamma, const double* gate, const double* A2, const double* B2, int mx, int mn,
+                               double tol, double* gA, double* gB, double* cost) = 0;
     virtual void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                              double* out) = 0;
     // persistent state to / from an open checkpoint file (checkpoint.cu)
@@ -278,6 +280,10 @@ struct Engine : EngineBase {
     void expval(int slot, const double* ops, int n_ops, double* vals) override;
     void correlation_length(int slot, int dir, int max_iter, double tol, double* out) override;   // xi.cu
     void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) override;
+    void cost_gradient(int gamma, const double* gate, const double* A2in, const double* B2in, int mx, int mn,
+                       double tol, double* gA, double* gB, double* cost_out) override;
+    void normal_equations(const double* oth, int side, const int* skip);   // R, S of one ALS side
+    int als_slot = 0;          // slot whose composite T' the normal equations read
     void observables(const double* H, double hA, double hB, int mx, int mn, double tol,
                      double* out) override;
     void save_checkpoint(std::FILE* f) override;
