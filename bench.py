@@ -413,6 +413,8 @@ def run_ours(a, rank, world, local, pg):
             variants.append(variant(g, dev, a, w, 6, 144, a.prec, 2, 3, flush, proj_fp64=a.proj_fp64))
             # the same workload with the double-layer site operand (the D^2 index formed)
             variants.append(variant(g, dev, a, w, D, chi, a.prec, 3, 3, flush, proj_fp64=a.proj_fp64, site_form=2))
+            # BF16 contractions (layered site contraction on kind::f16)
+            variants.append(variant(g, dev, a, w, D, chi, "bf16", 3, 3, flush, proj_fp64=a.proj_fp64))
             # sixteen coupling angles at once
             variants.append(batch_variant(g, dev, a, w, D, chi, a.prec, 3, 16, proj_fp64=a.proj_fp64))
         cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, wl.A0, wl.B0)   # N = 1 only
@@ -523,7 +525,7 @@ def run_reference(a, rank, world):
 def run_kernel(a):
     """Profiling mode: the tensor-core contraction GEMM on size^3 operands
     (inputs larger than L2), or the layered site contraction of one corner
-    (chi^2 blocks of D^2 x D^2, p = 16, 3xTF32), timed with CUDA events; one
+    (chi^2 blocks of D^2 x D^2, p = 16, in --prec), timed with CUDA events; one
     JSON line.  The times include the self-test's operand preparation."""
     import torch
     import paper_1906_02220_gb300 as g
@@ -532,16 +534,17 @@ def run_kernel(a):
         D, nb = a.D, a.chi * a.chi
         T = torch.randn((16, D, D, D, D), dtype=torch.float64, device="cuda:0", generator=gen)
         Y = torch.randn((nb, D * D, D * D), dtype=torch.float64, device="cuda:0", generator=gen)
+        npass = {"tf32x3": 3, "tf32": 1, "bf16": 16}[a.prec]
         t = []
         for i in range(a.warmup + a.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            g.selftest_site_layered(T, Y, 0, 0, 3)
+            g.selftest_site_layered(T, Y, 0, 0, npass)
             e1.record()
             torch.cuda.synchronize()
             if i >= a.warmup:
                 t.append(e0.elapsed_time(e1))
-        print(json.dumps({"kernel": "site_layered", "D": D, "chi": a.chi, "p": 16, "prec": "tf32x3",
+        print(json.dumps({"kernel": "site_layered", "D": D, "chi": a.chi, "p": 16, "prec": a.prec,
                           "ms_incl_preparation": min(t), "flops": 4.0 * 16 * nb * D ** 6}))
         return
     n = a.size

@@ -67,7 +67,9 @@ typedef enum {
     KH_FP32 = 1,        /* CUDA-core FP32 contractions, FP32 accumulate         */
     KH_TF32 = 2,        /* tcgen05 kind::tf32, FP32 accumulate in TMEM          */
     KH_TF32X3 = 3,      /* tcgen05 kind::tf32 with hi/lo operand split (3 MMAs) */
-    KH_BF16 = 4         /* tcgen05 kind::f16 with bf16 operands, FP32 accumulate */
+    KH_BF16 = 4         /* the layered site contraction on tcgen05 kind::f16 with
+                           BF16 operands (one pass), FP32 accumulate; the
+                           half-system product TF32 (one pass)                  */
 } kh_prec;
 
 typedef struct kh_config {
@@ -382,7 +384,7 @@ kh_status kh_selftest_orth(int prec, int n, int k, double cut, const double* dev
  * ob index D^2 leg pairs and TL is the site tensor dev_T[p][l][u][r][d] seen
  * from frame `frame` (0..3, each a quarter turn (l,u,r,d) <- (d,l,u,r) of the
  * previous): kind 0 (corner) TL[(l,u)][p][(r,d)], kind 1 (edge)
- * TL[(l,d)][p][(u,r)].  npass 1 = TF32, 3 = 3xTF32.  dev_scratch holds at
+ * TL[(l,d)][p][(u,r)].  npass 1 = TF32, 3 = 3xTF32, 16 = BF16.  dev_scratch holds at
  * least kh_selftest_site_layered_bytes(npass, D, p, nb) bytes (0 = invalid
  * arguments).  KH_ETIMEOUT if a wait in the kernel timed out.  Synchronises
  * stream. */

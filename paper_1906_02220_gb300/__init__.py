@@ -269,6 +269,10 @@ def default_config(D, chi, prec="fp64", **kw):
         c.jacobi_max_sweeps = 8
         c.svd_cut = 1e-4
         c.svd_iters_warm = 2
+        if c.prec == PREC["bf16"]:
+            # BF16 contractions (8-bit mantissas) leave the projector spectrum
+            # noisy at ~1e-3 s_1
+            c.svd_cut = 1e-3
     for k, v in kw.items():
         setattr(c, k, v)
     return c

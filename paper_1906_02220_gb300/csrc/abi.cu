@@ -151,7 +151,6 @@ kh_status kh_create(kh_ctx** out, const kh_config* c, void* ws, size_t bytes, vo
         if ((uintptr_t)ws % 256 != 0) kh::fail(KH_EINVAL, "workspace must be 256-byte aligned");
         size_t need = kh_workspace_bytes(c);
         if (bytes < need) kh::fail(KH_ENOMEM, "workspace smaller than kh_workspace_bytes()");
-        if (c->prec == KH_BF16) kh::fail(KH_EINVAL, "precision not built in this library version");
         cudaStream_t st = (cudaStream_t)stream;
         KH_CUDA(cudaGetDevice(&ctx->device));
         if (c->prec == KH_FP64) ctx->eng = new kh::Engine<double>(*c, ws, bytes, st);

@@ -11,6 +11,8 @@
 // SVD of T' as a (4D^2)x(4D^2) matrix; alternate the two quadratic
 // subproblems (R + reg tr(R)/m I) X = S (FP64 Cholesky); balanced gauge from
 // the Gram matrices of A'' and B''.
+#include <cuda_bf16.h>
+
 #include "engine.cuh"
 #include "layered.cuh"
 
@@ -147,20 +149,23 @@ __global__ void wt_kernel(const double* __restrict__ Tm, int p, int D, T* Wc, T*
 __global__ void layered_img_kernel(const double* __restrict__ Tm, int p, int D, lay::Plan P, int npass,
                                    float* __restrict__ img1, float* __restrict__ img2, long long per1,
                                    long long per2) {
+    // per1, per2 in floats; elements of P.esz bytes (TF32 values or BF16)
     const int npl = npass == 3 ? 2 : 1;
-    const long long tot1 = 8 * per1, tot = tot1 + 8 * per2;
+    const int epf = 4 / P.esz;                                 // elements per float slot
+    const long long e1 = per1 * epf, e2 = per2 * epf;          // elements per (kind, frame)
+    const long long tot1 = 8 * e1, tot = tot1 + 8 * e2;
     const long long D4 = (long long)D * D * D * D;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot;
          i += (long long)gridDim.x * blockDim.x) {
         const bool ket = i < tot1;
         const long long e = ket ? i : i - tot1;
-        const long long per = ket ? per1 : per2;
+        const long long per = ket ? e1 : e2;
         const int kf = (int)(e / per), kind = kf >> 2, f = kf & 3;
         const long long rem = e % per;
-        const int sub = (ket ? P.b1_bytes : P.b2_bytes) / 4;      // floats of one hi or lo image
+        const int sub = (ket ? P.b1_bytes : P.b2_bytes) / P.esz;  // elements of one hi or lo image
         const int idx = (int)(rem / sub), c = idx / npl, hl = idx % npl;
         int r, k;
-        lay::swz_position((int)(rem % sub) * 4, ket ? P.n1p : P.n2p, r, k);
+        lay::swz_position((int)(rem % sub) * P.esz, ket ? P.n1p : P.n2p, r, k, P.esz);
         int in = -1, out = -1, pp = p;
         if (ket && r < P.n1 && k < P.d2) {                 // row (pl, ok), column ik
             in = k;
@@ -177,20 +182,25 @@ __global__ void layered_img_kernel(const double* __restrict__ Tm, int p, int D, 
                                       : frame_offset(f, in / D, out / D, out % D, in % D, D);
             v = Tm[pp * D4 + off];
         }
-        float x = (float)v;
-        if (npass == 3) {
-            const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-            x = hl == 0 ? h : x - h;
+        if (P.esz == 2) {
+            __nv_bfloat16* dst = (__nv_bfloat16*)(ket ? img1 : img2);
+            dst[e] = __double2bfloat16(v);
+        } else {
+            float x = (float)v;
+            if (npass == 3) {
+                const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+                x = hl == 0 ? h : x - h;
+            }
+            (ket ? img1 : img2)[e] = x;
         }
-        (ket ? img1 : img2)[e] = x;
     }
 }
 
-void build_layered_images(const double* Tm, int p, int D, int npass, float* img1, float* img2, long long per1,
-                          long long per2, cudaStream_t st) {
-    const long long tot = 8 * (per1 + per2);
-    layered_img_kernel<<<grid_for(tot), 256, 0, st>>>(Tm, p, D, lay::make_plan(D, npass), npass, img1, img2, per1,
-                                                      per2);
+void build_layered_images(const double* Tm, int p, int D, int npass, bool bf16, float* img1, float* img2,
+                          long long per1, long long per2, cudaStream_t st) {
+    const long long tot = 8 * (per1 + per2) * (bf16 ? 2 : 1);
+    layered_img_kernel<<<grid_for(tot), 256, 0, st>>>(Tm, p, D, lay::make_plan(D, npass, bf16), npass, img1, img2,
+                                                      per1, per2);
     KH_LAUNCHED();
 }
 
@@ -202,7 +212,8 @@ void Engine<T>::build_derived(Slot<T>& sl) {
     // the double-layer form costs D^8 per block against 2 p D^6 layer by layer
     sl.dl = dm.dl_alloc && dm.d2 <= 2 * sl.p;
     if (dm.lay && !sl.dl)
-        build_layered_images(sl.Ts, sl.p, dm.D, dm.npass, (float*)sl.L1, (float*)sl.L2, dm.lay1, dm.lay2, st);
+        build_layered_images(sl.Ts, sl.p, dm.D, dm.npass, dm.bf16, (float*)sl.L1, (float*)sl.L2, dm.lay1, dm.lay2,
+                             st);
     if (sl.dl) {
         const bool split = sizeof(T) == 4 && tc_npass == 3 && dm.D4 % 4 == 0;
         const long long tot8 = 8LL * dm.D4 * dm.D4;

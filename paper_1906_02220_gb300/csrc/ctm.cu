@@ -45,14 +45,15 @@ Dims make_dims(const kh_config& c, bool fp64) {
     d.n = c.chi * d.d2;
     d.pmax = c.p_max;
     d.nslots = c.n_slots;
-    d.npass = fp64 ? 0 : (c.prec == KH_TF32 ? 1 : (c.prec == KH_TF32X3 ? 3 : 0));
+    d.npass = fp64 ? 0 : ((c.prec == KH_TF32 || c.prec == KH_BF16) ? 1 : (c.prec == KH_TF32X3 ? 3 : 0));
+    d.bf16 = !fp64 && c.prec == KH_BF16;
     // site contraction form: layered on the tensor cores unless the double-layer
     // operand is asked for; on the CUDA cores the double-layer operand where it
     // halves the flops, unless the layered form is asked for
     d.dl_alloc = d.d2 <= 2 * c.p_max && (c.site_form == 2 || (c.site_form == 0 && d.npass == 0));
     d.lay = d.npass != 0;
-    d.lay1 = d.lay ? layered_img1_floats(c.D, c.p_max, d.npass) : 0;
-    d.lay2 = d.lay ? layered_img2_floats(c.D, c.p_max, d.npass) : 0;
+    d.lay1 = d.lay ? layered_img1_floats(c.D, c.p_max, d.npass, d.bf16) : 0;
+    d.lay2 = d.lay ? layered_img2_floats(c.D, c.p_max, d.npass, d.bf16) : 0;
     if (d.lay && (d.lay1 == 0 || d.lay2 == 0)) fail(KH_EINVAL, "no tensor-core plan for this D");
     int kmax = fp64 ? 112 : 160;      // the one-CTA Jacobi limits (FP64, FP32)
     if (d.n <= kmax) {
@@ -249,7 +250,7 @@ Engine<T>::Engine(const kh_config& c, void* ws, size_t bytes, cudaStream_t s) {
     st = s;
     lanes[0].st = s;
     dm = make_dims(c, sizeof(T) == 8);
-    tc_npass = (c.prec == KH_TF32) ? 1 : (c.prec == KH_TF32X3 ? 3 : 0);
+    tc_npass = (c.prec == KH_TF32 || c.prec == KH_BF16) ? 1 : (c.prec == KH_TF32X3 ? 3 : 0);
     Carver cv(ws, bytes);
     layout(cv);
     for (int i = 1; i < nlanes; ++i) {
@@ -595,7 +596,7 @@ void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, const T* L1
     prof_begin(1);
     if (!Wt && L1) {                                   // layered, on the tensor cores
         site_layered_tc((const float*)Ybuf, nb, dm.D, p, (const float*)L1, (const float*)L2, (float*)out,
-                        tc_npass, tc_err, st);
+                        tc_npass, dm.bf16, tc_err, st);
         prof_end(1, 4.0 * (double)nb * p * d2 * (double)d2 * d2);
         return;
     }

@@ -44,7 +44,8 @@ struct Dims {
     bool full;                 // kk == n: exact Rayleigh-Ritz on the whole space
     bool dl_alloc;             // double-layer operands allocated (D^2 <= 2 p_max and the site form allows)
     bool lay;                  // layered tensor-core site contraction (tensor-core precisions)
-    int npass;                 // tensor-core passes: 0 (CUDA cores), 1 (TF32), 3 (3xTF32)
+    int npass;                 // tensor-core passes: 0 (CUDA cores), 1 (TF32 or BF16), 3 (3xTF32)
+    bool bf16;                 // layered site contraction with BF16 operands (kind::f16)
     long long lay1, lay2;      // floats per (kind, frame) of the ket and bra operand images
 };
 

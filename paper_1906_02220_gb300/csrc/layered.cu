@@ -26,6 +26,8 @@
 // returns with bits set in *err (8 producer, 16 MMA issuer, 32 workers).
 #include <atomic>
 
+#include <cuda_bf16.h>
+
 #include "engine.cuh"
 #include "layered.cuh"
 #include "tc_ptx.cuh"
@@ -48,8 +50,18 @@ constexpr int MAXST = 16;
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
 
-constexpr uint32_t idesc(int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// instruction descriptor: FP32 accumulator, A and B TF32 (kind::tf32) or BF16
+// (kind::f16), K-major, N and M = 128
+constexpr uint32_t idesc(int n, bool bf16) {
+    const uint32_t fmt = bf16 ? 1u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// packs two FP32 values as BF16 (round to nearest even), a in the low half
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+    return lo | (hi << 16);
 }
 
 struct Bars {
@@ -72,15 +84,17 @@ __device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
-template <int D, int NPASS>
+template <int D, int NPASS, bool BF>
 __global__ void __launch_bounds__(THREADS, 1)
 layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t* __restrict__ img1,
                const uint8_t* __restrict__ img2, float* __restrict__ out, int ntiles, int nst1, int nst2,
                int* err) {
-    constexpr Plan P = make_plan(D, NPASS);
+    static_assert(!BF || NPASS == 1, "BF16 runs one pass");
+    constexpr Plan P = make_plan(D, NPASS, BF);
     constexpr int D2 = P.d2;
     constexpr int NPL = NPASS == 3 ? 2 : 1;
-    constexpr uint32_t ID1 = idesc(P.n1p), ID2 = idesc(P.n2p);
+    constexpr int KS = P.kstep;
+    constexpr uint32_t ID1 = idesc(P.n1p, BF), ID2 = idesc(P.n2p, BF);
     constexpr int A1_SZ = NPL * P.a1_bytes, B1_SZ = NPL * P.b1_bytes, B2_SZ = NPL * P.b2_bytes;
 
     extern __shared__ uint8_t smem_raw[];
@@ -209,12 +223,15 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                             const uint32_t ab = a0 + (pass == 2 ? P.a1_bytes : 0);
                             const uint32_t bb = b0 + (pass == 1 ? P.b1_bytes : 0);
 #pragma unroll
-                            for (int ks = 0; ks < P.k1p / 8; ++ks) {
-                                const int i = pass * (P.k1p / 8) + ks;
+                            for (int ks = 0; ks < P.k1p / KS; ++ks) {
+                                const int i = pass * (P.k1p / KS) + ks;
                                 if ((i % P.nacc1) % NI1 != qi) continue;
+                                // 32 bytes of K per MMA, four per 128-byte block
                                 const uint64_t da = smem_desc(ab + (ks >> 2) * (128 * 128) + (ks & 3) * 32);
                                 const uint64_t db = smem_desc(bb + (ks >> 2) * (P.n1p * 128) + (ks & 3) * 32);
-                                umma_tf32(d0 + (i % P.nacc1) * P.acc1_cols, da, db, ID1, i >= P.nacc1 ? 1u : 0u);
+                                const uint32_t dd = d0 + (i % P.nacc1) * P.acc1_cols;
+                                if constexpr (BF) umma_f16(dd, da, db, ID1, i >= P.nacc1 ? 1u : 0u);
+                                else umma_tf32(dd, da, db, ID1, i >= P.nacc1 ? 1u : 0u);
                             }
                         }
                         umma_commit(&bars.acc1_full[j]);
@@ -246,12 +263,15 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                             const uint32_t aa = a2 + (pass == 2 ? P.a2_cols : 0);
                             const uint32_t bb = b0 + (pass == 1 ? P.b2_bytes : 0);
 #pragma unroll
-                            for (int ks = 0; ks < P.k2p / 8; ++ks) {
-                                const int i = pass * (P.k2p / 8) + ks;
+                            for (int ks = 0; ks < P.k2p / KS; ++ks) {
+                                const int i = pass * (P.k2p / KS) + ks;
                                 if ((i % P.nacc2) % NI2 != qi) continue;
                                 const uint64_t db = smem_desc(bb + (ks >> 2) * (P.n2p * 128) + (ks & 3) * 32);
-                                umma_tf32_tmem_a(d0 + (i % P.nacc2) * P.out_cols, aa + ks * 8, db, ID2,
-                                                 (cc > 0 || i >= P.nacc2) ? 1u : 0u);
+                                const uint32_t dd = d0 + (i % P.nacc2) * P.out_cols;
+                                const uint32_t acc = (cc > 0 || i >= P.nacc2) ? 1u : 0u;
+                                // 8 tensor-memory columns of Z per MMA (8 TF32 or 16 BF16 values)
+                                if constexpr (BF) umma_f16_tmem_a(dd, aa + ks * 8, db, ID2, acc);
+                                else umma_tf32_tmem_a(dd, aa + ks * 8, db, ID2, acc);
                             }
                         }
                         umma_commit(&bars.a2_empty[ja]);
@@ -299,8 +319,10 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
             for (int j = 0; j < YPER; ++j) {
                 const int i = wt + 128 * NSET * j;
                 if (i < P.rows * D2) {
-                    const int o = swz_offset(i / D2, i % D2, 128);
-                    if (NPASS == 3) {
+                    const int o = swz_offset(i / D2, i % D2, 128, P.esz);
+                    if constexpr (BF) {
+                        *(__nv_bfloat16*)(sA1 + o) = __float2bfloat16_rn(yv[j]);
+                    } else if (NPASS == 3) {
                         const float h = tf32_hi(yv[j]);
                         *(float*)(sA1 + o) = h;
                         *(float*)(sA1 + P.a1_bytes + o) = yv[j] - h;
@@ -374,7 +396,7 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                 }
                 fence_after();
                 constexpr int K2R = pad_to(P.k2, 4);          // values read per row
-                constexpr int K2S = pad_to(P.k2p, 16);        // columns stored per row
+                constexpr int K2S = pad_to(P.k2p, BF ? 32 : 16);   // values stored per row (whole 16-column groups)
                 float z[K2S];
 #pragma unroll
                 for (int i = 0; i < K2S; ++i) z[i] = 0.f;
@@ -390,17 +412,29 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                     }
                 }
                 const uint32_t a2 = tmem + lane_base + (uint32_t)(P.c_a2 + ja * NPL * P.a2_cols);
+                if constexpr (BF) {
+                    // two BF16 values per column, the lower K index in the low half
 #pragma unroll
-                for (int c0 = 0; c0 < K2S; c0 += 16) {
-                    float hi[16], lo[16];
+                    for (int c0 = 0; c0 < K2S / 2; c0 += 16) {
+                        float w[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float x = z[c0 + i];
-                        hi[i] = NPASS == 3 ? tf32_hi(x) : x;
-                        lo[i] = x - hi[i];
+                        for (int i = 0; i < 16; ++i)
+                            w[i] = __uint_as_float(pack_bf16x2(z[2 * (c0 + i)], z[2 * (c0 + i) + 1]));
+                        tmem_st16(a2 + (uint32_t)c0, w);
                     }
-                    tmem_st16(a2 + (uint32_t)c0, hi);
-                    if (NPASS == 3) tmem_st16(a2 + (uint32_t)(P.a2_cols + c0), lo);
+                } else {
+#pragma unroll
+                    for (int c0 = 0; c0 < K2S; c0 += 16) {
+                        float hi[16], lo[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const float x = z[c0 + i];
+                            hi[i] = NPASS == 3 ? tf32_hi(x) : x;
+                            lo[i] = x - hi[i];
+                        }
+                        tmem_st16(a2 + (uint32_t)c0, hi);
+                        if (NPASS == 3) tmem_st16(a2 + (uint32_t)(P.a2_cols + c0), lo);
+                    }
                 }
                 tmem_st_wait();
                 fence_before();
@@ -500,10 +534,10 @@ int smem_optin_max() {
     return v;
 }
 
-template <int D, int NPASS>
+template <int D, int NPASS, bool BF>
 void launch_layered(const float* Y, long long nb, int p, const float* img1, const float* img2, float* out, int* err,
                     cudaStream_t st) {
-    constexpr lay::Plan P = lay::make_plan(D, NPASS);
+    constexpr lay::Plan P = lay::make_plan(D, NPASS, BF);
     static_assert(P.pc > 0, "no tensor-memory plan");
     constexpr int NPL = NPASS == 3 ? 2 : 1;
     const int nc = lay::n_chunks(P, p);
@@ -534,50 +568,56 @@ void launch_layered(const float* Y, long long nb, int p, const float* img1, cons
     // would only wait in tcgen05.alloc)
     if (P.tmem > 256 && smem <= cap / 2) smem = cap / 2 + 1024;
     static std::atomic<size_t> granted[kMaxDevices] = {};
-    smem_opt_in(lay::layered_kernel<D, NPASS>, smem, granted);
+    smem_opt_in(lay::layered_kernel<D, NPASS, BF>, smem, granted);
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
-    lay::layered_kernel<D, NPASS><<<grid, lay::THREADS, smem, st>>>(
+    lay::layered_kernel<D, NPASS, BF><<<grid, lay::THREADS, smem, st>>>(
         Y, nb, nc, (const uint8_t*)img1, (const uint8_t*)img2, out, ntiles, nst1, nst2, err);
     KH_LAUNCHED();
 }
 
-template <int NPASS>
+template <int NPASS, bool BF>
 void dispatch_d(const float* Y, long long nb, int D, int p, const float* img1, const float* img2, float* out,
                 int* err, cudaStream_t st) {
     switch (D) {
-        case 1: launch_layered<1, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 2: launch_layered<2, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 3: launch_layered<3, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 4: launch_layered<4, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 5: launch_layered<5, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 6: launch_layered<6, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 7: launch_layered<7, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
-        case 8: launch_layered<8, NPASS>(Y, nb, p, img1, img2, out, err, st); break;
+        case 1: launch_layered<1, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 2: launch_layered<2, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 3: launch_layered<3, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 4: launch_layered<4, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 5: launch_layered<5, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 6: launch_layered<6, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 7: launch_layered<7, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
+        case 8: launch_layered<8, NPASS, BF>(Y, nb, p, img1, img2, out, err, st); break;
         default: fail(KH_EINVAL, "layered site contraction: D out of range");
     }
 }
 
 }  // namespace
 
-long long layered_img1_floats(int D, int p, int npass) {
-    const lay::Plan P = lay::make_plan(D, npass);
+long long layered_img1_floats(int D, int p, int npass, bool bf16) {
+    const lay::Plan P = lay::make_plan(D, npass, bf16);
     if (P.pc == 0) return 0;
     return (long long)lay::n_chunks(P, p) * (npass == 3 ? 2 : 1) * P.b1_bytes / 4;
 }
 
-long long layered_img2_floats(int D, int p, int npass) {
-    const lay::Plan P = lay::make_plan(D, npass);
+long long layered_img2_floats(int D, int p, int npass, bool bf16) {
+    const lay::Plan P = lay::make_plan(D, npass, bf16);
     if (P.pc == 0) return 0;
     return (long long)lay::n_chunks(P, p) * (npass == 3 ? 2 : 1) * P.b2_bytes / 4;
 }
 
 void site_layered_tc(const float* Y, long long nb, int D, int p, const float* img1, const float* img2, float* out,
-                     int npass, int* err, cudaStream_t st) {
+                     int npass, bool bf16, int* err, cudaStream_t st) {
     if (nb <= 0) return;
     if (((uintptr_t)img1 & 15) || ((uintptr_t)img2 & 15) || ((uintptr_t)out & 15) || ((uintptr_t)Y & 3))
         fail(KH_EINVAL, "layered site contraction: misaligned operand");
-    if (npass == 3) dispatch_d<3>(Y, nb, D, p, img1, img2, out, err, st);
-    else dispatch_d<1>(Y, nb, D, p, img1, img2, out, err, st);
+    if (bf16) {
+        if (npass != 1) fail(KH_EINVAL, "layered site contraction: BF16 runs one pass");
+        dispatch_d<1, true>(Y, nb, D, p, img1, img2, out, err, st);
+    } else if (npass == 3) {
+        dispatch_d<3, false>(Y, nb, D, p, img1, img2, out, err, st);
+    } else {
+        dispatch_d<1, false>(Y, nb, D, p, img1, img2, out, err, st);
+    }
 }
 
 }  // namespace kh

@@ -98,10 +98,13 @@ struct LayeredScratch {
     long long per1, per2;
 };
 
+// npass: 1 = TF32, 3 = 3xTF32, 16 = BF16 (one pass)
 LayeredScratch carve_layered(kh::Carver& cv, int npass, int D, int p, long long nb) {
     LayeredScratch L;
-    L.per1 = kh::layered_img1_floats(D, p, npass);
-    L.per2 = kh::layered_img2_floats(D, p, npass);
+    const bool bf = npass == 16;
+    const int np = bf ? 1 : npass;
+    L.per1 = kh::layered_img1_floats(D, p, np, bf);
+    L.per2 = kh::layered_img2_floats(D, p, np, bf);
     const long long d4 = (long long)D * D * D * D;
     L.img1 = cv.take<float>((size_t)(8 * L.per1));
     L.img2 = cv.take<float>((size_t)(8 * L.per2));
@@ -117,10 +120,12 @@ void run_site_layered(int npass, int D, int p, int kind, int frame, long long nb
     LayeredScratch L = carve_layered(cv, npass, D, p, nb);
     const long long d4 = (long long)D * D * D * D;
     KH_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
-    kh::build_layered_images(T, p, D, npass, L.img1, L.img2, L.per1, L.per2, st);
+    const bool bf = npass == 16;
+    const int np = bf ? 1 : npass;
+    kh::build_layered_images(T, p, D, np, bf, L.img1, L.img2, L.per1, L.per2, st);
     kh::cast<double, float>(Y, L.y, nb * d4, st);
     const int kf = kind * 4 + frame;
-    kh::site_layered_tc(L.y, nb, D, p, L.img1 + kf * L.per1, L.img2 + kf * L.per2, L.out, npass, L.err, st);
+    kh::site_layered_tc(L.y, nb, D, p, L.img1 + kf * L.per1, L.img2 + kf * L.per2, L.out, np, bf, L.err, st);
     kh::cast<float, double>(L.out, out, nb * d4, st);
     int h = 0;
     KH_CUDA(cudaMemcpyAsync(&h, L.err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -240,7 +245,7 @@ kh_status kh_selftest_svd_refined(int k, const double* X, double* S, double* L, 
 }
 
 size_t kh_selftest_site_layered_bytes(int npass, int D, int p, long long nb) {
-    if ((npass != 1 && npass != 3) || D < 1 || D > 8 || p < 1 || p > 16 || nb < 0) return 0;
+    if ((npass != 1 && npass != 3 && npass != 16) || D < 1 || D > 8 || p < 1 || p > 16 || nb < 0) return 0;
     kh::Carver cv;
     carve_layered(cv, npass, D, p, nb);
     return cv.off;
@@ -248,7 +253,8 @@ size_t kh_selftest_site_layered_bytes(int npass, int D, int p, long long nb) {
 
 kh_status kh_selftest_site_layered(int npass, int D, int p, int kind, int frame, long long nb, const double* T,
                                    const double* Y, double* out, void* scratch, size_t bytes, void* stream) {
-    if ((npass != 1 && npass != 3) || D < 1 || D > 8 || p < 1 || p > 16 || kind < 0 || kind > 1 || frame < 0 ||
+    if ((npass != 1 && npass != 3 && npass != 16) || D < 1 || D > 8 || p < 1 || p > 16 || kind < 0 || kind > 1 ||
+        frame < 0 ||
         frame > 3 || nb < 1 || !T || !Y || !out || !scratch)
         return KH_EINVAL;
     if (bytes < kh_selftest_site_layered_bytes(npass, D, p, nb)) return KH_ENOMEM;

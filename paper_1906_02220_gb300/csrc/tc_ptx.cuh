@@ -102,6 +102,29 @@ __device__ __forceinline__ void umma_tf32_tmem_a(uint32_t tmem_d, uint32_t tmem_
         : "memory");
 }
 
+// kind::f16 (BF16 or FP16 operands, K = 16 per instruction, FP32 accumulate
+// with the instruction descriptor's formats): A, B from shared memory, and A
+// from tensor memory (two 16-bit values per column, the lower K index in the
+// low half).
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_f16_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t idesc,
+                                                uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        ::"r"(tmem_d), "r"(tmem_a), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // Stores 16 consecutive 32-bit columns of this warp's 32 tensor-memory lanes
 // (one row per thread) and waits for the stores to complete.
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {

@@ -266,6 +266,33 @@ def test_kz_only_closed_form(g, prec):
     assert abs(r["E_site"] - exact.kz_only_energy(Kz, 0.4)) < TOL[prec]
 
 
+@pytest.mark.parametrize("D,chi,steps", [(2, 16, 4), (3, 12, 2)])
+def test_bf16_trotter_steps_near_oracle(g, D, chi, steps):
+    """BF16 contractions (the layered site contraction on kind::f16, one
+    pass, FP32 accumulation): after the same Trotter steps as the FP64 and
+    3xTF32 parity test, E/site, <H^gamma> and the magnetisations agree with
+    the oracle run at the same projector cut-off (1e-3 s_1, above the BF16
+    noise of the projector spectrum) within 1e-4 of max(1, |x|).  A single
+    BF16 contraction is good to its unit roundoff 2^-9 ~ 2e-3 (the kernel
+    test); the converged environment and the ALS do not accumulate it (1.7e-5
+    measured at (3, 12))."""
+    J, K = model.couplings(0.3 * np.pi)
+    hA, hB = 0.3, -0.1
+    A, B = kh_inputs.perturbed_product_state(D, seed=11, eps=0.05)
+    st = _oracle_state(D, chi, J, K, A, B, hA=hA, hB=hB, svd_cut=1e-3, ctm_tol=1e-12)
+    ctx = g.Context(D, chi, "bf16", svd_cut=1e-3)
+    ctx.set_state(_t(A), _t(B))
+    for n in range(steps):
+        eefu.trotter_step(st, 0.02)
+        ctx.eefu_trotter_step(J, [K, K, K], 0.02, hA, hB, ctm_max_sweeps=60, ctm_tol=1e-5)
+    ro = eefu.measure(st)
+    Hs = [g.bond_hamiltonian(gm, J, K) for gm in "xyz"]
+    r = ctx.observables(Hs, hA, hB, ctm_max_sweeps=60, ctm_tol=1e-5)
+    for key in ("E_site", "Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+        assert abs(r[key] - ro[key]) < 1e-4 * max(1.0, abs(ro[key])), (key, r[key], ro[key])
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("D,chi,steps", [(2, 16, 4), (3, 12, 2)])
 def test_trotter_steps_match_oracle(g, prec, D, chi, steps):
