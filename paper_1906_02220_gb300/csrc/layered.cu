@@ -13,15 +13,20 @@
 //   warps 2, 3           one lane each issues half of the bra GEMMs' MMAs
 //                          out         += Z_c   * B2_c    (A = Z in tensor memory)
 //                        (each group committed to an mbarrier);
-//   warps 4-7 (workers)  load the Y tile (hi/lo split) into shared memory, read
-//                        acc1 row (b, ib) per thread, scatter it into a
-//                        shared-memory buffer in (b, ok) row order, read back
-//                        row (b, ok), split it into TF32 hi/lo and store it to
+//   warps 4-7 (workers)  load the Y tile (hi/lo split, or BF16) into shared
+//                        memory (the next tile's values fetched into registers
+//                        while this tile's chunks run), read acc1 row (b, ib)
+//                        per thread, scatter it into a shared-memory buffer in
+//                        (b, ok) row order, read back row (b, ok), split it into
+//                        TF32 hi/lo (or round it to BF16 pairs) and store it to
 //                        tensor memory as the bra GEMM's A operand; at the end
-//                        of a tile they read the output accumulator and store
+//                        of a tile they read the output accumulators and store
 //                        out rows (b, ok).
 // With 3 passes every product is A_hi B_hi + A_hi B_lo + A_lo B_hi (FP32-level
-// accuracy from TF32 inputs).  Every wait is bounded: on time-out the kernel
+// accuracy from TF32 inputs); BF16 runs one kind::f16 pass (K = 16 per MMA).
+// The MMAs of each GEMM are spread round-robin over independent accumulators
+// (summed when read) and, for the bra GEMM, over two issuing threads: these
+// narrow MMAs are bound by their issue, not by the tensor pipe.  Every wait is bounded: on time-out the kernel
 // raises a flag, the roles drain, tensor memory is freed and the kernel
 // returns with bits set in *err (8 producer, 16 MMA issuer, 32 workers).
 #include <atomic>
@@ -304,17 +309,19 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
         for (int i = wt; i < A1_SZ / 16; i += 128 * NSET) ((float4*)sA1)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         asm volatile("bar.sync 1, %0;" ::"r"(128 * NSET) : "memory");   // zeros land before the first tile's values
 
-        // the tile's R D^2 values of Y (contiguous), all loads in flight at once
+        // the tile's R D^2 values of Y (contiguous), all loads in flight at once:
+        // fetched into registers, then written (hi/lo split) into the tile image
         constexpr int YPER = (P.rows * D2 + 128 * NSET - 1) / (128 * NSET);
-        auto load_y = [&](int tile) {
+        auto fetch_y = [&](int tile, float (&yv)[YPER]) {
             const long long e0 = (long long)tile * P.rows * D2, etot = total_rows * D2;
-            float yv[YPER];
 #pragma unroll
             for (int j = 0; j < YPER; ++j) {
                 const int i = wt + 128 * NSET * j;
                 const long long e = e0 + i;
                 yv[j] = (i < P.rows * D2 && e < etot) ? __ldg(Y + e) : 0.f;
             }
+        };
+        auto store_y = [&](const float (&yv)[YPER]) {
 #pragma unroll
             for (int j = 0; j < YPER; ++j) {
                 const int i = wt + 128 * NSET * j;
@@ -334,6 +341,15 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
             fence_proxy_async();
             mbar_arrive(&bars.a1_full);
         };
+        auto load_y = [&](int tile) {
+            float yv[YPER];
+            fetch_y(tile, yv);
+            store_y(yv);
+        };
+        // the next tile's values are fetched while this tile's chunks run (where
+        // the registers allow it), so their latency leaves the critical path
+        constexpr bool kPrefetch = YPER <= 32;
+        float ynext[kPrefetch ? YPER : 1];
 
         if ((int)blockIdx.x < ntiles) load_y(blockIdx.x);
         long long g0 = 0;
@@ -369,6 +385,9 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
                 };
                 fence_before();
                 mbar_arrive(&bars.acc1_empty[j]);
+                if constexpr (kPrefetch) {
+                    if (c == 0 && tile + (int)gridDim.x < ntiles) fetch_y(tile + gridDim.x, ynext);
+                }
                 if (t < P.rows) {
                     const int b = t / D2, ib = t % D2;
 #pragma unroll
@@ -448,7 +467,8 @@ layered_kernel(const float* __restrict__ Y, long long nb, int nc, const uint8_t*
             const int next = tile + gridDim.x;
             if (next < ntiles) {
                 if (!wait_warp(&bars.a1_empty, it & 1, abort_flag)) { ok = false; break; }
-                load_y(next);
+                if constexpr (kPrefetch) store_y(ynext);
+                else load_y(next);
             }
             if (set != 0) continue;
             // ---- output rows (b, ok) (first set)
