@@ -343,6 +343,43 @@ def batch_variant(g, dev, a, w, D, chi, prec, steps, nprob=16, proj_fp64=0):
             "E_site_first_last": [trajs[0][-1]["E_site"], trajs[-1][-1]["E_site"]]}
 
 
+def mixed_batch_variant(g, dev, a, w, prec, steps, proj_fp64=0):
+    """The batched shape of many couplings at several sizes: phi in {0, 2 pi/3,
+    4 pi/3} x (D, chi) in {(4, 64), (5, 100), (6, 144)}, nine problems advanced
+    together by one eefu_evolve_batch call (host clock around it, after a
+    one-step warm-up batch).  Reports the wall time of one batch step and the
+    aggregate Trotter steps/s."""
+    import torch
+    sizes = [(4, 64), (5, 100), (6, 144)]
+    phis = [2.0 * math.pi * i / 3 for i in range(3)]
+    ctxs, J, K = [], [], []
+    for D, chi in sizes:
+        for i, phi in enumerate(phis):
+            A0, B0 = kh_inputs.perturbed_product_state(D, seed=i, eps=0.05)
+            c = g.Context(D, chi, prec, device=dev, stream=torch.cuda.Stream(device=dev),
+                          proj_fp64=proj_fp64 if prec != "fp64" else 0)
+            c.set_state(torch.as_tensor(A0, device=dev), torch.as_tensor(B0, device=dev))
+            ctxs.append(c)
+            J.append(math.cos(phi))
+            K.append([2.0 * math.sin(phi)] * 3)
+    kw = dict(ctm_max_sweeps=a.ctm_sweeps, ctm_min_sweeps=a.ctm_sweeps, ctm_tol=-1.0, obs_max_sweeps=a.obs_sweeps,
+              obs_min_sweeps=a.obs_sweeps, obs_tol=-1.0)
+    g.evolve_batch(ctxs, J, K, w["dbeta"], 1, 1, **kw)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    g.evolve_batch(ctxs, J, K, w["dbeta"], steps, 1, **kw)
+    dt = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    n = len(ctxs)
+    return {"config": {"prec": prec, "problems": n, "sizes (D, chi)": sizes, "phi": "0, 2 pi/3, 4 pi/3 per size",
+                       "projector_svd": "fp64" if (proj_fp64 or prec == "fp64") else "fp32",
+                       "ctm_sweeps_per_layer": a.ctm_sweeps, "obs_sweeps_per_mapping": a.obs_sweeps,
+                       "timing": "host clock around one eefu_evolve_batch call"},
+            "value": n * steps / dt, "unit": "steps/s (all problems)", "steps": steps,
+            "ms_per_batch_step": dt / steps * 1e3}
+
+
 def run_ours(a, rank, world, local, pg):
     import torch
     import paper_1906_02220_gb300 as g
@@ -417,6 +454,8 @@ def run_ours(a, rank, world, local, pg):
             variants.append(variant(g, dev, a, w, D, chi, "bf16", 3, 3, flush, proj_fp64=a.proj_fp64))
             # sixteen coupling angles at once
             variants.append(batch_variant(g, dev, a, w, D, chi, a.prec, 3, 16, proj_fp64=a.proj_fp64))
+            # three couplings at each of three sizes at once
+            variants.append(mixed_batch_variant(g, dev, a, w, a.prec, 2, proj_fp64=a.proj_fp64))
         cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, wl.A0, wl.B0)   # N = 1 only
         sw = sweeps_per_step(a)
         out = {
