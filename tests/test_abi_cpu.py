@@ -123,3 +123,48 @@ def test_checkpoint_header_without_gpu(g, tmp_path):
     ctx = ctypes.c_void_p()
     assert g.lib().kh_load(ctypes.byref(ctx), str(tmp_path / "missing").encode(), None, 0, None) == g.KH_EINVAL
     assert ctx.value is None
+
+
+def test_batch_gradient_and_selftest_arguments_without_gpu(g):
+    """Host-side validation of the later entry points, before any GPU work:
+    the batch call rejects empty or null context lists and null couplings;
+    the cost gradient rejects a null context; the layered self-test sizes its
+    scratch for TF32, 3xTF32 and BF16 and returns 0 for an unknown pass count."""
+    import ctypes
+    P = ctypes.c_void_p
+    one = (P * 1)(None)
+    J = np.zeros(1)
+    K = np.zeros(3)
+    traj = np.zeros(13)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    lib = g.lib()
+    assert lib.eefu_evolve_batch(ctypes.cast(one, ctypes.POINTER(P)), 1, dp(J), dp(K), None, None, 0.01, 1, 1, 4, 1,
+                                 -1.0, 2, 1, -1.0, dp(traj), None) == g.KH_EINVAL
+    assert lib.eefu_evolve_batch(None, 0, dp(J), dp(K), None, None, 0.01, 1, 1, 4, 1, -1.0, 2, 1, -1.0, dp(traj),
+                                 None) == g.KH_EINVAL
+    gate = np.eye(4)
+    cost = np.zeros(3)
+    assert lib.eefu_cost_gradient(None, 0, dp(gate), None, None, 0, 1, 1e-12, None, None, dp(cost)) == g.KH_EINVAL
+    sizes = [lib.kh_selftest_site_layered_bytes(npass, 4, 16, 4096) for npass in (1, 3, 16)]
+    assert all(s > 0 for s in sizes)
+    # the 3xTF32 operand images carry a low part: more scratch than one TF32 pass
+    assert sizes[1] > sizes[0]
+    assert lib.kh_selftest_site_layered_bytes(2, 4, 16, 4096) == 0
+    assert lib.kh_selftest_site_layered_bytes(3, 9, 16, 4096) == 0
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
+@pytest.mark.parametrize("D", [2, 4, 6, 8])
+def test_layered_form_sizes_the_workspace(g, prec, D):
+    """In the tensor-core precisions the layered site contraction keeps its
+    chi^2 D^4 p intermediate on chip: doubling p_max grows the workspace only
+    by the slots' site-tensor copies and operand images (O(p D^8) at most),
+    while the CUDA-core layered form grows by its p n^2 scratch in each of
+    the three lanes (n = chi D^2)."""
+    chi = 64
+    n2 = (chi * D * D) ** 2
+    ws = lambda prec_, p, **kw: g.lib().kh_workspace_bytes(g.default_config(D, chi, prec_, p_max=p, **kw))
+    tc_growth = ws(prec, 16) - ws(prec, 8)
+    simt_growth = ws("fp32", 16, site_form=1) - ws("fp32", 8, site_form=1)
+    assert simt_growth >= 3 * 8 * n2 * 4
+    assert 0 <= tc_growth < 0.1 * simt_growth
