@@ -21,12 +21,13 @@ the Kitaev-Heisenberg model at finite temperature", arXiv:1906.02220):
 * ``ctmrg``        -- Fig. 4(c) and Sec. III: square-lattice CTMRG on the
                       quadruple (double-layer) tensor; the environment metric;
                       the correlation length of Sec. IV from the channel
-                      transfer matrix.
+                      transfer matrix; the 2 x 2 cluster in its environment.
 * ``bond``         -- Fig. 3(b) and Sec. III: the environment-weighted bond
                       update A'-B' -> A''-B''.
 * ``observables``  -- energy per site, <S^a> per sublattice, the printed
                       order parameters, the specific heat along a
-                      trajectory (Sec. V).
+                      trajectory, products of operators on a 2 x 2
+                      plaquette and the plaquette flux W (Sec. V).
 * ``eefu``         -- the imaginary-time driver of Sec. III.
 * ``exact``        -- independent pins: exact diagonalisation of honeycomb
                       clusters, Onsager's free energy, Yang's magnetisation,

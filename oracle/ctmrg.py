@@ -205,6 +205,29 @@ def expval_matrix(T, N, Tbra=None):
     return T.reshape(p, -1) @ N @ Tbra.reshape(p, -1).T
 
 
+def cluster_2x2(env, a_ul, a_ur, a_dr, a_dl):
+    """The 2 x 2 cluster of double-layer sites in its environment: the
+    clockwise ring C1 E1 E1 C2 E2 E2 C3 E3 E3 C4 E4 E4 (two edge tensors on
+    each side, chained previous-corner leg to next-corner leg) around the
+    sites a_ul, a_ur (top row) and a_dl, a_dr (bottom row), each edge on the
+    outer leg of the site it faces; neighbouring sites share their facing
+    legs (a_ul.r = a_ur.l, a_ur.d = a_dr.u, a_dr.l = a_dl.r, a_dl.u = a_ul.d).
+    Each quarter (one corner, its two edges, one site) is contracted first;
+    the four quarters close in a ring.  The cluster of the norm network of
+    Fig. 4(a,b) with its semi-infinite surroundings replaced by the CTM
+    environment of Fig. 4(c)."""
+    C1, C2, C3, C4 = env.C
+    E1, E2, E3, E4 = env.E
+    # legs: chi bonds lowercase, site legs uppercase (N, U upper-left outer;
+    # V, R upper-right outer; S, P lower-right outer; Q, M lower-left outer;
+    # H, J, K, I the inner bonds top, right, bottom, left)
+    q_ul = np.einsum("kNl,la,aUb,NUHI->kIbH", E4, C1, E1, a_ul, optimize=True)
+    q_ur = np.einsum("bVc,cd,dRe,HVRJ->bHeJ", E1, C2, E2, a_ur, optimize=True)
+    q_dr = np.einsum("eSf,fg,gPh,KJSP->eJhK", E2, C3, E3, a_dr, optimize=True)
+    q_dl = np.einsum("hQi,ij,jMk,MIKQ->hKkI", E3, C4, E4, a_dl, optimize=True)
+    return np.einsum("kIbH,bHeJ,eJhK,hKkI->", q_ul, q_ur, q_dr, q_dl, optimize=True)
+
+
 def correlation_length(env, a, direction=0):
     """Correlation length in lattice constants along the horizontal
     (direction 0) or vertical (1) axis: xi = 1 / ln|lambda_1 / lambda_2| of the

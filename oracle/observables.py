@@ -10,10 +10,14 @@ of the gamma bond).  Readings: every bond direction is measured on the
 un-gated state with its own gamma-mapped CTMRG; <S^a> of each sublattice is
 taken from the z-mapped environment; E/site = (1/2) sum_gamma <H^gamma> minus
 (h_A <S^z_A> + h_B <S^z_B>)/2 (N/2 sites per sublattice, 3N/2 bonds).
+
+Products of operators on the four composites of a 2 x 2 plaquette come from
+the plaquette's cluster in the same environment (``ctmrg.cluster_2x2``); the
+plaquette flux W of Sec. V is one such product.
 """
 import numpy as np
 
-from . import model
+from . import ctmrg, model, peps
 
 
 def phys_op(O_A=None, O_B=None, O_AB=None):
@@ -65,3 +69,52 @@ def specific_heat(betas, energies):
     e = np.asarray(energies, dtype=np.float64)
     dEdb = (e[2:] - e[:-2]) / (b[2:] - b[:-2])
     return b[1:-1], -b[1:-1] ** 2 * dEdb
+
+
+# ---------------------------------------------------------------- 2 x 2 plaquette, flux
+
+def plaquette_expectation(env, T, ops):
+    """<O_ul O_ur O_dr O_dl> on a 2 x 2 plaquette of composite sites T
+    (translation invariant): the cluster with site i's ket layer O_i T,
+    divided by the plain cluster (both in the converged environment env).
+    ops: four p x p operators (complex allowed) in the order upper-left,
+    upper-right, lower-right, lower-left.  Returns the complex ratio."""
+    p = T.shape[0]
+    Tc = T.astype(np.complex128)
+    plain = ctmrg.double_tensor(Tc)
+    sites = [ctmrg.double_tensor((np.asarray(O) @ Tc.reshape(p, -1)).reshape(T.shape), Tc) for O in ops]
+    return complex(ctmrg.cluster_2x2(env, *sites) / ctmrg.cluster_2x2(env, plain, plain, plain, plain))
+
+
+PAULI = {a: 2.0 * model.SPIN[a] for a in "xyz"}
+
+
+def flux_operators(gamma):
+    """The plaquette flux of the hexagonal lattice, W_p = prod_{i in p}
+    sigma_i^{o(i)} with o(i) the direction of the one bond at site i that
+    leaves the hexagon p (Kitaev's plaquette operator; Sec. V, the flux whose
+    average orders at the lower crossover), as four operators on the
+    composites of a 2 x 2 plaquette of the gamma mapping.
+
+    Geometry of the gamma mapping (``peps``): composite (i, j) holds A(i,j)
+    and B(i,j) joined by gamma; its leg r = A.alpha meets the leg l = B.alpha
+    of composite (i+1, j), its leg u = A.alpha' the leg d = B.alpha' of
+    composite (i, j+1), the one above.  The hexagon
+      A(0,0) -alpha- B(1,0) -gamma- A(1,0) -alpha'- B(1,1) -alpha- A(0,1)
+             -gamma- B(0,1) -alpha'- A(0,0)
+    lies in the plaquette of composites (0,1) upper-left, (1,1) upper-right,
+    (1,0) lower-right, (0,0) lower-left; the leaving bonds are gamma at A(0,0)
+    and B(1,1), alpha' at B(1,0) and A(0,1), alpha at A(1,0) and B(0,1).
+    Returns the 16 x 16 operators on p = (sA, aA, sB, aB), upper-left first."""
+    al, alp = peps.other_bonds(gamma)
+    s = PAULI
+    return [phys_op(O_A=s[alp], O_B=s[al]),     # (0,1): A(0,1) alpha', B(0,1) alpha
+            phys_op(O_B=s[gamma]),              # (1,1): B(1,1) gamma
+            phys_op(O_A=s[al], O_B=s[alp]),     # (1,0): A(1,0) alpha, B(1,0) alpha'
+            phys_op(O_A=s[gamma])]              # (0,0): A(0,0) gamma
+
+
+def flux(env, T, gamma):
+    """<W_p> of the composite T of the gamma mapping in its converged
+    environment (complex arithmetic; the value is real for a real state)."""
+    return plaquette_expectation(env, T, flux_operators(gamma))

@@ -170,3 +170,77 @@ def test_correlation_length_vertical_channel_is_the_rotated_horizontal_one():
     ar, envr, _ = _run(Tr, 16, tol=1e-14)
     assert abs(ctmrg.correlation_length(env, a, 1) - ctmrg.correlation_length(envr, ar, 0)) < 1e-9
     assert abs(ctmrg.correlation_length(env, a, 0) - ctmrg.correlation_length(envr, ar, 1)) < 1e-9
+
+
+# ---------------------------------------------------------------- 2 x 2 cluster
+
+SZ2 = np.diag([1.0, -1.0])
+I2 = np.eye(2)
+# plaquette positions: 0 upper-left, 1 upper-right, 2 lower-right, 3 lower-left
+PAIRS = {"h": [(0, 1), (3, 2)], "v": [(0, 3), (1, 2)], "diag": [(0, 2), (1, 3)]}
+
+
+def _pair_ops(i, j, O=SZ2, p=2):
+    ops = [np.eye(p) for _ in range(4)]
+    ops[i] = O
+    ops[j] = O
+    return ops
+
+
+@pytest.mark.parametrize("Kh,Kv,seed", [(0.3, 0.2, 7), (0.15, 0.36, 11)])
+def test_plaquette_neighbour_pairs_are_free_energy_derivatives(Kh, Kv, seed):
+    """<s s> of the two horizontal pairs of the 2 x 2 cluster is d(-beta f)/dK_h
+    and of the two vertical pairs d(-beta f)/dK_v (central differences of the
+    Onsager integral); with anisotropic couplings and random bond gauges, a
+    cluster that joins the wrong legs or places the sites wrongly fails."""
+    from oracle import observables
+    h = 1e-5
+    dh = (exact.onsager_lnZ(Kh + h, Kv) - exact.onsager_lnZ(Kh - h, Kv)) / (2 * h)
+    dv = (exact.onsager_lnZ(Kh, Kv + h) - exact.onsager_lnZ(Kh, Kv - h)) / (2 * h)
+    T = exact.ising_peps(Kh, Kv, gauge_seed=seed)
+    a, env, _ = _run(T, 24)
+    for kind, want in (("h", dh), ("v", dv)):
+        for i, j in PAIRS[kind]:
+            got = observables.plaquette_expectation(env, T, _pair_ops(i, j))
+            assert abs(got - want) < 1e-9, (kind, i, j, got, want)
+
+
+@pytest.mark.parametrize("hh,hv", [(0.4, -0.7)])
+def test_plaquette_pairs_without_reflection_symmetry(hh, hv):
+    """Directed bond weights (no reflection symmetry of the network, the
+    same Boltzmann weights on the infinite lattice): the pairs still give the
+    plain model's derivatives, and the two diagonals agree."""
+    from oracle import observables
+    Kh, Kv = 0.3, 0.2
+    h = 1e-5
+    dh = (exact.onsager_lnZ(Kh + h, Kv) - exact.onsager_lnZ(Kh - h, Kv)) / (2 * h)
+    dv = (exact.onsager_lnZ(Kh, Kv + h) - exact.onsager_lnZ(Kh, Kv - h)) / (2 * h)
+    T = _directed_ising(Kh, Kv, hh, hv)
+    a, env, _ = _run(T, 16, tol=1e-14)
+    for kind, want in (("h", dh), ("v", dv)):
+        for i, j in PAIRS[kind]:
+            assert abs(observables.plaquette_expectation(env, T, _pair_ops(i, j)) - want) < 1e-9
+    d = [observables.plaquette_expectation(env, T, _pair_ops(i, j)) for i, j in PAIRS["diag"]]
+    assert abs(d[0] - d[1]) < 1e-9
+    assert dv < abs(d[0]) < dh or dh < abs(d[0]) < dv or abs(d[0]) < min(dh, dv)
+
+
+def test_plaquette_single_operator_is_the_site_expectation():
+    """One operator at any of the four positions (identity elsewhere) is the
+    one-site expectation Tr(O X) / Tr(X) of the environment metric, up to the
+    finite-chi difference of the two environments (3e-8 at chi = 16)."""
+    from oracle import observables
+    import kh_inputs
+    T = kh_inputs.random_composite(2, 3, p=4)
+    a, env, info = _run(T, 16)
+    rng = np.random.default_rng(2)
+    O = rng.standard_normal((4, 4))
+    O = O + O.T
+    X = ctmrg.expval_matrix(T, ctmrg.metric(env, 2))
+    want = np.trace(O @ X.T) / np.trace(X)
+    assert abs(want) > 1e-2
+    for pos in range(4):
+        ops = [np.eye(4) for _ in range(4)]
+        ops[pos] = O
+        got = observables.plaquette_expectation(env, T, ops)
+        assert abs(got - want) < 1e-6 * max(1.0, abs(want)), (pos, got, want)

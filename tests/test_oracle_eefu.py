@@ -238,3 +238,73 @@ def test_gate_layer_minimises_the_environment_weighted_cost():
     returns is a stationary point of the cost weighted by the layer's own
     environment metric (Fig. 3(b)), not of the plain (N = 1) truncation."""
     assert _gate_layer_gradient_ratio() < 1e-4
+
+
+# ---------------------------------------------------------------- plaquette flux
+
+def _mapping_envs(A, B, chi=16):
+    """The composite and converged environment of each of the three mappings."""
+    out = {}
+    D = A.shape[2]
+    for gamma in "xyz":
+        T = peps.composite(A, B, gamma)
+        env, info = ctmrg.ctmrg(ctmrg.double_tensor(T), ctmrg.init_env(chi, D), 1e-13, 400)
+        assert info["delta"] < 1e-12
+        out[gamma] = (T, env)
+    return out
+
+
+def _flux_spread(seed):
+    from oracle import observables
+    A, B = kh_inputs.random_site_tensors(2, seed)
+    envs = _mapping_envs(A, B)
+    w = [observables.flux(envs[g][1], envs[g][0], g) for g in "xyz"]
+    return w
+
+
+@pytest.mark.parametrize("seed", [1, 3, 5])
+def test_flux_agrees_across_mappings(seed):
+    """The three mappings place the hexagon in three different ways (other
+    composites, other sites of each composite, other Pauli components at
+    each position) and contract three different networks; every hexagon of
+    the 2-site cell is the same, so <W_p> must agree.  A random real state
+    gives |<W>| ~ 1e-4; the imaginary part vanishes (two sigma^y)."""
+    w = _flux_spread(seed)
+    assert all(abs(x.imag) < 1e-15 for x in w)
+    v = [x.real for x in w]
+    assert min(abs(x) for x in v) > 2e-5
+    assert max(v) - min(v) < 1e-6 * max(abs(x) for x in v), v
+
+
+def test_bonds_between_composites_are_the_inner_bond_of_another_mapping():
+    """In the gamma mapping the alpha bond joins A of one composite to B of
+    its right neighbour and the alpha' bond A of one composite to B of the one
+    above; their two-site correlators on the 2 x 2 plaquette equal those of
+    the bond inside the composite of the alpha (alpha') mapping.  Asymmetric
+    pairs (S^x_A S^z_B against S^z_A S^x_B) fix which end is A."""
+    from oracle import observables
+    A, B = kh_inputs.random_site_tensors(2, 7)
+    envs = _mapping_envs(A, B)
+    S = observables.PAULI
+    I4 = np.eye(16)
+    for gamma in "xyz":
+        al, alp = peps.other_bonds(gamma)
+        T, env = envs[gamma]
+        for bond, (pa, pb) in ((al, (0, 1)), (al, (3, 2)), (alp, (3, 0)), (alp, (2, 1))):
+            Ti, envi = envs[bond]
+            X = ctmrg.expval_matrix(Ti, ctmrg.metric(envi, 2))
+            for a, b in (("x", "z"), ("z", "x"), ("y", "y"), ("z", "z")):
+                ops = [I4] * 4
+                ops = list(ops)
+                ops[pa] = observables.phys_op(O_A=S[a])
+                ops[pb] = observables.phys_op(O_B=S[b])
+                got = observables.plaquette_expectation(env, T, ops)
+                want = observables.expectation(X, observables.phys_op(O_AB=np.kron(S[a], S[b])))
+                assert abs(got.imag) < 1e-14
+                assert abs(got.real - want) < 1e-7, (gamma, bond, pa, pb, a, b, got, want)
+    # the asymmetric pairs differ, so the test sees which end is A
+    Ti, envi = envs["x"]
+    X = ctmrg.expval_matrix(Ti, ctmrg.metric(envi, 2))
+    xz = observables.expectation(X, observables.phys_op(O_AB=np.kron(S["x"], S["z"])))
+    zx = observables.expectation(X, observables.phys_op(O_AB=np.kron(S["z"], S["x"])))
+    assert abs(xz - zx) > 1e-3

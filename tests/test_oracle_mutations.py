@@ -148,8 +148,39 @@ def pin_environment_weighted_layer():
     return _gate_layer_gradient_ratio() / 1e-4
 
 
+def pin_plaquette_pairs(Kh=0.3, Kv=0.2, seed=7):
+    """Horizontal and vertical <s s> of the 2 x 2 cluster against the Onsager
+    derivatives (see test_oracle_ctmrg)."""
+    h = 1e-5
+    dh = (exact.onsager_lnZ(Kh + h, Kv) - exact.onsager_lnZ(Kh - h, Kv)) / (2 * h)
+    dv = (exact.onsager_lnZ(Kh, Kv + h) - exact.onsager_lnZ(Kh, Kv - h)) / (2 * h)
+    T = exact.ising_peps(Kh, Kv, gauge_seed=seed)
+    env, _ = ctmrg.ctmrg(ctmrg.double_tensor(T), ctmrg.init_env(24, 2), 1e-13, 400)
+    sz = np.diag([1.0, -1.0])
+    dev = []
+    for (i, j), want in (((0, 1), dh), ((3, 2), dh), ((0, 3), dv), ((1, 2), dv)):
+        ops = [np.eye(2)] * 4
+        ops = list(ops)
+        ops[i] = sz
+        ops[j] = sz
+        dev.append(abs(observables.plaquette_expectation(env, T, ops) - want))
+    return max(dev) / 1e-9
+
+
+def pin_flux_mappings(seed=3):
+    """<W_p> agrees between the three mappings (see test_oracle_eefu)."""
+    A, B = kh_inputs.random_site_tensors(2, seed)
+    w = []
+    for gamma in "xyz":
+        T = peps.composite(A, B, gamma)
+        env, _ = ctmrg.ctmrg(ctmrg.double_tensor(T), ctmrg.init_env(16, 2), 1e-13, 400)
+        w.append(observables.flux(env, T, gamma).real)
+    return (max(w) - min(w)) / (1e-6 * max(abs(x) for x in w))
+
+
 PINS = [pin_bond_spectrum, pin_beta0, pin_dimer, pin_kz_only, pin_field_only, pin_mappings, pin_onsager,
-        pin_bond_correlations, pin_eckart_young, pin_balanced_gauge, pin_environment_weighted_layer]
+        pin_bond_correlations, pin_eckart_young, pin_balanced_gauge, pin_environment_weighted_layer,
+        pin_plaquette_pairs, pin_flux_mappings]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=lambda p: p.__name__)
@@ -301,3 +332,44 @@ def test_bond_update_without_the_environment_metric_is_caught(monkeypatch):
     orig = bond.als
     monkeypatch.setattr(bond, "als", lambda Tp, N, D, *a, **k: orig(Tp, np.eye(N.shape[0]), D, *a, **k))
     assert _fails(pin_environment_weighted_layer)
+
+
+def test_cluster_with_two_sites_exchanged_is_caught(monkeypatch):
+    """The upper-right and lower-left sites trade places: a horizontal pair
+    becomes a vertical one."""
+    orig = ctmrg.cluster_2x2
+    monkeypatch.setattr(ctmrg, "cluster_2x2", lambda env, a, b, c, d: orig(env, a, d, c, b))
+    assert _fails(pin_plaquette_pairs)
+
+
+def test_cluster_with_a_transposed_corner_is_caught(monkeypatch):
+    orig = ctmrg.cluster_2x2
+
+    def cluster_2x2(env, *a):
+        e = env.copy()
+        e.C[1] = e.C[1].T
+        return orig(e, *a)
+    monkeypatch.setattr(ctmrg, "cluster_2x2", cluster_2x2)
+    assert _fails(pin_plaquette_pairs)
+
+
+@pytest.mark.parametrize("mistake", ["alpha_swapped_upper_left", "mirrored", "rotated", "sublattices_swapped"])
+def test_flux_with_misplaced_operators_is_caught(monkeypatch, mistake):
+    orig = observables.flux_operators
+
+    def flux_operators(gamma):
+        ops = orig(gamma)
+        al, alp = peps.other_bonds(gamma)
+        s = observables.PAULI
+        if mistake == "alpha_swapped_upper_left":
+            ops[0] = observables.phys_op(O_A=s[al], O_B=s[alp])
+        elif mistake == "mirrored":
+            ops = [ops[1], ops[0], ops[3], ops[2]]
+        elif mistake == "rotated":
+            ops = ops[1:] + ops[:1]
+        else:
+            ops = [observables.phys_op(O_A=s[al], O_B=s[alp]), observables.phys_op(O_A=s[gamma]),
+                   observables.phys_op(O_A=s[alp], O_B=s[al]), observables.phys_op(O_B=s[gamma])]
+        return ops
+    monkeypatch.setattr(observables, "flux_operators", flux_operators)
+    assert _fails(pin_flux_mappings)
