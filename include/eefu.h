@@ -216,6 +216,34 @@ kh_status ctm_expval(kh_ctx* ctx, int slot, const double* host_ops, int n_ops,
 kh_status ctm_correlation_length(kh_ctx* ctx, int slot, int direction, int max_iter, double tol,
                                  double* host_out);
 
+/* Product of four operators on a 2 x 2 plaquette of slot's square lattice
+ * (the plaquette flux of Sec. V is one such product).  host_ops holds four
+ * p x p real operators, row-major, acting on the physical index of slot's
+ * tensor, for the positions upper-left, upper-right, lower-right, lower-left.
+ * The cluster of the four sites in slot's environment -- the enlarged
+ * corners of the four frames closed in a ring, Tr(Q_0 Q_1 Q_2 Q_3) -- is
+ * evaluated with operator f applied to the ket layer of site f and divided
+ * by the plain cluster: host_out[0] = <O_0 O_1 O_2 O_3>, host_out[1] = the
+ * plain cluster (a normalisation diagnostic).  The environment should be
+ * converged (ctm_sweep).  Uses the context's scratch and synchronises the
+ * stream.  Errors: KH_EINVAL (bad slot, no tensor or environment, NULL
+ * pointers), KH_ENUMERIC (plain cluster zero or not finite). */
+kh_status ctm_plaquette(kh_ctx* ctx, int slot, const double* host_ops, double* host_out);
+
+/* Plaquette flux <W_p> (Sec. V): W_p = prod of sigma_i^{o(i)} over the six
+ * sites i of a hexagon, o(i) the direction of the one bond at i that leaves
+ * the hexagon (Kitaev's plaquette operator, +1 in the flux-free ground
+ * state).  slot holds the gamma composite (p = 16) of the un-gated state and
+ * its converged environment (after observables(): slot 3 + gamma).  In the
+ * gamma mapping, with (alpha, alpha') the other two directions in cyclic
+ * order, the hexagon's sites and operators are: upper-left composite A
+ * sigma^alpha', B sigma^alpha; upper-right B sigma^gamma; lower-right A
+ * sigma^alpha, B sigma^alpha'; lower-left A sigma^gamma.  Evaluated by
+ * ctm_plaquette with sigma^y = i [[0,-1],[1,0]] (W_p holds two of them).
+ * host_out[0] = <W_p>, host_out[1] = the plain cluster.  Errors as
+ * ctm_plaquette; KH_EINVAL also for gamma outside 0..2 or p != 16. */
+kh_status ctm_flux(kh_ctx* ctx, int slot, int gamma, double* host_out);
+
 /* --- eeFU bond update (Fig. 3(b), Sec. III) -------------------------------- */
 
 /* One gate layer on direction gamma (0 x, 1 y, 2 z): build the gated

@@ -25,7 +25,7 @@ ABI_FUNCTIONS = [
     "kh_config_defaults", "kh_workspace_bytes", "kh_create", "kh_destroy", "kh_last_error",
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
-    "ctm_expval", "ctm_correlation_length", "eefu_apply_gate", "eefu_cost_gradient", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
+    "ctm_expval", "ctm_correlation_length", "ctm_plaquette", "ctm_flux", "eefu_apply_gate", "eefu_cost_gradient", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
     "eefu_trotter_step", "eefu_evolve", "eefu_evolve_batch", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
     "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_svd_refined", "kh_selftest_orth", "kh_selftest_fp64_newton",
     "kh_selftest_site_layered_bytes", "kh_selftest_site_layered", "kh_gemm_noalloc",
@@ -77,6 +77,8 @@ def load_library(path=LIB_PATH):
         "ctm_kappa": (I, [P, I, dp]),
         "ctm_expval": (I, [P, I, dp, I, dp]),
         "ctm_correlation_length": (I, [P, I, I, I, D, dp]),
+        "ctm_plaquette": (I, [P, I, dp, dp]),
+        "ctm_flux": (I, [P, I, I, dp]),
         "eefu_apply_gate": (I, [P, I, dp, I, I, D, dp]),
         "eefu_cost_gradient": (I, [P, I, dp, P, P, I, I, D, P, P, dp]),
         "observables": (I, [P, dp, D, D, I, I, D, dp]),
@@ -477,6 +479,25 @@ class Context:
         o, op = _dptr(out)
         self._check(lib().ctm_correlation_length(self._ctx, slot, direction, max_iter, tol, op))
         return float(o[0]), float(o[1]), int(o[2])
+
+    def ctm_plaquette(self, slot, ops):
+        """(<O_ul O_ur O_dr O_dl>, plain cluster) for four p x p operators on
+        a 2 x 2 plaquette of slot's lattice (upper-left first, clockwise)."""
+        ops = np.ascontiguousarray(ops, dtype=np.float64)
+        o, op = _dptr(ops)
+        out = np.zeros(2)
+        r, rp = _dptr(out)
+        self._check(lib().ctm_plaquette(self._ctx, slot, op, rp))
+        return float(r[0]), float(r[1])
+
+    def flux(self, gamma, slot=None):
+        """<W_p> from the gamma composite's environment; slot defaults to the
+        observables' slot of that mapping (3 + gamma)."""
+        g = GAMMA.get(gamma, gamma)
+        out = np.zeros(2)
+        r, rp = _dptr(out)
+        self._check(lib().ctm_flux(self._ctx, 3 + g if slot is None else slot, g, rp))
+        return float(r[0])
 
     def eefu_apply_gate(self, gamma, gate, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12, info=True):
         g, gp = _dptr(gate)

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libeefu_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ctm.cu", "bond.cu", "abi.cu", "selftest.cu", "tcgen05.cu", "noalloc.cu", "checkpoint.cu", "refine.cu", "xi.cu", "layered.cu"]
+SOURCES = ["ctm.cu", "bond.cu", "abi.cu", "selftest.cu", "tcgen05.cu", "noalloc.cu", "checkpoint.cu", "refine.cu", "xi.cu", "layered.cu", "plaquette.cu"]
 
 
 def nvcc():

@@ -352,6 +352,28 @@ kh_status ctm_correlation_length(kh_ctx* ctx, int slot, int direction, int max_i
     });
 }
 
+kh_status ctm_plaquette(kh_ctx* ctx, int slot, const double* host_ops, double* host_out) {
+    KH_RANGE();
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !host_ops || !host_out) kh::fail(KH_EINVAL, "bad arguments");
+        ctx->eng->plaquette(slot, host_ops, host_out);
+    });
+}
+
+kh_status ctm_flux(kh_ctx* ctx, int slot, int gamma, double* host_out) {
+    KH_RANGE();
+    return guard(ctx, [&] {
+        if (!slot_ok(ctx, slot) || !host_out || gamma < 0 || gamma > 2) kh::fail(KH_EINVAL, "bad arguments");
+        if (ctx->eng->slot_p(slot) != 16) kh::fail(KH_EINVAL, "slot does not hold a composite (p = 16)");
+        std::vector<double> ops(4 * 256);
+        kh::flux_operators(gamma, ops.data());
+        double r[2];
+        ctx->eng->plaquette(slot, ops.data(), r);
+        host_out[0] = -r[0];         // sigma^y sigma^y = -Ytilde Ytilde
+        host_out[1] = r[1];
+    });
+}
+
 kh_status ctm_expval(kh_ctx* ctx, int slot, const double* ops, int n_ops, double* vals) {
     KH_RANGE();
     return guard(ctx, [&] {

@@ -146,9 +146,9 @@ __global__ void wt_kernel(const double* __restrict__ Tm, int p, int D, T* Wc, T*
 // tile (the TF32 head, then the FP32 remainder, with 3 passes), zero outside
 // the operand.  Layout [kind][frame][chunk][hi, lo], per1 / per2 floats per
 // (kind, frame).
-__global__ void layered_img_kernel(const double* __restrict__ Tm, int p, int D, lay::Plan P, int npass,
-                                   float* __restrict__ img1, float* __restrict__ img2, long long per1,
-                                   long long per2) {
+__global__ void layered_img_kernel(const double* __restrict__ Tm, const double* __restrict__ Tb, int p, int D,
+                                   lay::Plan P, int npass, float* __restrict__ img1, float* __restrict__ img2,
+                                   long long per1, long long per2) {
     // per1, per2 in floats; elements of P.esz bytes (TF32 values or BF16)
     const int npl = npass == 3 ? 2 : 1;
     const int epf = 4 / P.esz;                                 // elements per float slot
@@ -180,7 +180,7 @@ __global__ void layered_img_kernel(const double* __restrict__ Tm, int p, int D, 
         if (in >= 0 && pp < p) {
             const int off = kind == 0 ? frame_offset(f, in / D, in % D, out / D, out % D, D)
                                       : frame_offset(f, in / D, out / D, out % D, in % D, D);
-            v = Tm[pp * D4 + off];
+            v = (ket ? Tm : Tb)[pp * D4 + off];
         }
         if (P.esz == 2) {
             __nv_bfloat16* dst = (__nv_bfloat16*)(ket ? img1 : img2);
@@ -197,12 +197,20 @@ __global__ void layered_img_kernel(const double* __restrict__ Tm, int p, int D, 
 }
 
 void build_layered_images(const double* Tm, int p, int D, int npass, bool bf16, float* img1, float* img2,
-                          long long per1, long long per2, cudaStream_t st) {
+                          long long per1, long long per2, cudaStream_t st, const double* Tbra) {
     const long long tot = 8 * (per1 + per2) * (bf16 ? 2 : 1);
-    layered_img_kernel<<<grid_for(tot), 256, 0, st>>>(Tm, p, D, lay::make_plan(D, npass, bf16), npass, img1, img2,
-                                                      per1, per2);
+    layered_img_kernel<<<grid_for(tot), 256, 0, st>>>(Tm, Tbra ? Tbra : Tm, p, D, lay::make_plan(D, npass, bf16),
+                                                      npass, img1, img2, per1, per2);
     KH_LAUNCHED();
 }
+
+template <typename T>
+void derive_operands(const double* Tm, int p, int D, int pmax, T* Tcor, T* Tedg, cudaStream_t st) {
+    derived_kernel<T><<<grid_for(4LL * p * D * D * D * D), 256, 0, st>>>(Tm, p, D, pmax, Tcor, Tedg);
+    KH_LAUNCHED();
+}
+template void derive_operands<float>(const double*, int, int, int, float*, float*, cudaStream_t);
+template void derive_operands<double>(const double*, int, int, int, double*, double*, cudaStream_t);
 
 template <typename T>
 void Engine<T>::build_derived(Slot<T>& sl) {

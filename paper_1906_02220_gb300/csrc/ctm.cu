@@ -123,6 +123,14 @@ void Engine<T>::layout(Carver& cv) {
     cost = cv.take<double>(64);
     flags = cv.take<int>(64);
     tc_err = cv.take<int>(64);
+    pq_T = cv.take<double>((long long)d.pmax * d.D4);
+    if (d.lay) {
+        pq_img1 = cv.take<T>(8 * d.lay1);
+        pq_img2 = cv.take<T>(8 * d.lay2);
+    } else {
+        pq_cor = cv.take<T>(4LL * d.pmax * d.D4);
+        pq_edg = cv.take<T>(4LL * d.pmax * d.D4);
+    }
     nlanes = d.nslots >= 6 ? 3 : 1;
     for (int i = 1; i < nlanes; ++i) {
         carve_lane(cv);
@@ -572,7 +580,9 @@ void Engine<T>::refresh_operands(Slot<T>& sl) {
 //    out[b][(ok,ob)] = sum_{(ib,ik)} Y[b][(ib,ik)] Wt[(ok,ob)][(ib,ik)]   (2 nb D^8 flops),
 //    on the tensor cores when the precision asks for them;
 //  otherwise layer by layer: the ket layer as one GEMM (K = D^2), then the
-//    bra layer batched over b (K = p D^2)                                  (4 nb p D^6 flops).
+//    bra layer batched over b (K = p D^2)                                  (4 nb p D^6 flops);
+//    with TLb given, the bra layer reads TLb instead of TL (an operator on
+//    the ket layer only).
 // The double-layer site contraction runs as a 3xTF32 tensor-core GEMM: its
 // Y operand is then written directly as the (hi, lo) pair into (mup, mdn).
 template <typename T>
@@ -591,7 +601,7 @@ void Engine<T>::site_operand(const Slot<T>& sl, const T* Y, T* Yp, const std::ve
 
 template <typename T>
 void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, const T* L1, const T* L2, int p, T* out,
-                           const T* Wt, const T* Wt_lo, bool presplit) {
+                           const T* Wt, const T* Wt_lo, bool presplit, const T* TLb) {
     const int d2 = dm.d2, d4 = dm.D4;
     prof_begin(1);
     if (!Wt && L1) {                                   // layered, on the tensor cores
@@ -622,7 +632,7 @@ void Engine<T>::site_layer(const T* Ybuf, long long nb, const T* TL, const T* L1
         g.M = d2; g.N = d2; g.K = d2 * p;
         g.batch = (int)((nb - b0) < 65535 ? (nb - b0) : 65535);
         g.A = Zk + b0 * (long long)d2 * p * d2; g.sAm = 1; g.sAk = d2; g.sAb = (long long)d2 * p * d2;
-        g.B = TL; g.sBk = d2; g.sBn = 1; g.sBb = 0;
+        g.B = TLb ? TLb : TL; g.sBk = d2; g.sBn = 1; g.sBb = 0;
         g.C = out + b0 * (long long)d2 * d2; g.sCm = d2; g.sCn = 1; g.sCb = (long long)d2 * d2;
         g.alpha = T(1); g.beta = T(0); g.colscale = nullptr;
         gemm<T>(g, st);

@@ -115,6 +115,8 @@ struct EngineBase {
     virtual double kappa(int slot) = 0;
     virtual void expval(int slot, const double* ops, int n_ops, double* vals) = 0;
     virtual void correlation_length(int slot, int dir, int max_iter, double tol, double* out) = 0;
+    virtual void plaquette(int slot, const double* ops, double* out) = 0;
+    virtual int slot_p(int slot) const = 0;    // physical dimension of slot's tensor (0 = none)
     virtual void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) = 0;
     virtual void cost_gradient(int gamma, const double* gate, const double* A2, const double* B2, int mx, int mn,
                                double tol, double* gA, double* gB, double* cost) = 0;
@@ -236,7 +238,7 @@ struct Engine : EngineBase {
     void corner(Slot<T>& sl, int frame, int which);
     void site_layer(const T* Ybuf, long long nb, const T* TL, const T* L1, const T* L2, int p, T* out,
                     const T* Wt, const T* Wt_lo,
-                    bool presplit = false);
+                    bool presplit = false, const T* TLb = nullptr);
     bool site_presplit(const Slot<T>& sl) const;
     // operand image (1 = ket, 2 = bra) of the layered tensor-core contraction
     // for (kind: 0 corner, 1 edge; frame f), or null when the slot uses
@@ -280,6 +282,13 @@ struct Engine : EngineBase {
     double kappa(int slot) override;
     void expval(int slot, const double* ops, int n_ops, double* vals) override;
     void correlation_length(int slot, int dir, int max_iter, double tol, double* out) override;   // xi.cu
+    void plaquette(int slot, const double* ops, double* out) override;                            // plaquette.cu
+    int slot_p(int slot) const override { return slots[slot].p; }
+    void plaquette_corner(Slot<T>& sl, int f, const double* Tk, T* out);
+    // scratch of the plaquette: the operator-dressed site tensor (FP64) and
+    // its site-contraction operands (layered images, or frame layouts)
+    double* pq_T = nullptr;
+    T *pq_img1 = nullptr, *pq_img2 = nullptr, *pq_cor = nullptr, *pq_edg = nullptr;
     void apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) override;
     void cost_gradient(int gamma, const double* gate, const double* A2in, const double* B2in, int mx, int mn,
                        double tol, double* gA, double* gB, double* cost_out) override;
@@ -316,6 +325,17 @@ void gram2(const T* A, const T* B, int n, int k, double* dG, cudaStream_t st);
 size_t svd_refine_scratch(int k);
 void svd_refine_fp64(const double* G, int k, const double* L, const double* Q, double* s, double* Lo, double* Qo,
                      double* work, double rel_gap, cudaStream_t st);
+
+// Frame layouts of a site tensor Tm[p][D^4] for the two-layer site
+// contraction (bond.cu): Tcor, Tedg 4 frames x pmax D^4 each.
+template <typename T>
+void derive_operands(const double* Tm, int p, int D, int pmax, T* Tcor, T* Tedg, cudaStream_t st);
+
+// The four 16 x 16 composite-site operators of the plaquette flux W_p in the
+// gamma mapping (plaquette.cu), real form: sigma^y enters as i Ytilde with
+// Ytilde = [[0, -1], [1, 0]], and W_p = -(product of these) since W_p holds
+// sigma^y on exactly two sites.
+void flux_operators(int gamma, double* ops);
 
 Dims make_dims(const kh_config& c, bool fp64);
 void validate(const kh_config& c);

@@ -140,9 +140,11 @@ long long layered_img2_floats(int D, int p, int npass, bool bf16 = false);
 // Operand images of all (kind, frame) pairs from the FP64 site tensor
 // Tm[p][D^4] (legs l, u, r, d of frame 0): img1 holds 8 x per1 floats, img2
 // 8 x per2 (per1, per2 at least layered_img1_floats / layered_img2_floats for
-// p), layout [kind][frame][chunk][hi, lo].
+// p), layout [kind][frame][chunk][hi, lo].  With Tbra given, the bra images
+// come from Tbra (same shape) and the ket images from Tm: the mixed double
+// layer of an operator applied to the ket layer only.
 void build_layered_images(const double* Tm, int p, int D, int npass, bool bf16, float* img1, float* img2,
-                          long long per1, long long per2, cudaStream_t st);
+                          long long per1, long long per2, cudaStream_t st, const double* Tbra = nullptr);
 
 // out[b][ok][ob] (row-major, nb x D^2 x D^2) from Y[b][ib][ik] (row-major,
 // nb x D^2 x D^2) and the operand images of one (kind, frame).  Tensor-core

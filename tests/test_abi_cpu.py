@@ -153,6 +153,16 @@ def test_batch_gradient_and_selftest_arguments_without_gpu(g):
     assert lib.kh_selftest_site_layered_bytes(3, 9, 16, 4096) == 0
 
 
+def test_plaquette_and_flux_arguments_without_gpu(g):
+    """ctm_plaquette and ctm_flux reject a null context before any GPU work."""
+    import ctypes
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ops = np.tile(np.eye(16), (4, 1, 1))
+    out = np.zeros(2)
+    assert g.lib().ctm_plaquette(None, 0, dp(ops), dp(out)) == g.KH_EINVAL
+    assert g.lib().ctm_flux(None, 3, 0, dp(out)) == g.KH_EINVAL
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "tf32", "bf16"])
 @pytest.mark.parametrize("D", [2, 4, 6, 8])
 def test_layered_form_sizes_the_workspace(g, prec, D):
