@@ -458,6 +458,15 @@ def run_ours(a, rank, world, local, pg):
             variants.append(mixed_batch_variant(g, dev, a, w, a.prec, 2, proj_fp64=a.proj_fp64))
         cpu = None if (a.no_cpu_baseline or world > 1) else cpu_baseline(a, w, wl.A0, wl.B0)   # N = 1 only
         sw = sweeps_per_step(a)
+        try:
+            # plaquette flux of the final state (Sec. V), from the z mapping's
+            # observables environment; outside the timed region
+            t0 = time.perf_counter()
+            wv = wl.ctx.flux("z")
+            flux = {"value": wv, "mapping": "z", "ms": (time.perf_counter() - t0) * 1e3,
+                    "note": "state after all steps; not timed"}
+        except Exception as e:                      # reported, never fatal to the bench line
+            flux = {"error": str(e)}
         out = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -474,6 +483,7 @@ def run_ours(a, rank, world, local, pg):
             "ctm_sweep_tflops": step_flops(D, chi, sw) / (t_max / a.steps * 1e-3) / 1e12,
             "E_site": last["E_site"] if last else None,
             "err_vs_fp64": err,
+            "flux_W": flux,
             "roofline": roofs.get("corners"),
             "roofline_half_system_product": roofs.get("half_system_product"),
             "roofline_absorb": roofs.get("absorb"),

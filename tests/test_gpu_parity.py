@@ -573,6 +573,28 @@ def test_trajectory_matches_oracle_evolution(g):
     assert np.abs(C - Cref).max() < 1e-9 * 2 * ref[-1]["beta"] ** 2 / (2 * dbeta) + 1e-12
 
 
+@pytest.mark.parametrize("prec,D,chi,dbeta,n", [("fp64", 2, 8, 0.05, 10), ("fp64", 4, 12, 0.02, 10),
+                                                 ("tf32x3", 4, 16, 0.05, 6)])
+def test_klein_duality_of_trajectories(g, prec, D, chi, dbeta, n):
+    """Eq. (4): the library's trajectories at (J, K) and at the dual couplings
+    (-J, K + 2J), both from the beta = 0 state in the 2-site cell, give the
+    same E/site and bond energies (exactly in exact arithmetic: the duality
+    is a product of single-site rotations that the symmetric iterates absorb
+    as a virtual gauge; see the oracle pin).  FP64 within 1e-9; 3xTF32 within
+    twice the single-precision energy target (two independent runs)."""
+    J, K = model.couplings(0.3 * np.pi)
+    rows = []
+    for j, k in ((J, K), (-J, K + 2 * J)):
+        ctx = g.Context(D, chi, prec, svd_cut=CUT[prec])
+        traj = ctx.evolve(j, [k, k, k], dbeta, n, n // 2, ctm_max_sweeps=200,
+                          ctm_tol=1e-12 if prec == "fp64" else 1e-7)
+        rows.append(np.array([[r["E_site"], r["Hx"], r["Hy"], r["Hz"]] for r in traj]))
+        ctx.close()
+    tol = 1e-9 if prec == "fp64" else 2 * E_TOL
+    assert np.abs(rows[0]).min() > 1e-3
+    assert np.abs(rows[0] - rows[1]).max() < tol, rows[0] - rows[1]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
 @pytest.mark.parametrize("Kh", [0.3, 0.6])
 def test_correlation_length_of_decoupled_chains(g, prec, Kh):

@@ -308,3 +308,27 @@ def test_bonds_between_composites_are_the_inner_bond_of_another_mapping():
     xz = observables.expectation(X, observables.phys_op(O_AB=np.kron(S["x"], S["z"])))
     zx = observables.expectation(X, observables.phys_op(O_AB=np.kron(S["z"], S["x"])))
     assert abs(xz - zx) > 1e-3
+
+
+# ---------------------------------------------------------------- Klein duality on the iPEPS
+
+@pytest.mark.parametrize("phi", [0.3 * np.pi, -0.35 * np.pi])
+def test_klein_duality_on_the_two_site_ipeps(phi):
+    """Eq. (4): H(J, K) and H(-J, K + 2J) are related by a product of
+    single-site pi rotations (R_gamma on one end of every gamma bond, a
+    4-sublattice pattern), and so are the Trotter gates bond by bond.  The
+    beta = 0 start and every truncated update stay symmetric under the
+    global pi rotations, which lets the 4-sublattice pattern act as a
+    virtual gauge on the gamma legs: the 2-site-cell eeFU trajectories of
+    the two couplings give the same bond energies to rounding (the
+    duality the paper uses to keep 2 sublattices)."""
+    J, K = model.couplings(phi)
+    out = []
+    for j, k in ((J, K), (-J, K + 2 * J)):
+        st = _fresh(2, 8, J=j, K=k)
+        res = eefu.evolve(st, 0.05, 10, measure_every=5)
+        out.append(np.array([[r["E_site"], r["Hx"], r["Hy"], r["Hz"]] for r in res]))
+    assert np.abs(out[0]).min() > 1e-3
+    assert np.abs(out[0] - out[1]).max() < 1e-12, out[0] - out[1]
+    # the map is not trivial: the couplings differ and so do the gates
+    assert abs(J) > 0.1
