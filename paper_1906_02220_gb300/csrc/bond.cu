@@ -512,6 +512,26 @@ __global__ void svd_init_kernel(const TJ* Ut, const TJ* sv, int mT, int D, doubl
     }
 }
 
+// Start of the wide bonds (4 D^2 > 160, D = 7, 8): the leading left singular
+// pairs of Tm from a subspace iteration (engine's bond_start_subspace); U
+// (mT x kq, FP64) and the Ritz eigenvalues e (descending) of Tm Tm^T are
+// stored as the FP32 triplets svd_init_kernel reads: Ut[r][j] = U[r][j]
+// (row stride mT), sv[j] = sqrt(max(e_j, 0)), zero past kq.
+__global__ void start_store_kernel(const double* __restrict__ U, const double* __restrict__ ev, int mT, int kq,
+                                   float* __restrict__ Ut, float* __restrict__ sv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mT * kq; i += gridDim.x * blockDim.x) {
+        const int r = i / kq, j = i % kq;
+        Ut[(long long)r * mT + j] = (float)U[i];
+        if (r == 0) sv[j] = (float)sqrt(fmax(ev[j], 0.0));
+    }
+    for (int j = kq + blockIdx.x * blockDim.x + threadIdx.x; j < mT; j += gridDim.x * blockDim.x) sv[j] = 0.0f;
+}
+
+__global__ void uniform_fill_kernel(double* __restrict__ V, long long n, uint64_t seed, uint64_t stream) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        V[i] = rnd_uniform(seed, stream, (uint64_t)i);
+}
+
 // ------------------------------------------------------------------ gauge
 
 __device__ void jacobi_serial(double* A, double* V, int n) {
@@ -748,6 +768,34 @@ void Engine<T>::cost_gradient(int gamma, const double* gate, const double* A2in,
 
 // ------------------------------------------------------------------ ALS driver
 
+// Leading left singular vectors of Tm (mT x mT, FP64) for the start of a bond
+// too wide for the one-CTA Jacobi (4 D^2 > 160): subspace iteration on
+// Tm Tm^T with a block of kq = D + 8 columns from a seeded uniform draw,
+// V <- orth(Tm (Tm^T V)) (ordered CholQR2) twelve times, then the
+// Rayleigh-Ritz step H = Z^T Z with Z = Tm^T V, H = W diag(e) W^T (Jacobi),
+// U = V W.  The start only seeds the ALS, which converges in FP64.  Scratch:
+// Gt (four mT x kq blocks), Wt (kq x kq blocks).
+template <typename T>
+void Engine<T>::bond_start_subspace(int mT, int D) {
+    const int kq = std::min(mT, D + 8);
+    const long long blk = (long long)mT * kq;
+    double *V = Gt, *Z = Gt + blk, *Y = Gt + 2 * blk, *tmp = Gt + 3 * blk;
+    double *Xk = Wt, *dG = Wt + kq * kq, *H = Wt + 2 * kq * kq, *W = Wt + 3 * kq * kq, *ev = Wt + 4 * kq * kq;
+    uniform_fill_kernel<<<grid_for(blk), 256, 0, st>>>(V, blk, cfg.seed, 0xb0adULL);
+    KH_LAUNCHED();
+    for (int it = 0; it < 12; ++it) {
+        gemm_rm<double>(mT, kq, mT, Tm, true, V, false, Z, st);     // Z = Tm^T V
+        gemm_rm<double>(mT, kq, mT, Tm, false, Z, false, Y, st);    // Y = Tm Z
+        cholqr2<double>(Y, mT, kq, 1e-12, tmp, Xk, dG, V, st);
+    }
+    gemm_rm<double>(mT, kq, mT, Tm, true, V, false, Z, st);
+    gemm_rm<double>(kq, kq, mT, Z, true, Z, false, H, st);          // H = Z^T Z
+    jacobi_eig<double>(H, kq, kq, 0, W, kq, 0, ev, 0, 1, 60, 1e-14, nullptr, nullptr, st);
+    gemm_rm<double>(mT, kq, kq, V, false, W, false, Y, st);         // U = V W
+    start_store_kernel<<<grid_for(blk), 256, 0, st>>>(Y, ev, mT, kq, Wtf, Ltf);
+    KH_LAUNCHED();
+}
+
 template <typename T>
 int Engine<T>::als_run(int gamma, double* rel_cost) {
     const int D = dm.D, D4 = dm.D4, m = D * D * D, mT = 4 * dm.d2;
@@ -767,8 +815,12 @@ int Engine<T>::als_run(int gamma, double* rel_cost) {
     // Tm^T (Tm^T Q = L S, so Tm = Q S L^T and U = Q); only the D leading
     // triplets are used, so only the D + 4 largest columns must converge
     // (the near-null tail of Tm would otherwise keep the sweeps going).
-    permute<double, float>(Tm, Gtf, {mT, mT}, {1, 0}, st);
-    svd_jacobi<float>(Gtf, mT, Ltf, (float*)Gt, Wtf, 60, 2e-6, 0.0, st, nullptr, D + 4);
+    if (mT <= jacobi_kmax<float>()) {
+        permute<double, float>(Tm, Gtf, {mT, mT}, {1, 0}, st);
+        svd_jacobi<float>(Gtf, mT, Ltf, (float*)Gt, Wtf, 60, 2e-6, 0.0, st, nullptr, D + 4);
+    } else {
+        bond_start_subspace(mT, D);
+    }
     svd_init_kernel<float><<<grid_for(mT * D), 256, 0, st>>>(Wtf, Ltf, mT, D, A2, colsc, Wd);
     KH_LAUNCHED();
     // B''[(sB,aB,d,l)][k] = sum_i Tm[i][.] Wd[i][k] colsc[k]
@@ -834,7 +886,6 @@ template <typename T>
 void Engine<T>::apply_gate(int gamma, const double* gate, int mx, int mn, double tol, double* info) {
     if (gamma < 0 || gamma > 2) fail(KH_EINVAL, "gamma must be 0, 1 or 2");
     if (dm.nslots < 3) fail(KH_EINVAL, "eeFU needs n_slots >= 3");
-    if (4 * dm.d2 > jacobi_kmax<float>()) fail(KH_EINVAL, "bond update start limited to D <= 6");
     build_composite(gamma, gamma, gate);
     double delta = 0.0;
     int sw = sweep(gamma, mx, mn, tol, &delta);

@@ -259,6 +259,7 @@ struct Engine : EngineBase {
 
     // bond internals
     int als_run(int gamma, double* rel_cost);
+    void bond_start_subspace(int mT, int D);
     void gauge_and_store(int gamma);
 
     // API

@@ -266,6 +266,76 @@ def test_kz_only_closed_form(g, prec):
     assert abs(r["E_site"] - exact.kz_only_energy(Kz, 0.4)) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec,D", [("fp64", 7), ("fp64", 8), ("tf32x3", 8)])
+def test_wide_bonds_closed_forms(g, prec, D):
+    """D = 7, 8: the bond matrix T' has 4 D^2 = 196, 256 rows, past the
+    one-CTA Jacobi, so the bond update starts from the subspace-iteration
+    triplets.  One x layer from the beta = 0 state is the exact dimer (the
+    gated bond has Schmidt rank 4 <= D: no truncation, zero cost); K_z-only
+    Trotter steps (decoupled z dimers) follow the closed form."""
+    J, K = model.couplings(0.3 * np.pi)
+    chi = 8
+    ctx = g.Context(D, chi, prec, svd_cut=CUT[prec])
+    db = 0.2
+    info = ctx.eefu_apply_gate("x", g.gate(g.bond_hamiltonian("x", J, K), db / 4),
+                               ctm_tol=1e-12 if prec == "fp64" else 1e-7)
+    r = ctx.observables([g.bond_hamiltonian(gm, J, K) for gm in "xyz"], ctm_tol=1e-12 if prec == "fp64" else 1e-7)
+    want = exact.dimer_energy(J, K, db / 2)
+    tol = TOL[prec]
+    assert abs(r["Hx"] - want) < tol
+    assert abs(r["Hy"]) < tol and abs(r["Hz"]) < tol
+    assert info["rel_cost"] < (1e-10 if prec == "fp64" else 1e-6)
+    ctx.close()
+    Kz = 1.3
+    ctx = g.Context(D, chi, prec, svd_cut=CUT[prec])
+    for _ in range(2):
+        ctx.eefu_trotter_step(0.0, [0.0, 0.0, Kz], 0.05)
+    r = ctx.observables([g.bond_hamiltonian(gm, 0.0, k) for gm, k in zip("xyz", [0.0, 0.0, Kz])])
+    assert abs(r["E_site"] - exact.kz_only_energy(Kz, 0.1)) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_wide_bond_gate_layer_matches_oracle(g, prec):
+    """D = 8 (the bond matrix 256 x 256, the subspace-iteration start): one z
+    layer of a Kitaev-Heisenberg step on a random state with its CTMRG
+    converged, the bond update, then the observables, against the oracle's
+    stored values (tests/golden/wide_bond_parity_D8_chi8.json, written by
+    make_wide_bond_parity.py from oracle/ only).  All eight kept singular
+    values lie above 1e-3 s_1, so the single-precision cut-off (1e-4) and the
+    FP64 one truncate alike.  FP64: energies and moments within 1e-8, spectra
+    1e-7 (the kept tail is flat, s_8 / s_2 ~ 0.6, so the fixed point converges
+    slowly in the tail), relative cost 1e-6 relative; 3xTF32 with the FP64
+    projector SVD: the single-precision targets."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wide_bond_parity_D8_chi8.json")))
+    c = gold["case"]
+    D, chi = c["D"], c["chi"]
+    gl = gold["gate_layer"]
+    assert min(min(s) for s in gl["spectra"]) > 1e-3 * max(max(s) for s in gl["spectra"])
+    A, B = kh_inputs.random_site_tensors(D, c["seed"])
+    fp64 = prec == "fp64"
+    ctx = g.Context(D, chi, prec, svd_cut=CUT[prec], proj_fp64=0 if fp64 else 1)
+    ctx.set_state(_t(A), _t(B))
+    gate = g.gate(g.bond_hamiltonian("z", c["J"], c["K"]), c["dbeta"] / 2)
+    ctm_tol = 1e-10 if fp64 else 1e-7
+    info = ctx.eefu_apply_gate("z", gate, ctm_max_sweeps=400, ctm_min_sweeps=3, ctm_tol=ctm_tol)
+    assert abs(info["rel_cost"] - gl["rel_cost"]) < (1e-6 if fp64 else 1e-4) * gl["rel_cost"], \
+        (info["rel_cost"], gl["rel_cost"])
+    for d in range(4):
+        s, _ = ctx.ctm_projectors(2, d)
+        err = np.abs(_nrm(s.cpu().numpy()) - _nrm(gl["spectra"][d])).max()
+        assert err < (1e-7 if fp64 else SPEC_TOL), (d, err)
+    Hs = [g.bond_hamiltonian(gm, c["J"], c["K"]) for gm in "xyz"]
+    r = ctx.observables(Hs, ctm_max_sweeps=400, ctm_min_sweeps=3, ctm_tol=ctm_tol)
+    ro = gold["observables"]
+    tol = 1e-8 if fp64 else E_TOL
+    for key in ("E_site", "Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+        assert abs(r[key] - ro[key]) < tol * max(1.0, abs(ro[key])), (key, r[key], ro[key])
+    ctx.close()
+
+
 @pytest.mark.parametrize("D,chi,steps", [(2, 16, 4), (3, 12, 2)])
 def test_bf16_trotter_steps_near_oracle(g, D, chi, steps):
     """BF16 contractions (the layered site contraction on kind::f16, one
