@@ -444,10 +444,13 @@ def run_ours(a, rank, world, local, pg):
         variants = []
         if not a.no_variants and world == 1:
             # the plain FP64 GPU form of the same workload, and the largest
-            # single-precision configuration (D, chi) = (6, 144)
+            # single-precision configurations (D, chi) = (6, 144), (8, 144)
             variants.append(variant(g, dev, a, w, D, chi, "fp64", 2, 3, flush))
             variants.append(variant(g, dev, a, w, D, chi, a.prec, 3, 3, flush, proj_fp64=1 - a.proj_fp64))
             variants.append(variant(g, dev, a, w, 6, 144, a.prec, 2, 3, flush, proj_fp64=a.proj_fp64))
+            # the largest bond dimension, D = 8 (n = chi D^2 = 9216), at the largest chi of the
+            # one-CTA projector solvers
+            variants.append(variant(g, dev, a, w, 8, 144, a.prec, 2, 3, flush, proj_fp64=a.proj_fp64))
             # the same workload with the double-layer site operand (the D^2 index formed)
             variants.append(variant(g, dev, a, w, D, chi, a.prec, 3, 3, flush, proj_fp64=a.proj_fp64, site_form=2))
             # BF16 contractions (layered site contraction on kind::f16)
