@@ -296,6 +296,14 @@ kh_status kh_bond_hamiltonian(int gamma, double J, double K_gamma, double hA, do
 /* g = exp(-tau H) for a real symmetric 4x4 H (eigendecomposition by Jacobi). */
 kh_status kh_gate(const double* host_H, double tau, double* host_g);
 
+/* The four 16 x 16 composite-site operators that ctm_flux places on the 2 x 2
+ * plaquette of the gamma mapping (Sec. V flux; layout and geometry as in
+ * ctm_flux), in real form: sigma^y entered as [[0,-1],[1,0]], so W_p is
+ * minus the product of these four.  host_ops[4][16][16], row-major on
+ * p = (sA, aA, sB, aB), upper-left first.  Host only.  KH_EINVAL for gamma
+ * outside 0..2 or a NULL pointer. */
+kh_status kh_flux_operators(int gamma, double* host_ops);
+
 /* One second-order Trotter step (Eq. 6): gate layers x, y, z, y, x with
  * exp(-tau H^gamma), tau = dbeta/4, dbeta/4, dbeta/2, dbeta/4, dbeta/4, the
  * bias (hA, hB) in the z gate, couplings J and K_gamma = K_xyz[gamma].  Each

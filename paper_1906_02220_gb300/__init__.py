@@ -25,7 +25,7 @@ ABI_FUNCTIONS = [
     "kh_config_defaults", "kh_workspace_bytes", "kh_create", "kh_destroy", "kh_last_error",
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
-    "ctm_expval", "ctm_correlation_length", "ctm_plaquette", "ctm_flux", "eefu_apply_gate", "eefu_cost_gradient", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate",
+    "ctm_expval", "ctm_correlation_length", "ctm_plaquette", "ctm_flux", "eefu_apply_gate", "eefu_cost_gradient", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate", "kh_flux_operators",
     "eefu_trotter_step", "eefu_evolve", "eefu_evolve_batch", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
     "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_svd_refined", "kh_selftest_orth", "kh_selftest_fp64_newton",
     "kh_selftest_site_layered_bytes", "kh_selftest_site_layered", "kh_gemm_noalloc",
@@ -84,6 +84,7 @@ def load_library(path=LIB_PATH):
         "observables": (I, [P, dp, D, D, I, I, D, dp]),
         "kh_bond_hamiltonian": (I, [I, D, D, D, D, dp]),
         "kh_gate": (I, [dp, D, dp]),
+        "kh_flux_operators": (I, [I, dp]),
         "eefu_trotter_step": (I, [P, D, dp, D, D, D, I, I, D, dp]),
         "eefu_evolve": (I, [P, D, dp, D, D, D, I, I, I, I, D, I, I, D, dp]),
         "eefu_evolve_batch": (I, [ctypes.POINTER(P), I, dp, dp, dp, dp, D, I, I, I, I, D, I, I, D, dp, ip]),

@@ -423,6 +423,13 @@ kh_status kh_gate(const double* H, double tau, double* g) {
     return KH_OK;
 }
 
+kh_status kh_flux_operators(int gamma, double* ops) {
+    KH_RANGE();
+    if (!ops || gamma < 0 || gamma > 2) return KH_EINVAL;
+    kh::flux_operators(gamma, ops);
+    return KH_OK;
+}
+
 kh_status eefu_trotter_step(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta,
                             int mx, int mn, double tol, double* info) {
     KH_RANGE();

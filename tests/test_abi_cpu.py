@@ -153,6 +153,30 @@ def test_batch_gradient_and_selftest_arguments_without_gpu(g):
     assert lib.kh_selftest_site_layered_bytes(3, 9, 16, 4096) == 0
 
 
+def test_flux_operators_match_the_oracle(g):
+    """The library's real-form flux operators (host code) against the oracle's
+    complex ones: each position's operator is the oracle's up to a factor i
+    (one sigma^y at that composite) or 1, the factors multiply to -1 (two
+    sigma^y), so W_p = -(product of the real forms) -- in every mapping."""
+    import ctypes
+    from oracle import observables
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    for gi, gamma in enumerate("xyz"):
+        ops = np.zeros((4, 16, 16))
+        assert g.lib().kh_flux_operators(gi, dp(ops)) == g.KH_OK
+        ref = observables.flux_operators(gamma)
+        phase = 1.0 + 0j
+        for f in range(4):
+            if np.abs(ref[f].imag).max() > 0:
+                assert np.abs(ref[f] - 1j * ops[f]).max() < 1e-15, (gamma, f)
+                phase *= 1j
+            else:
+                assert np.abs(ref[f] - ops[f]).max() < 1e-15, (gamma, f)
+        assert abs(phase + 1.0) < 1e-15
+    assert g.lib().kh_flux_operators(3, dp(np.zeros(1024))) == g.KH_EINVAL
+    assert g.lib().kh_flux_operators(0, None) == g.KH_EINVAL
+
+
 def test_plaquette_and_flux_arguments_without_gpu(g):
     """ctm_plaquette and ctm_flux reject a null context before any GPU work."""
     import ctypes
