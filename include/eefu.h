@@ -329,6 +329,17 @@ kh_status eefu_evolve(kh_ctx* ctx, double J, const double* host_K_xyz, double hA
                       int n_steps, int measure_every, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
                       int obs_max_sweeps, int obs_min_sweeps, double obs_tol, double* host_traj);
 
+/* eefu_evolve plus the plaquette flux <W_p> (Sec. V: its ordering marks
+ * the lower crossover of the pure Kitaev model) after every measurement, as
+ * ctm_flux computes it from the z mapping's observables environment (slot 5):
+ * host_flux[n_steps / measure_every] (host, not NULL).  host_traj as in
+ * eefu_evolve.  Needs the six slots of the observables (KH_EINVAL
+ * otherwise). */
+kh_status eefu_evolve_flux(kh_ctx* ctx, double J, const double* host_K_xyz, double hA, double hB, double dbeta,
+                           int n_steps, int measure_every, int ctm_max_sweeps, int ctm_min_sweeps, double ctm_tol,
+                           int obs_max_sweeps, int obs_min_sweeps, double obs_tol, double* host_traj,
+                           double* host_flux);
+
 /* Batched trajectories: n independent problems (different couplings, or
  * different D / chi / precision per context) advanced concurrently, one host
  * thread per context, each context's kernels on its own streams, so that the

@@ -26,7 +26,7 @@ ABI_FUNCTIONS = [
     "kh_set_state", "kh_get_state", "ctm_set_tensor", "ctm_build_composite", "ctm_init",
     "ctm_copy_env", "ctm_sweep", "ctm_projectors", "ctm_get_env", "ctm_metric", "ctm_kappa",
     "ctm_expval", "ctm_correlation_length", "ctm_plaquette", "ctm_flux", "eefu_apply_gate", "eefu_cost_gradient", "observables", "kh_version", "kh_bond_hamiltonian", "kh_gate", "kh_flux_operators",
-    "eefu_trotter_step", "eefu_evolve", "eefu_evolve_batch", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
+    "eefu_trotter_step", "eefu_evolve", "eefu_evolve_flux", "eefu_evolve_batch", "kh_launch_count", "kh_profile", "kh_selftest_bytes", "kh_selftest_gemm",
     "kh_selftest_symeig", "kh_selftest_svd", "kh_selftest_svd_refined", "kh_selftest_orth", "kh_selftest_fp64_newton",
     "kh_selftest_site_layered_bytes", "kh_selftest_site_layered", "kh_gemm_noalloc",
     "kh_gemm_noalloc_max_bytes", "kh_save", "kh_load_config", "kh_load",
@@ -87,6 +87,7 @@ def load_library(path=LIB_PATH):
         "kh_flux_operators": (I, [I, dp]),
         "eefu_trotter_step": (I, [P, D, dp, D, D, D, I, I, D, dp]),
         "eefu_evolve": (I, [P, D, dp, D, D, D, I, I, I, I, D, I, I, D, dp]),
+        "eefu_evolve_flux": (I, [P, D, dp, D, D, D, I, I, I, I, D, I, I, D, dp, dp]),
         "eefu_evolve_batch": (I, [ctypes.POINTER(P), I, dp, dp, dp, dp, D, I, I, I, I, D, I, I, D, dp, ip]),
         "kh_launch_count": (ctypes.c_ulonglong, []),
         "kh_profile": (I, [P, I, dp]),
@@ -545,19 +546,31 @@ class Context:
     TRAJ_KEYS = ["beta", "E_site", "Hx", "Hy", "Hz", "Ax", "Ay", "Az", "Bx", "By", "Bz", "trunc", "C"]
 
     def evolve(self, J, K_xyz, dbeta, n_steps, measure_every=1, hA=0.0, hB=0.0, ctm_max_sweeps=100,
-               ctm_min_sweeps=1, ctm_tol=1e-12, obs_max_sweeps=None, obs_min_sweeps=None, obs_tol=None):
+               ctm_min_sweeps=1, ctm_tol=1e-12, obs_max_sweeps=None, obs_min_sweeps=None, obs_tol=None,
+               flux=False):
         """Imaginary-time trajectory: list of dicts (TRAJ_KEYS) per measurement,
-        C the specific heat per site (NaN at the ends of the grid)."""
+        C the specific heat per site (NaN at the ends of the grid); with
+        flux=True each row also carries W, the plaquette flux (eefu_evolve_flux)."""
         nm = n_steps // measure_every
         out = np.zeros(max(nm, 1) * len(self.TRAJ_KEYS))
         o, op = _dptr(out)
         K, kp = _dptr(np.asarray(K_xyz, dtype=np.float64))
-        st = lib().eefu_evolve(self._ctx, J, kp, hA, hB, dbeta, n_steps, measure_every, ctm_max_sweeps,
-                               ctm_min_sweeps, ctm_tol, obs_max_sweeps or ctm_max_sweeps,
-                               obs_min_sweeps or ctm_min_sweeps, ctm_tol if obs_tol is None else obs_tol, op)
+        args = (self._ctx, J, kp, hA, hB, dbeta, n_steps, measure_every, ctm_max_sweeps, ctm_min_sweeps, ctm_tol,
+                obs_max_sweeps or ctm_max_sweeps, obs_min_sweeps or ctm_min_sweeps,
+                ctm_tol if obs_tol is None else obs_tol, op)
+        if flux:
+            w = np.zeros(max(nm, 1))
+            w, wp = _dptr(w)
+            st = lib().eefu_evolve_flux(*args, wp)
+        else:
+            st = lib().eefu_evolve(*args)
         self._check(st)
         rows = o.reshape(-1, len(self.TRAJ_KEYS))[:nm]
-        return [dict(zip(self.TRAJ_KEYS, r.tolist())) for r in rows]
+        res = [dict(zip(self.TRAJ_KEYS, r.tolist())) for r in rows]
+        if flux:
+            for r, x in zip(res, w[:nm].tolist()):
+                r["W"] = x
+        return res
 
     def observables(self, H_xyz, hA=0.0, hB=0.0, ctm_max_sweeps=100, ctm_min_sweeps=1, ctm_tol=1e-12):
         H = np.ascontiguousarray(np.stack([np.asarray(h, dtype=np.float64) for h in H_xyz]))

@@ -460,9 +460,15 @@ namespace {
 // The trajectory of eefu_evolve for one context (throws kh::Error).
 void evolve_one(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta, int n_steps,
                 int measure_every, int mx, int mn, double tol, int obs_mx, int obs_mn, double obs_tol,
-                double* traj) {
+                double* traj, double* wflux = nullptr) {
     if (!Kxyz || !traj || mx < 1 || obs_mx < 1 || n_steps < 1 || measure_every < 1 || !(dbeta > 0.0))
         kh::fail(KH_EINVAL, "bad arguments");
+    std::vector<double> wops;
+    if (wflux) {                       // the flux from the z mapping's observables slot
+        if (ctx->eng->dm.nslots < 6) kh::fail(KH_EINVAL, "the flux needs the six slots of the observables");
+        wops.resize(4 * 256);
+        kh::flux_operators(2, wops.data());
+    }
     static const int order[5] = {0, 1, 2, 1, 0};
     const double taus[5] = {dbeta / 4, dbeta / 4, dbeta / 2, dbeta / 4, dbeta / 4};
     double H3[48], G[5][16];
@@ -485,6 +491,11 @@ void evolve_one(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB,
             row[0] = beta0 + n * dbeta;
             for (int i = 0; i < 10; ++i) row[1 + i] = out[i];
             row[11] = out[10];
+            if (wflux) {
+                double r[2];
+                ctx->eng->plaquette(5, wops.data(), r);
+                wflux[n / measure_every - 1] = -r[0];       // sigma^y sigma^y = -Ytilde Ytilde
+            }
         }
     }
     // C = dE/dT = -beta^2 dE/dbeta by central differences on the uniform
@@ -509,6 +520,17 @@ kh_status eefu_evolve(kh_ctx* ctx, double J, const double* Kxyz, double hA, doub
     KH_RANGE();
     return guard(ctx, [&] {
         evolve_one(ctx, J, Kxyz, hA, hB, dbeta, n_steps, measure_every, mx, mn, tol, obs_mx, obs_mn, obs_tol, traj);
+    });
+}
+
+kh_status eefu_evolve_flux(kh_ctx* ctx, double J, const double* Kxyz, double hA, double hB, double dbeta,
+                           int n_steps, int measure_every, int mx, int mn, double tol, int obs_mx, int obs_mn,
+                           double obs_tol, double* traj, double* host_flux) {
+    KH_RANGE();
+    return guard(ctx, [&] {
+        if (!host_flux) kh::fail(KH_EINVAL, "bad arguments");
+        evolve_one(ctx, J, Kxyz, hA, hB, dbeta, n_steps, measure_every, mx, mn, tol, obs_mx, obs_mn, obs_tol, traj,
+                   host_flux);
     });
 }
 

@@ -171,3 +171,34 @@ def test_flux_after_observables_and_argument_checks(g):
         ctx.flux("x", slot=0)
     assert e.value.status == g.KH_EINVAL
     ctx.close()
+
+
+def test_trajectory_with_flux(g):
+    """eefu_evolve_flux: the same rows as eefu_evolve (the flux reads the
+    environments and changes nothing), and in every row the flux of the z
+    mapping's observables environment at that point: the last one equal to
+    ctm_flux afterwards and to the oracle's cluster on the library's
+    environment and state."""
+    from oracle import model
+    J, K = model.couplings(0.3 * np.pi)
+    D, chi = 2, 8
+    A, B = kh_inputs.random_site_tensors(D, 36)
+    kw = dict(ctm_max_sweeps=300, ctm_tol=1e-12)
+    c1 = g.Context(D, chi, "fp64")
+    c1.set_state(_t(A), _t(B))
+    t1 = c1.evolve(J, [K, K, K], 0.02, 4, 2, flux=True, **kw)
+    c2 = g.Context(D, chi, "fp64")
+    c2.set_state(_t(A), _t(B))
+    t2 = c2.evolve(J, [K, K, K], 0.02, 4, 2, **kw)
+    assert len(t1) == 2 and all("W" in r for r in t1)
+    for r1, r2 in zip(t1, t2):
+        for key in ("beta", "E_site", "Hx", "Hy", "Hz", "Ax", "Az", "Bx", "Bz"):
+            assert abs(r1[key] - r2[key]) < 1e-10 * max(1.0, abs(r2[key])), (key, r1[key], r2[key])
+    w_last = c1.flux("z")
+    assert abs(t1[-1]["W"] - w_last) < 1e-12 * abs(w_last) + 1e-18
+    As, Bs = c1.get_state()
+    ref = observables.flux(_gpu_env(c1, 5, D, chi), peps.composite(As.cpu().numpy(), Bs.cpu().numpy(), "z"), "z")
+    assert abs(t1[-1]["W"] - ref.real) < 1e-10 * abs(ref.real), (t1[-1]["W"], ref)
+    assert abs(ref.real) > 1e-6
+    c1.close()
+    c2.close()
